@@ -1,0 +1,262 @@
+"""Plain, slow, obviously correct CPU reference for batched tridiagonal solves.
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, ``__graft_entry__.smoke()`` and the CPU
+baseline leg of ``bench.py``; never by the CUDA library, with which it shares no code.
+
+Problem (Algorithm 1, "Problem: Ax = d (N times)"; Section 3.2.1: a, b and c are the
+sub-, main and super-diagonal of A): for every line,
+    a_i x_{i-1} + b_i x_i + c_i x_{i+1} = d_i,   i = 0..n-1,
+with a_0 and c_{n-1} ignored (no coupling outside the line). Arrays are numpy float64 of
+shape (lines, n) (or (n,)); ``d`` may carry extra trailing right-hand-side axes.
+
+Functions and the passage each follows:
+  thomas          -- the Thomas algorithm (Section 1), the plain definition x = A^{-1} d.
+  thomas_ext      -- the same sweep in numpy.longdouble (extended precision) for badly
+                     conditioned lines (the pinned Poisson zero mode).
+  dense_solve     -- x = A^{-1} d by dense LU with partial pivoting (numpy.linalg.solve).
+  partition_rows  -- split of a line into p contiguous partitions (Section 2.2; the paper
+                     is silent on uneven splits: the first n mod p partitions take one
+                     extra row, and every partition needs at least 2 rows).
+  dc_spike        -- the divide-and-conquer solve in the paper's own three-stage form
+                     (Section 2.1 stages 1-5; Algorithm 1: solve the decoupled system
+                     A~ x~ = d~, solve the reduced system Z y = E^T x~ of size 2p - 2
+                     (Section 2.2), correct x = x~ - Y y).
+  residual        -- r = d - A x.
+  adjoint_grads   -- gradients of a scalar loss through x = A^{-1} d: lambda = A^{-T} g,
+                     grad_d = lambda, grad_b = -lambda*x, grad_a_i = -lambda_i x_{i-1},
+                     grad_c_i = -lambda_i x_{i+1} (standard adjoint of a linear solve;
+                     the paper has no backward pass).
+  thomas_ragged   -- Thomas over lines of uneven length packed back to back.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+__all__ = ["thomas", "thomas_ext", "dense_matrix", "dense_solve", "partition_rows", "dc_spike",
+           "residual", "adjoint_grads", "transpose_coefficients", "thomas_ragged", "rel_l2"]
+
+
+def _as2d(*arrs):
+    return [np.asarray(x) for x in arrs]
+
+
+def thomas(a, b, c, d, dtype=np.float64):
+    """Thomas algorithm (Section 1): LU without pivoting, forward elimination then back substitution.
+
+    c'_0 = c_0/b_0, d'_0 = d_0/b_0; for i >= 1: w = b_i - a_i c'_{i-1}, c'_i = c_i/w,
+    d'_i = (d_i - a_i d'_{i-1})/w; then x_{n-1} = d'_{n-1}, x_i = d'_i - c'_i x_{i+1}.
+    Vectorised over lines (leading axes); loops over rows. ``d`` may have trailing RHS axes.
+    """
+    a, b, c, d = (np.asarray(t, dtype=dtype) for t in (a, b, c, d))
+    n = b.shape[-1]
+    extra = d.ndim - b.ndim  # trailing right-hand-side axes of d
+    rows_d = d.shape[b.ndim - 1]
+    assert rows_d == n
+    def col(t, i):
+        return t[..., i]
+    def rhs(t, i):
+        return t[(Ellipsis, i) + (slice(None),) * extra] if extra else t[..., i]
+    def bc(v):  # broadcast a per-row coefficient over the RHS axes
+        return v.reshape(v.shape + (1,) * extra) if extra else v
+    cp = np.empty(b.shape, dtype=dtype)
+    dp = np.empty(d.shape, dtype=dtype)
+    cp[..., 0] = col(c, 0) / col(b, 0) if n > 1 else 0.0
+    if extra:
+        dp[(Ellipsis, 0) + (slice(None),) * extra] = rhs(d, 0) / bc(col(b, 0))
+    else:
+        dp[..., 0] = d[..., 0] / b[..., 0]
+    for i in range(1, n):
+        w = col(b, i) - col(a, i) * cp[..., i - 1]
+        cp[..., i] = (col(c, i) / w) if i < n - 1 else 0.0
+        if extra:
+            sl = (Ellipsis, i) + (slice(None),) * extra
+            slp = (Ellipsis, i - 1) + (slice(None),) * extra
+            dp[sl] = (d[sl] - bc(col(a, i)) * dp[slp]) / bc(w)
+        else:
+            dp[..., i] = (d[..., i] - a[..., i] * dp[..., i - 1]) / w
+    x = np.empty(d.shape, dtype=dtype)
+    if extra:
+        last = (Ellipsis, n - 1) + (slice(None),) * extra
+        x[last] = dp[last]
+        for i in range(n - 2, -1, -1):
+            sl = (Ellipsis, i) + (slice(None),) * extra
+            sln = (Ellipsis, i + 1) + (slice(None),) * extra
+            x[sl] = dp[sl] - bc(cp[..., i]) * x[sln]
+    else:
+        x[..., n - 1] = dp[..., n - 1]
+        for i in range(n - 2, -1, -1):
+            x[..., i] = dp[..., i] - cp[..., i] * x[..., i + 1]
+    return x
+
+
+def thomas_ext(a, b, c, d):
+    """The Thomas sweep of :func:`thomas` in numpy.longdouble; returns float64.
+
+    longdouble is the 80-bit x87 format on x86-64 and IEEE binary128 on AArch64; both carry
+    more than 53 significant bits, which is all this reference needs.
+    """
+    return thomas(a, b, c, d, dtype=np.longdouble).astype(np.float64)
+
+
+def dense_matrix(a, b, c):
+    """The dense n x n matrix of one line (a_0 and c_{n-1} dropped)."""
+    a, b, c = (np.asarray(t, dtype=np.float64) for t in (a, b, c))
+    n = b.shape[-1]
+    A = np.zeros(b.shape[:-1] + (n, n))
+    idx = np.arange(n)
+    A[..., idx, idx] = b
+    if n > 1:
+        A[..., idx[1:], idx[:-1]] = a[..., 1:]
+        A[..., idx[:-1], idx[1:]] = c[..., :-1]
+    return A
+
+
+def dense_solve(a, b, c, d):
+    """x = A^{-1} d by LAPACK LU with partial pivoting, line by line (brute-force pin)."""
+    A = dense_matrix(a, b, c)
+    d = np.asarray(d, dtype=np.float64)
+    return np.linalg.solve(A, d[..., None])[..., 0]
+
+
+def partition_rows(n: int, p: int):
+    """Contiguous partitions [start, end) of a line of n rows into p parts.
+
+    The first (n mod p) partitions hold ceil(n/p) rows, the rest floor(n/p). Raises if a
+    partition would hold fewer than 2 rows (the two-endpoint reduction needs m >= 2).
+    """
+    if p < 1:
+        raise ValueError("p must be >= 1")
+    q, r = divmod(n, p)
+    sizes = [q + 1] * r + [q] * (p - r)
+    if min(sizes) < 2 and not (p == 1 and n >= 1):
+        raise ValueError(f"partition of {n} rows into {p} parts leaves a part with < 2 rows")
+    bounds, s = [], 0
+    for m in sizes:
+        bounds.append((s, s + m))
+        s += m
+    return bounds
+
+
+def dc_spike(a, b, c, d, p: int):
+    """Divide-and-conquer solve in the paper's three computation stages (Section 2.1, Algorithm 1).
+
+    Stage A (decoupled solve, A~ x~ = d~): each partition k = [s, e] is solved on its own with
+    its outer couplings a_s and c_e removed, for the right-hand side d and for the two coupling
+    columns: v = A_k^{-1}(a_s e_first) (k > 0) and w = A_k^{-1}(c_e e_last) (k < p-1). Then
+    inside partition k, x_i = x~_i - v_i x_{s-1} - w_i x_{e+1}.
+    Stage B (reduced system Z y = E^T x~, size 2p - 2, Section 2.2): the interface unknowns
+    y = [x_{e_0}, x_{s_1}, x_{e_1}, ..., x_{e_{p-2}}, x_{s_{p-1}}] satisfy, for each interface
+    row i in {s_k (k > 0), e_k (k < p-1)}: x_i + v_i x_{e_{k-1}} + w_i x_{s_{k+1}} = x~_i.
+    Solved here by dense LU (numpy.linalg.solve).
+    Stage C (correction, x = x~ - Y y): apply the relation above to every row.
+    Works on (lines, n) arrays; returns x with the shape of d.
+    """
+    a, b, c, d = (np.atleast_2d(np.asarray(t, dtype=np.float64)) for t in (a, b, c, d))
+    squeeze = np.asarray(b).ndim == 1
+    L, n = b.shape
+    parts = partition_rows(n, p)
+    xt = np.zeros((L, n))
+    v = np.zeros((L, n))
+    w = np.zeros((L, n))
+    for k, (s, e) in enumerate(parts):  # Stage A
+        ak, bk, ck = a[:, s:e].copy(), b[:, s:e], c[:, s:e].copy()
+        ak[:, 0] = 0.0
+        ck[:, -1] = 0.0
+        xt[:, s:e] = thomas(ak, bk, ck, d[:, s:e])
+        if k > 0:
+            rhs = np.zeros((L, e - s))
+            rhs[:, 0] = a[:, s]
+            v[:, s:e] = thomas(ak, bk, ck, rhs)
+        if k < p - 1:
+            rhs = np.zeros((L, e - s))
+            rhs[:, -1] = c[:, e - 1]
+            w[:, s:e] = thomas(ak, bk, ck, rhs)
+    if p == 1:
+        x = xt
+    else:
+        # interface unknown j: 2k-1 -> x_{s_k} (k >= 1), 2k -> x_{e_k} (k <= p-2)
+        m = 2 * p - 2
+        iface_row = []
+        for k, (s, e) in enumerate(parts):
+            if k > 0:
+                iface_row.append((2 * k - 1, s, k))
+            if k < p - 1:
+                iface_row.append((2 * k, e - 1, k))
+        Z = np.zeros((L, m, m))
+        rhs = np.zeros((L, m))
+        for j, row, k in iface_row:  # Stage B assembly
+            Z[:, j, j] = 1.0
+            if k > 0:
+                Z[:, j, 2 * (k - 1)] += v[:, row]        # coefficient of x_{e_{k-1}}
+            if k < p - 1:
+                Z[:, j, 2 * (k + 1) - 1] += w[:, row]    # coefficient of x_{s_{k+1}}
+            rhs[:, j] = xt[:, row]
+        y = np.linalg.solve(Z, rhs[..., None])[..., 0]
+        x = xt.copy()
+        for k, (s, e) in enumerate(parts):  # Stage C
+            if k > 0:
+                x[:, s:e] -= v[:, s:e] * y[:, 2 * (k - 1)][:, None]
+            if k < p - 1:
+                x[:, s:e] -= w[:, s:e] * y[:, 2 * (k + 1) - 1][:, None]
+    return x[0] if squeeze else x
+
+
+def residual(a, b, c, d, x, dtype=np.float64):
+    """r = d - A x along the last axis (a_0 and c_{n-1} ignored)."""
+    a, b, c, d, x = (np.asarray(t, dtype=dtype) for t in (a, b, c, d, x))
+    ax = b * x
+    ax[..., 1:] += a[..., 1:] * x[..., :-1]
+    ax[..., :-1] += c[..., :-1] * x[..., 1:]
+    return d - ax
+
+
+def transpose_coefficients(a, b, c):
+    """Diagonals of A^T: sub'_i = c_{i-1}, diag'_i = b_i, super'_i = a_{i+1} (ends zero)."""
+    a, b, c = (np.asarray(t, dtype=np.float64) for t in (a, b, c))
+    at = np.zeros_like(a)
+    ct = np.zeros_like(c)
+    at[..., 1:] = c[..., :-1]
+    ct[..., :-1] = a[..., 1:]
+    return at, b.copy(), ct
+
+
+def adjoint_grads(a, b, c, x, g):
+    """Gradients of L with dL/dx = g through x = A^{-1} d (standard adjoint: dL/dA = -lambda x^T).
+
+    lambda = A^{-T} g (Thomas on the transposed diagonals); grad_d = lambda;
+    grad_b = -lambda x; grad_a_i = -lambda_i x_{i-1} (0 at i = 0);
+    grad_c_i = -lambda_i x_{i+1} (0 at i = n-1).
+    """
+    at, bt, ct = transpose_coefficients(a, b, c)
+    lam = thomas(at, bt, ct, g)
+    x = np.asarray(x, dtype=np.float64)
+    ga = np.zeros_like(lam)
+    gc = np.zeros_like(lam)
+    ga[..., 1:] = -lam[..., 1:] * x[..., :-1]
+    gc[..., :-1] = -lam[..., :-1] * x[..., 1:]
+    return ga, -lam * x, gc, lam
+
+
+def thomas_ragged(a, b, c, d, offsets, lengths, lines=None, dtype=np.float64):
+    """Thomas over packed lines of uneven length; solves ``lines`` (default all) and returns
+    {line index: x}. Lines of equal length are solved together.
+    """
+    offsets = np.asarray(offsets, dtype=np.int64)
+    lengths = np.asarray(lengths, dtype=np.int64)
+    lines = np.arange(len(lengths)) if lines is None else np.asarray(lines)
+    out = {}
+    for n in np.unique(lengths[lines]):
+        sel = lines[lengths[lines] == n]
+        idx = offsets[sel][:, None] + np.arange(n)[None, :]
+        x = thomas(a[idx], b[idx], c[idx], d[idx], dtype=dtype)
+        for k, li in enumerate(sel):
+            out[int(li)] = x[k].astype(np.float64)
+    return out
+
+
+def rel_l2(x, ref):
+    """Relative L2 error ||x - ref|| / ||ref||."""
+    x = np.asarray(x, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    den = np.linalg.norm(ref.ravel())
+    return float(np.linalg.norm((x - ref).ravel()) / (den if den > 0 else 1.0))
