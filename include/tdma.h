@@ -1,0 +1,163 @@
+/*
+ * tdma.h -- C ABI of a batched divide-and-conquer tridiagonal solver for one GB300 (sm_103a).
+ *
+ * Problem (Algorithm 1: "Ax = d, N times; input a, b, c, d; output x"; Section 3.2.1: a, b
+ * and c are the sub-, main and super-diagonal of A). For every line l = 0..n_lines-1:
+ *
+ *     a_i x_{i-1} + b_i x_i + c_i x_{i+1} = d_i,      i = 0..n-1,
+ *
+ * with a_0 and c_{n-1} of every line ignored (treated as 0: no coupling outside the line).
+ * Lines run along one axis of a strided grid (Section 4.2.1 groups the systems of one
+ * direction of a 3D field into batches). Each line is split into P contiguous partitions
+ * (Section 2.1: Stage A decoupled solve, Stage B reduced solve, Stage C correction; Section
+ * 2.2: the reduced system grows with P); on one GPU the partitions are threads and the
+ * paper's A2B/B2C exchanges become on-chip data movement.
+ *
+ * Memory and ownership
+ *   - Every array argument is a DEVICE pointer owned by the caller and must stay valid until
+ *     the work queued on `stream` has finished. The library never frees caller memory.
+ *   - `workspace` is caller-owned device scratch of at least the size reported by
+ *     tdma_plan_create (may be 0 bytes, then NULL is accepted).
+ *   - A plan owns host state plus one small device status block, allocated in
+ *     tdma_plan_create and freed in tdma_plan_destroy. tdma_solve and tdma_solve_backward
+ *     allocate nothing.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *
+ * Element layout
+ *   An "element" is one unknown of one line. Line l starts at element
+ *       off(l) = (l / inner_count) * outer_stride + (l % inner_count) * inner_stride
+ *   and its unknown i sits at element off(l) + i * elem_stride (strides in elements, may be
+ *   any non-negative values; lines must not overlap when x is written). d and x hold nrhs
+ *   consecutive values per element (nrhs = 2: interleaved real/imaginary parts of a complex
+ *   right-hand side sharing real coefficients). a, b, c hold one value per element, or, with
+ *   coef_broadcast = 1, are 1D arrays of length n shared by all lines.
+ *   Ragged batches (n = 0): line l has ragged_lengths[l] unknowns starting at element
+ *   ragged_offsets[l], unit stride (packed lines); both arrays are device pointers.
+ *
+ * Precision (`precision`)
+ *   TDMA_F64         a, b, c, d, x, diag_shift double; arithmetic double.
+ *   TDMA_F32         all float; arithmetic float.
+ *   TDMA_F32_REFINE  a, b, c float; d, x, diag_shift double. Sweeps in float, then
+ *                    iterative refinement with an extra-precise residual r = d - A x
+ *                    until the estimated error is below refine_tol (relative, per line).
+ *
+ * Errors
+ *   Every call validates its arguments synchronously and returns a status; nothing aborts.
+ *   Numerical faults found on the device (a zero or non-finite pivot, refinement that did
+ *   not converge, a bounded wait that ran out) are recorded in the plan's device status
+ *   block and read back by tdma_last_device_error.
+ */
+#ifndef TDMA_H_
+#define TDMA_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TDMA_OK = 0,
+  TDMA_ERR_INVALID_ARG = 1,   /* bad descriptor or pointer, detected on the host          */
+  TDMA_ERR_UNSUPPORTED = 2,   /* valid but not supported (e.g. misaligned vector access)  */
+  TDMA_ERR_WORKSPACE = 3,     /* workspace smaller than tdma_plan_create reported         */
+  TDMA_ERR_CUDA = 4,          /* a CUDA runtime call failed                               */
+  TDMA_ERR_NONFINITE = 5,     /* device: zero or non-finite pivot / result                */
+  TDMA_ERR_TIMEOUT = 6,       /* device: a bounded wait gave up                           */
+  TDMA_ERR_NOT_CONVERGED = 7  /* device: refinement hit max_refine_iters                  */
+} tdma_status_t;
+
+typedef enum { TDMA_F64 = 0, TDMA_F32 = 1, TDMA_F32_REFINE = 2 } tdma_precision_t;
+
+typedef struct tdma_plan_s* tdma_plan_t;
+
+typedef struct {
+  int64_t n;             /* unknowns per line (uniform lines, >= 1); 0 selects a ragged batch */
+  int64_t n_lines;       /* number of lines (>= 0)                                            */
+  int64_t elem_stride;   /* element stride between consecutive unknowns of a line             */
+  int64_t inner_count;   /* line addressing, see off(l) above (>= 1)                          */
+  int64_t inner_stride;
+  int64_t outer_stride;
+  const int64_t* ragged_offsets; /* device, n_lines entries (n == 0 only)                     */
+  const int32_t* ragged_lengths; /* device, n_lines entries, each >= 1 (n == 0 only)          */
+  int64_t ragged_max_n;  /* host-known upper bound of ragged_lengths (n == 0 only)            */
+  int64_t ragged_total;  /* host-known sum of ragged_lengths (n == 0 only)                    */
+  int32_t nrhs;          /* 1, or 2 (interleaved complex right-hand side)                     */
+  int32_t coef_broadcast;/* 0: per-element a, b, c; 1: 1D a, b, c of length n for all lines   */
+  const void* diag_shift;/* optional device array, one value per line, added to b (may be NULL)*/
+  tdma_precision_t precision;
+  int32_t partitions;    /* P partitions per line; 0 = choose automatically                   */
+  int32_t max_refine_iters; /* TDMA_F32_REFINE: correction steps at most (0 = default 4)     */
+  double refine_tol;     /* TDMA_F32_REFINE: target relative error per line (<= 0: 1e-13)   */
+} tdma_desc_t;
+
+/* Launch configuration a plan has settled on (reported for benchmarks and tests). */
+typedef struct {
+  int32_t partitions;      /* P                                                        */
+  int32_t rows_per_thread; /* ceil(n / P) for uniform lines                            */
+  int32_t lines_per_block; /* lines handled by one thread block                        */
+  int32_t threads_per_block;
+  int32_t variant;         /* kernel family, see TDMA_VARIANT_*                        */
+  int32_t blocks;          /* grid size of the main launch                             */
+  int64_t smem_bytes;      /* dynamic shared memory of the main launch                 */
+} tdma_config_t;
+
+enum {
+  TDMA_VARIANT_DC = 0,       /* fused Stage A/B/C, one block per group of lines          */
+  TDMA_VARIANT_THOMAS = 1,   /* P = 1 Thomas sweep, elimination factors in the workspace */
+  TDMA_VARIANT_REFINE = 2,   /* fused float sweeps with on-chip refinement               */
+  TDMA_VARIANT_RAGGED = 3    /* persistent launch over a device queue of ragged lines    */
+};
+
+/* Validate `desc`, choose a launch configuration and report the workspace it needs.
+ * Allocates the plan's host state and its small device status block (cudaMalloc on the
+ * current device). Returns TDMA_ERR_INVALID_ARG for a bad descriptor (n < 0, n_lines < 0,
+ * nrhs not 1 or 2, P larger than n/2 for P > 1, ragged fields missing, ...). */
+tdma_status_t tdma_plan_create(tdma_plan_t* plan, const tdma_desc_t* desc, size_t* workspace_bytes);
+
+/* Release a plan (synchronises its device status block first). NULL is accepted. */
+tdma_status_t tdma_plan_destroy(tdma_plan_t plan);
+
+/* Solve A x = d for every line (forward pass). x may alias d. Enqueues kernels on `stream`
+ * and returns without waiting; allocates nothing. */
+tdma_status_t tdma_solve(tdma_plan_t plan, const void* a, const void* b, const void* c,
+                         const void* d, void* x, void* workspace, size_t workspace_bytes,
+                         void* stream);
+
+/* Backward pass of x = A^{-1} d for a scalar loss with dL/dx = grad_x (adjoint method; the
+ * paper has no backward pass): solves A^T lambda = grad_x with the same divide-and-conquer
+ * kernels on the transposed diagonals, then writes
+ *   grad_d = lambda, grad_b_i = -lambda_i x_i, grad_a_i = -lambda_i x_{i-1} (0 at i = 0),
+ *   grad_c_i = -lambda_i x_{i+1} (0 at i = n-1).
+ * x is the forward solution. Any grad_* pointer may be NULL to skip that output. With
+ * coef_broadcast = 1 the coefficient gradients are summed over lines (length-n arrays).
+ * Types follow `precision` (F32_REFINE: grad_a/b/c float, grad_d double). */
+tdma_status_t tdma_solve_backward(tdma_plan_t plan, const void* a, const void* b, const void* c,
+                                  const void* x, const void* grad_x, void* grad_a, void* grad_b,
+                                  void* grad_c, void* grad_d, void* workspace,
+                                  size_t workspace_bytes, void* stream);
+
+/* Time the candidate launch configurations on the caller's data (runs tdma_solve several
+ * times, overwriting x) and keep the fastest in the plan. Synchronises `stream`. The choice
+ * is cached per process by problem shape; the workspace must be sized for the largest
+ * candidate, which tdma_plan_create already reports when partitions == 0. */
+tdma_status_t tdma_plan_autotune(tdma_plan_t plan, const void* a, const void* b, const void* c,
+                                 const void* d, void* x, void* workspace, size_t workspace_bytes,
+                                 void* stream);
+
+/* Report the launch configuration in use. */
+tdma_status_t tdma_plan_get_config(tdma_plan_t plan, tdma_config_t* config);
+
+/* Synchronise `stream`, read and clear the plan's device status block. Returns TDMA_OK or
+ * the first device-side error recorded since the last call. If `info` is not NULL it
+ * receives the largest number of refinement corrections any line used. */
+tdma_status_t tdma_last_device_error(tdma_plan_t plan, void* stream, int32_t* info);
+
+/* Static, human-readable name of a status code. */
+const char* tdma_status_string(tdma_status_t status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDMA_H_ */

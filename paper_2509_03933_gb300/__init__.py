@@ -1,0 +1,324 @@
+"""Batched divide-and-conquer tridiagonal solves on one GB300 (Pipelined-TDMA hot path).
+
+Thin ctypes binding over the C ABI in include/tdma.h (libtdma.so, built in-tree by
+``_build.build``): argument marshalling only, every step of a solve runs in the library's
+CUDA kernels. PyTorch provides device memory and streams. There is no CPU fallback: without
+the library or a CUDA device the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import torch
+
+from . import _build
+
+__all__ = ["Plan", "solve", "solve_backward", "TDMASolve", "line_layout", "TDMAError", "F64", "F32",
+           "F32_REFINE", "load_library", "declared_symbols", "sweep_graph"]
+
+F64, F32, F32_REFINE = 0, 1, 2
+_PREC = {"f64": F64, "f32": F32, "f32r": F32_REFINE, F64: F64, F32: F32, F32_REFINE: F32_REFINE}
+STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported configuration", 3: "workspace too small",
+          4: "CUDA runtime error", 5: "zero or non-finite pivot", 6: "bounded wait timed out",
+          7: "refinement did not converge"}
+
+
+class TDMAError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {STATUS.get(status, status)} (status {status})")
+        self.status = status
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_lines", ctypes.c_int64), ("elem_stride", ctypes.c_int64),
+                ("inner_count", ctypes.c_int64), ("inner_stride", ctypes.c_int64),
+                ("outer_stride", ctypes.c_int64), ("ragged_offsets", ctypes.c_void_p),
+                ("ragged_lengths", ctypes.c_void_p), ("ragged_max_n", ctypes.c_int64),
+                ("ragged_total", ctypes.c_int64), ("nrhs", ctypes.c_int32), ("coef_broadcast", ctypes.c_int32),
+                ("diag_shift", ctypes.c_void_p), ("precision", ctypes.c_int32), ("partitions", ctypes.c_int32),
+                ("max_refine_iters", ctypes.c_int32), ("refine_tol", ctypes.c_double)]
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("partitions", ctypes.c_int32), ("rows_per_thread", ctypes.c_int32),
+                ("lines_per_block", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
+                ("variant", ctypes.c_int32), ("blocks", ctypes.c_int32), ("smem_bytes", ctypes.c_int64)]
+
+
+_LIB = None
+_VP = ctypes.c_void_p
+
+
+def load_library(build: bool = True) -> ctypes.CDLL:
+    """Load libtdma.so (building it first if it is missing or stale)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    path = _build.build() if build else _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"libtdma.so not found at {path}; run paper_2509_03933_gb300._build.build()")
+    lib = ctypes.CDLL(path)
+    st = ctypes.c_int
+    lib.tdma_plan_create.argtypes = [ctypes.POINTER(_VP), ctypes.POINTER(Desc), ctypes.POINTER(ctypes.c_size_t)]
+    lib.tdma_plan_create.restype = st
+    lib.tdma_plan_destroy.argtypes = [_VP]
+    lib.tdma_plan_destroy.restype = st
+    lib.tdma_solve.argtypes = [_VP] + [_VP] * 6 + [ctypes.c_size_t, _VP]
+    lib.tdma_solve.restype = st
+    lib.tdma_solve_backward.argtypes = [_VP] + [_VP] * 10 + [ctypes.c_size_t, _VP]
+    lib.tdma_solve_backward.restype = st
+    lib.tdma_plan_autotune.argtypes = [_VP] + [_VP] * 6 + [ctypes.c_size_t, _VP]
+    lib.tdma_plan_autotune.restype = st
+    lib.tdma_plan_get_config.argtypes = [_VP, ctypes.POINTER(Config)]
+    lib.tdma_plan_get_config.restype = st
+    lib.tdma_last_device_error.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_int32)]
+    lib.tdma_last_device_error.restype = st
+    lib.tdma_status_string.argtypes = [ctypes.c_int]
+    lib.tdma_status_string.restype = ctypes.c_char_p
+    _LIB = lib
+    return lib
+
+
+def declared_symbols() -> list:
+    """Function names declared in include/*.h."""
+    names = []
+    inc = _build.INCLUDE
+    for f in sorted(os.listdir(inc)):
+        if f.endswith(".h"):
+            txt = open(os.path.join(inc, f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names += re.findall(r"^\s*(?:const\s+)?\w+\**\s+\**(tdma_\w+)\s*\(", txt, flags=re.M)
+    return sorted(set(names))
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def line_layout(t: torch.Tensor, axis: int, nrhs: int = 1):
+    """(n, n_lines, elem_stride, inner_count, inner_stride, outer_stride) of lines along ``axis``.
+
+    For nrhs = 2 the tensor carries a trailing axis of 2 interleaved values (re, im) per element.
+    """
+    shape, strides = list(t.shape), list(t.stride())
+    if nrhs == 2:
+        if shape[-1] != 2 or strides[-1] != 1:
+            raise ValueError("nrhs = 2 needs a trailing axis of 2 contiguous values")
+        shape, strides = shape[:-1], strides[:-1]
+        if any(s % 2 for s in strides):
+            raise ValueError("element strides must be whole (re, im) pairs")
+        strides = [s // 2 for s in strides]
+    nd = len(shape)
+    axis = axis % nd
+    n, es = shape[axis], strides[axis]
+    dims = [(shape[i], strides[i]) for i in range(nd) if i != axis and shape[i] != 1]
+    merged = []
+    for sz, st in dims:  # merge dims that are contiguous with the previous one
+        if merged and merged[-1][1] == st * sz:
+            psz, _ = merged[-1]
+            merged[-1] = (psz * sz, st)
+        else:
+            merged.append((sz, st))
+    if len(merged) == 0:
+        return n, 1, es, 1, 0, 0
+    if len(merged) == 1:
+        return n, merged[0][0], es, merged[0][0], merged[0][1], 0
+    if len(merged) == 2:
+        (so, sto), (si, sti) = merged
+        return n, so * si, es, si, sti, sto
+    raise ValueError("lines must be addressable with at most two line axes")
+
+
+class Plan:
+    """A solve plan for one layout (wraps tdma_plan_t)."""
+
+    def __init__(self, n, n_lines, elem_stride=1, inner_count=None, inner_stride=None, outer_stride=0,
+                 precision="f64", partitions=0, nrhs=1, coef_broadcast=False, diag_shift=None,
+                 ragged_offsets=None, ragged_lengths=None, ragged_max_n=0, ragged_total=0,
+                 max_refine_iters=0, refine_tol=0.0):
+        self._lib = load_library()
+        if inner_count is None:
+            inner_count = max(1, n_lines)
+        if inner_stride is None:
+            inner_stride = n
+        self._keep = (diag_shift, ragged_offsets, ragged_lengths)
+        self.desc = Desc(n=n, n_lines=n_lines, elem_stride=elem_stride, inner_count=inner_count,
+                         inner_stride=inner_stride, outer_stride=outer_stride,
+                         ragged_offsets=_ptr(ragged_offsets), ragged_lengths=_ptr(ragged_lengths),
+                         ragged_max_n=ragged_max_n, ragged_total=ragged_total, nrhs=nrhs,
+                         coef_broadcast=int(bool(coef_broadcast)), diag_shift=_ptr(diag_shift),
+                         precision=_PREC[precision], partitions=partitions,
+                         max_refine_iters=max_refine_iters, refine_tol=refine_tol)
+        self._h = ctypes.c_void_p()
+        ws = ctypes.c_size_t(0)
+        st = self._lib.tdma_plan_create(ctypes.byref(self._h), ctypes.byref(self.desc), ctypes.byref(ws))
+        if st != 0:
+            raise TDMAError(st, "tdma_plan_create")
+        self.workspace_bytes = ws.value
+        self._ws = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None) and self._h.value:
+                self._lib.tdma_plan_destroy(self._h)
+        except Exception:
+            pass
+
+    @property
+    def config(self) -> dict:
+        c = Config()
+        self._lib.tdma_plan_get_config(self._h, ctypes.byref(c))
+        return {f: getattr(c, f) for f, _ in Config._fields_}
+
+    def workspace(self, device) -> torch.Tensor:
+        if self._ws is None or self._ws.numel() < self.workspace_bytes:
+            self._ws = torch.empty(max(1, self.workspace_bytes), dtype=torch.uint8, device=device)
+        return self._ws
+
+    def solve(self, a, b, c, d, x, workspace=None, stream=None):
+        ws = workspace if workspace is not None else (self.workspace(d.device) if self.workspace_bytes else None)
+        st = self._lib.tdma_solve(self._h, _ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(x), _ptr(ws),
+                                  ctypes.c_size_t(ws.numel() if ws is not None else 0), _stream(stream))
+        if st != 0:
+            raise TDMAError(st, "tdma_solve")
+        return x
+
+    def backward(self, a, b, c, x, grad_x, grad_a=None, grad_b=None, grad_c=None, grad_d=None,
+                 workspace=None, stream=None):
+        ws = workspace if workspace is not None else (self.workspace(x.device) if self.workspace_bytes else None)
+        st = self._lib.tdma_solve_backward(self._h, _ptr(a), _ptr(b), _ptr(c), _ptr(x), _ptr(grad_x),
+                                           _ptr(grad_a), _ptr(grad_b), _ptr(grad_c), _ptr(grad_d), _ptr(ws),
+                                           ctypes.c_size_t(ws.numel() if ws is not None else 0), _stream(stream))
+        if st != 0:
+            raise TDMAError(st, "tdma_solve_backward")
+
+    def autotune(self, a, b, c, d, x, workspace=None, stream=None):
+        ws = workspace if workspace is not None else (self.workspace(d.device) if self.workspace_bytes else None)
+        st = self._lib.tdma_plan_autotune(self._h, _ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(x), _ptr(ws),
+                                          ctypes.c_size_t(ws.numel() if ws is not None else 0), _stream(stream))
+        if st != 0:
+            raise TDMAError(st, "tdma_plan_autotune")
+        self.workspace_bytes = max(self.workspace_bytes, 0)
+        return self.config
+
+    def last_error(self, stream=None):
+        """(status, max refinement corrections used); synchronises the stream."""
+        info = ctypes.c_int32(0)
+        st = self._lib.tdma_last_device_error(self._h, _stream(stream), ctypes.byref(info))
+        return st, info.value
+
+
+def _check_same_layout(ref, *ts):
+    for t in ts:
+        if t is not None and (t.shape != ref.shape or t.stride() != ref.stride()):
+            return False
+    return True
+
+
+_PLAN_CACHE = {}
+
+
+def _plan_for(d, axis, precision, partitions, nrhs, coef_broadcast, diag_shift, max_refine_iters, refine_tol):
+    lay = line_layout(d, axis, nrhs)
+    key = (lay, precision, partitions, nrhs, coef_broadcast,
+           None if diag_shift is None else diag_shift.data_ptr(), max_refine_iters, refine_tol, d.device)
+    p = _PLAN_CACHE.get(key)
+    if p is None:
+        n, nl, es, ic, isd, osd = lay
+        p = Plan(n, nl, es, ic, isd, osd, precision=precision, partitions=partitions, nrhs=nrhs,
+                 coef_broadcast=coef_broadcast, diag_shift=diag_shift, max_refine_iters=max_refine_iters,
+                 refine_tol=refine_tol)
+        _PLAN_CACHE[key] = p
+    return p
+
+
+def solve(a, b, c, d, axis=-1, precision="f64", partitions=0, out=None, nrhs=1, coef_broadcast=False,
+          diag_shift=None, max_refine_iters=0, refine_tol=0.0, check=False):
+    """Solve a_i x_{i-1} + b_i x_i + c_i x_{i+1} = d_i along ``axis`` of every line of ``d``.
+
+    a, b, c have d's layout (or are 1D of length n with ``coef_broadcast``); ``out`` may be d.
+    ``check`` synchronises and raises on device-side numerical errors.
+    """
+    if not d.is_cuda:
+        raise RuntimeError("tdma.solve needs CUDA tensors (no CPU fallback)")
+    if not coef_broadcast and not _check_same_layout(d if nrhs == 1 else d[..., 0], a, b, c):
+        a, b, c = (t.contiguous() for t in (a, b, c))
+        d = d.contiguous()
+    if out is None:
+        x = torch.empty_like(d)
+        if not _check_same_layout(d, x):  # d is a view with gaps: solve a dense copy
+            d = d.contiguous()
+            if not coef_broadcast:
+                a, b, c = (t.contiguous() for t in (a, b, c))
+            x = torch.empty_like(d)
+    else:
+        x = out
+        if not _check_same_layout(d, x):
+            raise ValueError("out must have d's layout")
+    p = _plan_for(d, axis, precision, partitions, nrhs, coef_broadcast, diag_shift, max_refine_iters, refine_tol)
+    p.solve(a, b, c, d, x)
+    if check:
+        st, _ = p.last_error()
+        if st != 0:
+            raise TDMAError(st, "device")
+    return x
+
+
+def solve_backward(a, b, c, x, grad_x, axis=-1, precision="f64", partitions=0, nrhs=1, coef_broadcast=False,
+                   diag_shift=None, need=(True, True, True, True)):
+    """Gradients (grad_a, grad_b, grad_c, grad_d) of a loss with dL/dx = grad_x through x = A^{-1} d."""
+    p = _plan_for(x, axis, precision, partitions, nrhs, coef_broadcast, diag_shift, 0, 0.0)
+    if coef_broadcast:
+        ga, gb, gc = (torch.zeros_like(t) if f else None for t, f in zip((a, b, c), need[:3]))
+    else:
+        ga, gb, gc = (torch.empty_like(t) if f else None for t, f in zip((a, b, c), need[:3]))
+    gd = torch.empty_like(x) if need[3] else None
+    p.backward(a, b, c, x, grad_x.contiguous() if grad_x.stride() != x.stride() else grad_x, ga, gb, gc, gd)
+    return ga, gb, gc, gd
+
+
+class TDMASolve(torch.autograd.Function):
+    """x = A^{-1} d along ``axis`` with a hand-written adjoint (tdma_solve_backward)."""
+
+    @staticmethod
+    def forward(ctx, a, b, c, d, axis=-1, precision="f64", partitions=0):
+        x = solve(a, b, c, d, axis=axis, precision=precision, partitions=partitions)
+        ctx.save_for_backward(a, b, c, x)
+        ctx.cfg = (axis, precision, partitions)
+        return x
+
+    @staticmethod
+    def backward(ctx, grad_x):
+        a, b, c, x = ctx.saved_tensors
+        axis, precision, partitions = ctx.cfg
+        need = ctx.needs_input_grad[:4]
+        ga, gb, gc, gd = solve_backward(a, b, c, x, grad_x, axis=axis, precision=precision,
+                                        partitions=partitions, need=tuple(bool(v) for v in need))
+        return ga, gb, gc, gd, None, None, None
+
+
+def sweep_graph(plans_and_args, stream=None):
+    """Capture a sequence of solves (e.g. the x, y, z sweeps of an ADI step) in one CUDA graph.
+
+    ``plans_and_args`` is a list of (Plan, (a, b, c, d, x)) run in order on one stream; the
+    returned torch.cuda.CUDAGraph replays them with a single launch.
+    """
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream() if stream is None else stream
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        for p, args in plans_and_args:  # warm-up outside capture
+            p.solve(*args, stream=s)
+    torch.cuda.current_stream().wait_stream(s)
+    with torch.cuda.graph(g, stream=s):
+        for p, args in plans_and_args:
+            p.solve(*args, stream=s)
+    return g

@@ -1,0 +1,241 @@
+// Fused divide-and-conquer solve of uniform lines: Stage A, Stage B and Stage C in one block.
+//
+// Section 2.1 splits each system into p partitions: Stage A solves the decoupled partitions,
+// Stage B the reduced interface system (size 2p - 2, Section 2.2), Stage C corrects every
+// unknown (about 4 L / p flops). On one GPU a partition is one thread: thread (j, k) of a
+// block owns partition k of line j, adjacent threads own adjacent lines, so on strided axes
+// a warp's loads of one row are contiguous. The paper's A2B/B2C messages become shared
+// memory traffic inside the block.
+//
+// Stage A here is the modified Thomas sweep (each partition reduced to relations between
+// its two endpoint unknowns and the neighbouring partitions' endpoints):
+//   row 0:           a_0 x_{-1} + b_0 x_0 + c_0 x_1 = d_0             (kept in registers)
+//   rows t = 1..m-1: alpha_t x_0 + x_t + gamma_t x_{t+1} = delta_t, with
+//     r = 1 / (b_t - a_t gamma_{t-1}), alpha_t = -r a_t alpha_{t-1}, gamma_t = r c_t,
+//     delta_t = r (d_t - a_t delta_{t-1}), starting from (alpha, gamma, delta) = (-1, 0, 0).
+//   Row m-1 is then a reduced row. Row 1 expressed through x_0 and x_{m-1} is accumulated
+//   in the same forward pass (x_1 = F - G x_0 + Q x_{m-1}, F = sum Q_t delta_t,
+//   G = sum Q_t alpha_t, Q_{t+1} = -Q_t gamma_t over t = 1..m-2), so row 0 becomes the
+//   other reduced row without a backward elimination pass:
+//     rho = 1 / (b_0 - c_0 G): rho a_0 x_{-1} + x_0 + rho c_0 Q x_{m-1} = rho (d_0 - c_0 F).
+// Stage B solves the 2P-row unit-diagonal tridiagonal system of every line by Thomas, one
+// thread per line. Stage C walks back: x_t = delta_t - alpha_t x_0 - gamma_t x_{t+1}.
+#pragma once
+#include "layout.cuh"
+
+namespace tdma {
+
+template <class CT, int NR> struct Row {
+  CT a, b, c;
+  CT d[NR];
+};
+
+template <class CT, int NR>
+TDMA_DEV void load_row(Row<CT, NR>& r, const Args& A, int64_t e, int64_t i, CT shift) {
+  const int64_t ci = A.bcast ? i : e;
+  r.a = ldg((const CT*)A.a + ci);
+  r.b = ldg((const CT*)A.b + ci) + shift;
+  r.c = ldg((const CT*)A.c + ci);
+  if constexpr (NR == 1) {
+    r.d[0] = ldg((const CT*)A.d + e);
+  } else if constexpr (sizeof(CT) == 8) {
+    const double2 v = ldg((const double2*)A.d + e);
+    r.d[0] = v.x;
+    r.d[1] = v.y;
+  } else {
+    const float2 v = ldg((const float2*)A.d + e);
+    r.d[0] = v.x;
+    r.d[1] = v.y;
+  }
+}
+
+template <class CT, int NR> TDMA_DEV void store_x(const Args& A, int64_t e, const CT* v) {
+  if constexpr (NR == 1) {
+    ((CT*)A.x)[e] = v[0];
+  } else if constexpr (sizeof(CT) == 8) {
+    ((double2*)A.x)[e] = make_double2(v[0], v[1]);
+  } else {
+    ((float2*)A.x)[e] = make_float2(v[0], v[1]);
+  }
+}
+
+// In-place Thomas on a unit-diagonal tridiagonal system of `rows` rows held in shared memory.
+// On return rhs[r][*] holds the solution. Returns false on a non-finite result.
+template <class AT, int NR>
+TDMA_DEV bool reduced_solve(AT* sub, AT* sup, AT* rhs, int rows, int rhs_pitch) {
+  AT cp = sup[0];
+  AT dp[NR];
+#pragma unroll
+  for (int r = 0; r < NR; ++r) dp[r] = rhs[r * rhs_pitch];
+  for (int i = 1; i < rows; ++i) {
+    const AT s = sub[i];
+    const AT iw = rcp(AT(1) - s * cp);
+    cp = sup[i] * iw;
+    sup[i] = cp;
+#pragma unroll
+    for (int r = 0; r < NR; ++r) {
+      dp[r] = (rhs[r * rhs_pitch + i] - s * dp[r]) * iw;
+      rhs[r * rhs_pitch + i] = dp[r];
+    }
+  }
+  bool ok = true;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    AT u = dp[r];
+    ok &= finite(u);
+    for (int i = rows - 2; i >= 0; --i) {
+      u = rhs[r * rhs_pitch + i] - sup[i] * u;
+      rhs[r * rhs_pitch + i] = u;
+    }
+    ok &= finite(u);
+  }
+  return ok;
+}
+
+// Shared-memory plan of the fused kernel (all in units of CT):
+//   scratch  alpha, gamma, delta[NR]: (mmax - 2) slots x T threads each, slot-major
+//   reduced  per line: sub[2P], sup[2P], rhs[NR][2P], line pitch (2 + NR) 2P + 1
+template <class CT, int NR>
+__host__ __device__ inline size_t dc_smem_bytes(int T, int Lb, int P, int mmax) {
+  const size_t slots = mmax > 2 ? (size_t)(mmax - 2) : 0;
+  const size_t pitch = (size_t)(2 + NR) * 2 * P + 1;
+  return sizeof(CT) * ((2 + NR) * slots * T + (size_t)Lb * pitch);
+}
+
+constexpr int kChunk = 4;  // rows loaded ahead of the forward sweep
+
+template <class CT, int NR>
+__global__ void __launch_bounds__(512) dc_kernel(const Args A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  CT* sm = reinterpret_cast<CT*>(smem_raw);
+  const int T = blockDim.x, tid = threadIdx.x;
+  const int P = A.P, Lb = A.Lb;
+  const int j = tid % Lb, k = tid / Lb;
+  const int64_t line = (int64_t)blockIdx.x * Lb + j;
+  const bool active = line < A.lay.n_lines;
+  const int slots = A.mmax > 2 ? A.mmax - 2 : 0;
+  CT* s_alpha = sm;
+  CT* s_gamma = s_alpha + (size_t)slots * T;
+  CT* s_delta = s_gamma + (size_t)slots * T;  // NR blocks
+  CT* red = s_delta + (size_t)NR * slots * T;
+  const int R2 = 2 * P;
+  const int pitch = (2 + NR) * R2 + 1;
+  CT* r_sub = red + (size_t)j * pitch;
+  CT* r_sup = r_sub + R2;
+  CT* r_rhs = r_sup + R2;
+
+  int64_t start = 0;
+  int m = 0;
+  partition(A.lay.n, P, k, start, m);
+  const int64_t base = active ? A.lay.off(line) : 0;
+  const int64_t es = A.lay.es;
+  const CT shift = (active && A.shift) ? ldg((const CT*)A.shift + line) : CT(0);
+
+  // ---------------- Stage A: forward modified-Thomas sweep
+  if (active) {
+    Row<CT, NR> r0;
+    load_row<CT, NR>(r0, A, base + start * es, start, shift);
+    if (k == 0) r0.a = CT(0);                      // a_0 of the line is ignored
+    if (m == 1) {                                  // n == 1: a single equation b x = d
+      CT v[NR];
+      const CT ib = rcp(r0.b);
+#pragma unroll
+      for (int q = 0; q < NR; ++q) v[q] = r0.d[q] * ib;
+      bool ok = true;
+#pragma unroll
+      for (int q = 0; q < NR; ++q) ok &= finite(v[q]);
+      if (!ok) report_error(A.st, 5);
+      store_x<CT, NR>(A, base + start * es, v);
+    } else {
+      CT alpha = CT(-1), gamma = CT(0), delta[NR];
+      CT Q = CT(1), G = CT(0), F[NR];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) { delta[q] = CT(0); F[q] = CT(0); }
+
+      Row<CT, NR> buf[kChunk];
+#pragma unroll
+      for (int u = 0; u < kChunk; ++u)
+        if (1 + u < m) load_row<CT, NR>(buf[u], A, base + (start + 1 + u) * es, start + 1 + u, shift);
+      for (int t0 = 1; t0 < m; t0 += kChunk) {
+        Row<CT, NR> nxt[kChunk];
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) {
+          const int t = t0 + kChunk + u;
+          if (t < m) load_row<CT, NR>(nxt[u], A, base + (start + t) * es, start + t, shift);
+        }
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) {
+          const int t = t0 + u;
+          if (t < m) {
+            Row<CT, NR>& rw = buf[u];
+            if (k == P - 1 && t == m - 1) rw.c = CT(0);  // c_{n-1} of the line is ignored
+            const CT r = rcp(rw.b - rw.a * gamma);
+            const CT ar = rw.a * r;
+            alpha = -ar * alpha;
+            gamma = rw.c * r;
+#pragma unroll
+            for (int q = 0; q < NR; ++q) delta[q] = r * rw.d[q] - ar * delta[q];
+            if (t <= m - 2) {
+              const size_t o = (size_t)(t - 1) * T + tid;
+              s_alpha[o] = alpha;
+              s_gamma[o] = gamma;
+#pragma unroll
+              for (int q = 0; q < NR; ++q) {
+                s_delta[(size_t)q * slots * T + o] = delta[q];
+                F[q] += Q * delta[q];
+              }
+              G += Q * alpha;
+              Q = -Q * gamma;
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kChunk; ++u) buf[u] = nxt[u];
+      }
+      // reduced rows 2k (row 0 after the fix) and 2k+1 (row m-1)
+      const CT rho = rcp(r0.b - r0.c * G);
+      r_sub[2 * k] = rho * r0.a;
+      r_sup[2 * k] = rho * r0.c * Q;
+      r_sub[2 * k + 1] = alpha;
+      r_sup[2 * k + 1] = gamma;
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        r_rhs[q * R2 + 2 * k] = rho * (r0.d[q] - r0.c * F[q]);
+        r_rhs[q * R2 + 2 * k + 1] = delta[q];
+      }
+    }
+  }
+  if (A.lay.n == 1) return;  // no Stage B / C for single-unknown lines
+  __syncthreads();
+
+  // ---------------- Stage B: reduced 2P-row system per line, one thread per line
+  if (tid < Lb) {
+    const int64_t l2 = (int64_t)blockIdx.x * Lb + tid;
+    if (l2 < A.lay.n_lines) {
+      CT* sub = red + (size_t)tid * pitch;
+      if (!reduced_solve<CT, NR>(sub, sub + R2, sub + 2 * R2, R2, R2)) report_error(A.st, 5);
+    }
+  }
+  __syncthreads();
+
+  // ---------------- Stage C: endpoint values from Stage B, interior by back substitution
+  if (active) {
+    CT x0[NR], xn[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      x0[q] = r_rhs[q * R2 + 2 * k];
+      xn[q] = r_rhs[q * R2 + 2 * k + 1];
+    }
+    store_x<CT, NR>(A, base + start * es, x0);
+    store_x<CT, NR>(A, base + (start + m - 1) * es, xn);
+    for (int t = m - 2; t >= 1; --t) {
+      const size_t o = (size_t)(t - 1) * T + tid;
+      const CT al = s_alpha[o], ga = s_gamma[o];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) xn[q] = s_delta[(size_t)q * slots * T + o] - al * x0[q] - ga * xn[q];
+      store_x<CT, NR>(A, base + (start + t) * es, xn);
+    }
+  }
+}
+
+}  // namespace tdma

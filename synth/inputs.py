@@ -107,20 +107,46 @@ def apply_tridiag(a: torch.Tensor, b: torch.Tensor, c: torch.Tensor, x: torch.Te
     return d
 
 
+def _global_index(shape, full_shape, origin):
+    """Map flat indices of a sub-block ``shape`` at ``origin`` to flat indices of ``full_shape``."""
+    if full_shape is None:
+        return lambda i: i
+    full_shape = tuple(int(s) for s in full_shape)
+    strides_full = [1] * len(full_shape)
+    for k in range(len(full_shape) - 2, -1, -1):
+        strides_full[k] = strides_full[k + 1] * full_shape[k + 1]
+    def g(i):
+        out = torch.zeros_like(i)
+        rem = i
+        for k in range(len(shape) - 1, -1, -1):
+            q = rem % shape[k]
+            rem = rem // shape[k]
+            out += (q + origin[k]) * strides_full[k]
+        return out
+    return g
+
+
 def grid_general(shape, axis: int, seed: int, device="cpu", fp32_coefficients: bool = False,
-                 with_solution: bool = True):
+                 with_solution: bool = True, full_shape=None, origin=None):
     """General diagonally dominant problem (the distribution of the 64^3 and 1024^3 workloads).
 
     a, c ~ U(-1, 0); b = 2 + |a| + |c| + U(0, 1); x_true ~ U(-1, 1); d = A x_true along ``axis``.
     With ``fp32_coefficients`` the drawn a, b, c are rounded to float32 and those rounded values
     define the problem (returned both as float64 and float32); d is formed in float64 from them.
+    With ``full_shape``/``origin`` the block ``shape`` at ``origin`` of that larger grid is drawn
+    (identical values to the full draw; the block must span the whole solve axis).
     Returns a dict of tensors shaped like the grid.
     """
     shape = tuple(int(s) for s in shape)
+    if full_shape is not None:
+        origin = tuple(origin or (0,) * len(shape))
+        if shape[axis] != full_shape[axis] or origin[axis] != 0:
+            raise ValueError("a sampled block must span the whole solve axis")
+    gi = _global_index(shape, full_shape, origin)
     f64 = dict(dtype=torch.float64, device=device)
-    a = _fill(torch.empty(shape, **f64), lambda i: uniform(seed, AID["a"], i) - 1.0)
-    c = _fill(torch.empty(shape, **f64), lambda i: uniform(seed, AID["c"], i) - 1.0)
-    b = _fill(torch.empty(shape, **f64), lambda i: uniform(seed, AID["b"], i))
+    a = _fill(torch.empty(shape, **f64), lambda i: uniform(seed, AID["a"], gi(i)) - 1.0)
+    c = _fill(torch.empty(shape, **f64), lambda i: uniform(seed, AID["c"], gi(i)) - 1.0)
+    b = _fill(torch.empty(shape, **f64), lambda i: uniform(seed, AID["b"], gi(i)))
     b.add_(2.0).add_(a.abs()).add_(c.abs())  # 2 + |a| + |c| + U, evaluated as ((U + 2) + |a|) + |c|
     out = {}
     if fp32_coefficients:
@@ -129,7 +155,7 @@ def grid_general(shape, axis: int, seed: int, device="cpu", fp32_coefficients: b
         a, b, c = a32.double(), b32.double(), c32.double()
     out.update(a=a, b=b, c=c)
     if with_solution:
-        x = _fill(torch.empty(shape, **f64), lambda i: 2.0 * uniform(seed, AID["x_true"], i) - 1.0)
+        x = _fill(torch.empty(shape, **f64), lambda i: 2.0 * uniform(seed, AID["x_true"], gi(i)) - 1.0)
         out["x_true"] = x
         out["d"] = apply_tridiag(a, b, c, x, axis)
     return out

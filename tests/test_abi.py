@@ -1,0 +1,64 @@
+"""The C-ABI library builds, loads and exports every symbol include/tdma.h declares, and its
+host-side validation rejects bad descriptors (no GPU needed: validation runs before any CUDA call)."""
+import ctypes
+
+import pytest
+
+import paper_2509_03933_gb300 as tdma
+
+
+def test_library_exports_declared_symbols():
+    lib = tdma.load_library()
+    names = tdma.declared_symbols()
+    assert {"tdma_plan_create", "tdma_solve", "tdma_solve_backward", "tdma_plan_destroy",
+            "tdma_last_device_error", "tdma_status_string", "tdma_plan_autotune",
+            "tdma_plan_get_config"} <= set(names)
+    for n in names:
+        assert hasattr(lib, n), n
+
+
+def test_status_strings():
+    lib = tdma.load_library()
+    for code, text in tdma.STATUS.items():
+        assert lib.tdma_status_string(code).decode() == text
+    assert lib.tdma_status_string(99).decode() == "unknown status"
+
+
+def _create(**kw):
+    lib = tdma.load_library()
+    base = dict(n=64, n_lines=16, elem_stride=1, inner_count=16, inner_stride=64, outer_stride=0, nrhs=1,
+                precision=0, partitions=0)
+    base.update(kw)
+    d = tdma.Desc(**base)
+    h = ctypes.c_void_p()
+    ws = ctypes.c_size_t(0)
+    return lib.tdma_plan_create(ctypes.byref(h), ctypes.byref(d), ctypes.byref(ws))
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(n=-1), 1), (dict(n_lines=-5), 1), (dict(nrhs=3), 1), (dict(precision=7), 1),
+    (dict(partitions=-1), 1), (dict(partitions=40), 1),  # 64 / 40 < 2 rows per partition
+    (dict(inner_count=0), 1), (dict(elem_stride=-1), 1),
+    (dict(n=0, ragged_max_n=0), 1),                       # ragged without offsets/lengths
+    (dict(precision=2, nrhs=2), 2), (dict(precision=2, coef_broadcast=1), 2),
+])
+def test_invalid_descriptors_are_rejected_on_the_host(kw, code):
+    assert _create(**kw) == code
+
+
+def test_null_arguments():
+    lib = tdma.load_library()
+    assert lib.tdma_plan_create(None, None, None) == 1
+    assert lib.tdma_plan_destroy(None) == 0
+    assert lib.tdma_solve(None, None, None, None, None, None, None, 0, None) == 1
+    assert lib.tdma_last_device_error(None, None, None) == 1
+
+
+def test_line_layout_of_grid_axes():
+    import torch
+    g = torch.empty(4, 5, 6)
+    assert tdma.line_layout(g, 0) == (4, 30, 30, 30, 1, 0)       # z lines: merged (y, x)
+    assert tdma.line_layout(g, 1) == (5, 24, 6, 6, 1, 30)         # y lines
+    assert tdma.line_layout(g, 2) == (6, 20, 1, 20, 6, 0)         # x lines: merged (z, y)
+    c = torch.empty(4, 5, 6, 2)
+    assert tdma.line_layout(c, 0, nrhs=2) == (4, 30, 30, 30, 1, 0)

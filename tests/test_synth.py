@@ -55,3 +55,10 @@ def test_poisson_lines_shapes():
     assert p["d"].shape == (32, 8, 8, 2) and p["shift"].shape == (64,)
     assert p["shift"][0] == 0.0 and (p["shift"][1:] < 0).all()
     assert float(p["d"][0, 0, 0, 0]) == 0.0
+
+
+def test_sampled_block_equals_full_draw():
+    full = synth.grid_general((16, 12, 10), 0, 3, fp32_coefficients=True)
+    part = synth.grid_general((16, 4, 3), 0, 3, fp32_coefficients=True, full_shape=(16, 12, 10), origin=(0, 5, 6))
+    for k in ("a32", "b32", "c32", "d", "x_true"):
+        assert torch.equal(part[k], full[k][:, 5:9, 6:9])
