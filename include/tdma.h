@@ -89,7 +89,7 @@ typedef struct {
   tdma_precision_t precision;
   int32_t partitions;    /* P partitions per line; 0 = choose automatically                   */
   int32_t max_refine_iters; /* TDMA_F32_REFINE: correction steps at most (0 = default 4)     */
-  double refine_tol;     /* TDMA_F32_REFINE: target relative error per line (<= 0: 1e-13)   */
+  double refine_tol;     /* TDMA_F32_REFINE: target relative error per line (<= 0: 2.5e-13) */
 } tdma_desc_t;
 
 /* Launch configuration a plan has settled on (reported for benchmarks and tests). */
@@ -107,7 +107,10 @@ enum {
   TDMA_VARIANT_DC = 0,       /* fused Stage A/B/C, one block per group of lines          */
   TDMA_VARIANT_THOMAS = 1,   /* P = 1 Thomas sweep, elimination factors in the workspace */
   TDMA_VARIANT_REFINE = 2,   /* fused float sweeps with on-chip refinement               */
-  TDMA_VARIANT_RAGGED = 3    /* persistent launch over a device queue of ragged lines    */
+  TDMA_VARIANT_RAGGED = 3,   /* persistent launch over a device queue of ragged lines    */
+  TDMA_VARIANT_REFINE_REG = 4, /* refinement with per-row state in registers             */
+  TDMA_VARIANT_REFINE_TMA = 5, /* refinement on a TMA-staged shared-memory tile          */
+  TDMA_VARIANT_REFINE_CLUSTER = 6 /* refinement with each line spread over a CTA cluster  */
 };
 
 /* Validate `desc`, choose a launch configuration and report the workspace it needs.

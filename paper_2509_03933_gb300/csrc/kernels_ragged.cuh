@@ -9,5 +9,5 @@ inline cudaError_t launch_ragged(tdma_precision_t, const Args&, const tdma_confi
   return cudaErrorNotSupported;
 }
 inline cudaError_t prepare_ragged(tdma_precision_t, size_t) { return cudaSuccess; }
-inline size_t workspace_for(const tdma_desc_t&, const tdma_config_t&) { return 0; }
+inline size_t ragged_workspace(const tdma_desc_t&, const tdma_config_t&) { return 0; }
 }  // namespace tdma

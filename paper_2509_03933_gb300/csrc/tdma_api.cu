@@ -2,6 +2,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -11,6 +12,9 @@
 #include "tdma.h"
 #include "kernels_dc.cuh"
 #include "kernels_refine.cuh"
+#include "kernels_refine_reg.cuh"
+#include "kernels_refine_tma.cuh"
+#include "kernels_refine_cluster.cuh"
 #include "kernels_thomas.cuh"
 #include "kernels_ragged.cuh"
 #include "kernels_backward.cuh"
@@ -23,12 +27,15 @@ struct tdma_plan_s {
   DevStatus* status = nullptr;  // device
   int device = 0;
   bool refine_sb64 = true;
+  bool allow_tma = true;  // TDMA_DISABLE_TMA=1 loads tiles with ordinary loads instead (diagnostics)
   size_t workspace = 0;
 };
 
 namespace {
 
 constexpr int kMaxSmem = 227 * 1024;
+// Default refinement target: estimated error per line (max norm) 4x below 1e-12.
+constexpr double kDefaultRefineTol = 2.5e-13;
 
 bool is_uniform(const tdma_desc_t& d) { return d.n > 0; }
 
@@ -75,6 +82,42 @@ int default_partitions(const tdma_desc_t& d) {
   return std::max(1, P);
 }
 
+// Register-resident refinement kernel: rows per thread bucketed to M in {8, 16, 32}, block of
+// Lb lines x P partitions with Lb a power of two and Lb * P <= 256.
+bool refine_reg_config(const tdma_desc_t& d, int P_req, tdma_config_t& c) {
+  const int64_t n = d.n;
+  int P = P_req;
+  if (P <= 0) {
+    P = n <= 16 ? 1 : (int)((n + 15) / 16);
+    if (P > 256) P = (int)((n + 31) / 32);
+  }
+  if (P < 1 || P > 256) return false;
+  if (P > 1 && n / P < 2) return false;
+  const int64_t mmax = (n + P - 1) / P;
+  const int M = mmax <= 8 ? 8 : mmax <= 16 ? 16 : mmax <= 32 ? 32 : 0;
+  if (!M) return false;
+  int Lb = 1;
+  while (Lb * 2 * P <= 256 && Lb < 256 && Lb < d.n_lines) Lb *= 2;
+  const int T = Lb * P;
+  c.partitions = P;
+  c.rows_per_thread = M;
+  c.lines_per_block = Lb;
+  c.threads_per_block = T;
+  c.smem_bytes = (int64_t)refine_reg_smem_bytes<float>(T, Lb, P, M);
+  c.blocks = (int32_t)((d.n_lines + Lb - 1) / Lb);
+  c.variant = TDMA_VARIANT_REFINE_REG;
+  return c.smem_bytes <= kMaxSmem;
+}
+
+// Thomas (P = 1, factors in the workspace) fills the GPU when there are enough lines.
+bool prefer_thomas(const tdma_desc_t& d) { return d.n > 1 && d.n_lines >= 65536; }
+
+size_t workspace_for(const tdma_desc_t& d, const tdma_config_t& c) {
+  if (c.variant == TDMA_VARIANT_THOMAS) return thomas_workspace(d);
+  if (c.variant == TDMA_VARIANT_RAGGED) return ragged_workspace(d, c);
+  return 0;
+}
+
 tdma_status_t validate(const tdma_desc_t& d) {
   if (d.n < 0 || d.n_lines < 0) return TDMA_ERR_INVALID_ARG;
   if (d.nrhs != 1 && d.nrhs != 2) return TDMA_ERR_INVALID_ARG;
@@ -111,12 +154,130 @@ Args make_args(const tdma_plan_s* p, const void* a, const void* b, const void* c
   A.bcast = p->desc.coef_broadcast;
   A.st = p->status;
   A.max_iters = p->desc.max_refine_iters > 0 ? p->desc.max_refine_iters : 4;
-  A.tol = (float)(p->desc.refine_tol > 0 ? p->desc.refine_tol : 1e-13);
+  A.tol = (float)(p->desc.refine_tol > 0 ? p->desc.refine_tol : kDefaultRefineTol);
   A.roff = p->desc.ragged_offsets;
   A.rlen = p->desc.ragged_lengths;
   A.ws = ws;
   return A;
 }
+
+bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
+
+// ---- TMA tensor maps (cuTensorMapEncodeTiled through the runtime's driver entry point)
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(ptr);
+  });
+  return fn;
+}
+
+// Can the block tile {Lb lines, 1, P partitions, m rows} be described by a 4D tensor map?
+bool tma_layout_ok(const tdma_desc_t& d, const tdma_config_t& c) {
+  if (d.n <= 0 || d.inner_stride != 1 || d.n % c.partitions) return false;
+  const int64_t m = d.n / c.partitions;
+  if (m > 256 || c.partitions > 256 || c.lines_per_block > 256 || c.lines_per_block % 4) return false;
+  if (d.n_lines > d.inner_count && (d.inner_count % c.lines_per_block || d.n_lines % d.inner_count)) return false;
+  if ((d.elem_stride * 4) % 16 || (d.n_lines > d.inner_count && (d.outer_stride * 4) % 16)) return false;
+  if (d.inner_count >= (1ll << 32) || d.elem_stride * 8 >= (1ll << 40)) return false;
+  return true;
+}
+
+bool encode_map(CUtensorMap* map, const void* ptr, bool f64, const tdma_desc_t& d, const tdma_config_t& c,
+                int box_partitions = 0) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || !aligned(ptr, 16)) return false;
+  const cuuint64_t eb = f64 ? 8 : 4;
+  const int64_t m = d.n / c.partitions;
+  const int64_t outer = d.n_lines > d.inner_count ? d.n_lines / d.inner_count : 1;
+  const int64_t inner = d.n_lines > d.inner_count ? d.inner_count : std::max<int64_t>(1, d.n_lines);
+  cuuint64_t dims[4] = {(cuuint64_t)inner, (cuuint64_t)outer, (cuuint64_t)c.partitions, (cuuint64_t)m};
+  cuuint64_t os = outer > 1 ? (cuuint64_t)d.outer_stride * eb : ((cuuint64_t)inner * eb + 15) / 16 * 16;
+  cuuint64_t strides[3] = {os, (cuuint64_t)(m * d.elem_stride) * eb, (cuuint64_t)d.elem_stride * eb};
+  cuuint32_t box[4] = {(cuuint32_t)c.lines_per_block, 1,
+                       (cuuint32_t)(box_partitions > 0 ? box_partitions : c.partitions), (cuuint32_t)m};
+  cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = fn(map, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+                        const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+int reduced_groups(int P) {
+  int G = 1;
+  while (2 * G <= P && (2 * P) % (2 * G) == 0 && (2 * P) / (2 * G) >= 2 * (2 * G)) G *= 2;
+  return G;
+}
+
+// Is (M, P) one of the compiled fixed geometries (T = 256, n = P M exactly)?
+bool fixed_shape(int M, int P) {
+#define TDMA_SHAPE_EQ(MM, PP) if (M == MM && P == PP) return true;
+  TDMA_REFINE_FIXED_SHAPES(TDMA_SHAPE_EQ)
+#undef TDMA_SHAPE_EQ
+  return false;
+}
+bool fixed_ok(const tdma_desc_t& d, const tdma_config_t& c) {
+  return c.threads_per_block == 256 && d.n == (int64_t)c.partitions * c.rows_per_thread &&
+         fixed_shape(c.rows_per_thread, c.partitions);
+}
+
+// Cluster refinement: lines of n = C * PC * M rows, 32 lines per cluster, one TMA tile per CTA.
+bool cluster_shape(int64_t n, int& M, int& PC, int& C) {
+#define TDMA_CL_MATCH(MM, PP, CC) if (n == (int64_t)MM * PP * CC) { M = MM; PC = PP; C = CC; return true; }
+  TDMA_REFINE_CLUSTER_SHAPES(TDMA_CL_MATCH)
+#undef TDMA_CL_MATCH
+  return false;
+}
+size_t cluster_smem(int M, int PC, int C) {
+#define TDMA_CL_SMEM(MM, PP, CC) if (M == MM && PC == PP && C == CC) return refine_cluster_smem_bytes<MM, PP, CC>();
+  TDMA_REFINE_CLUSTER_SHAPES(TDMA_CL_SMEM)
+#undef TDMA_CL_SMEM
+  return 0;
+}
+bool refine_cluster_config(const tdma_desc_t& d, int P_req, tdma_config_t& c) {
+  int M, PC, C;
+  if (!cluster_shape(d.n, M, PC, C)) return false;
+  if (P_req > 0 && P_req != C * PC) return false;
+  tdma_config_t t{};
+  t.partitions = C * PC;
+  t.rows_per_thread = M;
+  t.lines_per_block = 256 / PC;
+  t.threads_per_block = 256;
+  t.blocks = (int32_t)(C * ((d.n_lines + t.lines_per_block - 1) / t.lines_per_block));
+  t.smem_bytes = (int64_t)cluster_smem(M, PC, C);
+  t.variant = TDMA_VARIANT_REFINE_CLUSTER;
+  if (!tma_layout_ok(d, t)) return false;
+  if (d.n_lines < t.lines_per_block) return false;  // a cluster needs a full line group
+  c = t;
+  return true;
+}
+
+// TMA-staged refinement: uniform partitions, tile fits shared memory.
+bool refine_tma_config(const tdma_desc_t& d, tdma_config_t& c) {
+  tdma_config_t t = c;
+  if (t.variant != TDMA_VARIANT_REFINE_REG) return false;
+  if (d.n % t.partitions) return false;
+  const int M = t.rows_per_thread;
+  const int G = fixed_ok(d, t) ? fixed_groups(t.partitions) : reduced_groups(t.partitions);
+  const size_t sm = refine_tma_smem_bytes(t.threads_per_block, t.lines_per_block, t.partitions, M, G);
+  if (sm > (size_t)kMaxSmem) return false;
+  t.smem_bytes = (int64_t)sm;
+  t.variant = TDMA_VARIANT_REFINE_TMA;
+  c = t;
+  return true;
+}
+
 
 template <class K> cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -141,6 +302,53 @@ cudaError_t launch_forward(const tdma_plan_s* p, const Args& A, cudaStream_t s) 
       if (p->refine_sb64) refine_kernel<double><<<grid, block, sm, s>>>(A);
       else refine_kernel<float><<<grid, block, sm, s>>>(A);
       break;
+    case TDMA_VARIANT_REFINE_REG:
+      switch (c.rows_per_thread) {
+        case 8: refine_reg_kernel<8, float, 2><<<grid, block, sm, s>>>(A); break;
+        case 16: refine_reg_kernel<16, float, 2><<<grid, block, sm, s>>>(A); break;
+        default: refine_reg_kernel<32, float, 1><<<grid, block, sm, s>>>(A); break;
+      }
+      break;
+    case TDMA_VARIANT_REFINE_TMA: {
+      TmaMaps maps;
+      std::memset(&maps, 0, sizeof(maps));
+      int use_tma = p->allow_tma && tma_layout_ok(p->desc, c) && encode_map(&maps.a, A.a, false, p->desc, c) &&
+                    encode_map(&maps.b, A.b, false, p->desc, c) && encode_map(&maps.c, A.c, false, p->desc, c) &&
+                    encode_map(&maps.d, A.d, true, p->desc, c) && encode_map(&maps.x, A.x, true, p->desc, c);
+      if (fixed_ok(p->desc, c)) {
+#define TDMA_LAUNCH_FIXED(MM, PP)                                                       \
+  if (c.rows_per_thread == MM && c.partitions == PP) {                                   \
+    refine_tma_fixed_kernel<MM, PP><<<grid, block, sm, s>>>(A, maps, use_tma);            \
+    return cudaGetLastError();                                                            \
+  }
+        TDMA_REFINE_FIXED_SHAPES(TDMA_LAUNCH_FIXED)
+#undef TDMA_LAUNCH_FIXED
+      }
+      const int G = reduced_groups(c.partitions);
+      switch (c.rows_per_thread) {
+        case 8: refine_tma_kernel<8, 2><<<grid, block, sm, s>>>(A, maps, G, use_tma); break;
+        case 16: refine_tma_kernel<16, 2><<<grid, block, sm, s>>>(A, maps, G, use_tma); break;
+        default: refine_tma_kernel<32, 1><<<grid, block, sm, s>>>(A, maps, G, use_tma); break;
+      }
+      break;
+    }
+    case TDMA_VARIANT_REFINE_CLUSTER: {
+      TmaMaps maps;
+      std::memset(&maps, 0, sizeof(maps));
+      const int PC = 256 / c.lines_per_block, C = c.partitions / PC;
+      const bool ok = encode_map(&maps.a, A.a, false, p->desc, c, PC) && encode_map(&maps.b, A.b, false, p->desc, c, PC) &&
+                      encode_map(&maps.c, A.c, false, p->desc, c, PC) && encode_map(&maps.d, A.d, true, p->desc, c, PC) &&
+                      encode_map(&maps.x, A.x, true, p->desc, c, PC);
+      if (!ok) return cudaErrorInvalidValue;
+#define TDMA_LAUNCH_CL(MM, PP, CC)                                                  \
+  if (c.rows_per_thread == MM && PC == PP && C == CC) {                              \
+    refine_cluster_kernel<MM, PP, CC><<<grid, block, sm, s>>>(A, maps);               \
+    return cudaGetLastError();                                                        \
+  }
+      TDMA_REFINE_CLUSTER_SHAPES(TDMA_LAUNCH_CL)
+#undef TDMA_LAUNCH_CL
+      return cudaErrorInvalidValue;
+    }
     case TDMA_VARIANT_THOMAS:
       return launch_thomas(p->desc.precision, p->desc.nrhs, A, c, s);
     case TDMA_VARIANT_RAGGED:
@@ -160,6 +368,32 @@ cudaError_t prepare_kernel(const tdma_plan_s* p) {
       return p->desc.nrhs == 1 ? set_smem(dc_kernel<float, 1>, sm) : set_smem(dc_kernel<float, 2>, sm);
     case TDMA_VARIANT_REFINE:
       return p->refine_sb64 ? set_smem(refine_kernel<double>, sm) : set_smem(refine_kernel<float>, sm);
+    case TDMA_VARIANT_REFINE_REG:
+      switch (p->cfg.rows_per_thread) {
+        case 8: return set_smem(refine_reg_kernel<8, float, 2>, sm);
+        case 16: return set_smem(refine_reg_kernel<16, float, 2>, sm);
+        default: return set_smem(refine_reg_kernel<32, float, 1>, sm);
+      }
+    case TDMA_VARIANT_REFINE_TMA:
+      if (fixed_ok(p->desc, p->cfg)) {
+#define TDMA_PREP_FIXED(MM, PP) \
+  if (p->cfg.rows_per_thread == MM && p->cfg.partitions == PP) return set_smem(refine_tma_fixed_kernel<MM, PP>, sm);
+        TDMA_REFINE_FIXED_SHAPES(TDMA_PREP_FIXED)
+#undef TDMA_PREP_FIXED
+      }
+      switch (p->cfg.rows_per_thread) {
+        case 8: return set_smem(refine_tma_kernel<8, 2>, sm);
+        case 16: return set_smem(refine_tma_kernel<16, 2>, sm);
+        default: return set_smem(refine_tma_kernel<32, 1>, sm);
+      }
+    case TDMA_VARIANT_REFINE_CLUSTER: {
+      const int PC = 256 / p->cfg.lines_per_block, C = p->cfg.partitions / PC;
+#define TDMA_PREP_CL(MM, PP, CC) \
+  if (p->cfg.rows_per_thread == MM && PC == PP && C == CC) return set_smem(refine_cluster_kernel<MM, PP, CC>, sm);
+      TDMA_REFINE_CLUSTER_SHAPES(TDMA_PREP_CL)
+#undef TDMA_PREP_CL
+      return cudaErrorInvalidValue;
+    }
     case TDMA_VARIANT_THOMAS:
       return prepare_thomas(p->desc.precision, p->desc.nrhs, sm);
     case TDMA_VARIANT_RAGGED:
@@ -167,8 +401,6 @@ cudaError_t prepare_kernel(const tdma_plan_s* p) {
   }
   return cudaSuccess;
 }
-
-bool aligned(const void* ptr, size_t a) { return ((uintptr_t)ptr % a) == 0; }
 
 }  // namespace
 
@@ -196,13 +428,26 @@ tdma_status_t tdma_plan_create(tdma_plan_t* plan, const tdma_desc_t* desc, size_
   tdma_plan_s* p = new (std::nothrow) tdma_plan_s();
   if (!p) return TDMA_ERR_INVALID_ARG;
   p->desc = *desc;
+  if (const char* e = std::getenv("TDMA_DISABLE_TMA")) p->allow_tma = !(e[0] == '1');
   if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return TDMA_ERR_CUDA; }
   tdma_config_t c{};
   if (is_uniform(*desc)) {
-    const int P = desc->partitions > 0 ? desc->partitions : default_partitions(*desc);
-    if (desc->precision != TDMA_F32_REFINE && desc->partitions == 1 && use_thomas_variant(*desc)) {
+    bool ok = false;
+    if (desc->precision == TDMA_F32_REFINE) {
+      ok = p->allow_tma && refine_cluster_config(*desc, desc->partitions, c);
+      if (!ok) {
+        ok = refine_reg_config(*desc, desc->partitions, c);
+        if (ok) refine_tma_config(*desc, c);
+      }
+      if (!ok) ok = choose_block(*desc, desc->partitions > 0 ? desc->partitions : default_partitions(*desc), c);
+    } else if (use_thomas_variant(*desc) &&
+               (desc->partitions == 1 || (desc->partitions == 0 && prefer_thomas(*desc)))) {
       thomas_config(*desc, c);
-    } else if (!choose_block(*desc, P, c)) {
+      ok = true;
+    } else {
+      ok = choose_block(*desc, desc->partitions > 0 ? desc->partitions : default_partitions(*desc), c);
+    }
+    if (!ok) {
       delete p;
       return TDMA_ERR_UNSUPPORTED;
     }

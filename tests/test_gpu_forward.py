@@ -146,3 +146,14 @@ def test_poisson_lines_broadcast_complex():
     ref = O.thomas_ext(a, b, c, dn)
     got = x.cpu().numpy().transpose(1, 0, 2)
     assert O.rel_l2(got, ref) <= 1e-12
+
+
+@pytest.mark.parametrize("n,lines", [(1024, 64), (512, 48), (256, 40), (64, 100), (1024, 37), (256, 6)])
+def test_refine_tile_kernels_z_lines(n, lines):
+    # lines along the strided axis of an [n][lines] grid: element stride = line count. Line
+    # counts divisible by 4 take the TMA-staged tile; others the plain-load fallback; 6 lines
+    # leave a partial last block.
+    x, ref = _grid_case((n, lines), 0, 17 + n, "f32r", 0)
+    assert O.rel_l2(x, ref) <= TOL["f32r"]
+    x, ref = _grid_case((n, lines), 0, 17 + n, "f32", 0)
+    assert O.rel_l2(x, ref) <= TOL["f32"]
