@@ -160,6 +160,24 @@ tdma_status_t tdma_last_device_error(tdma_plan_t plan, void* stream, int32_t* in
 /* Static, human-readable name of a status code. */
 const char* tdma_status_string(tdma_status_t status);
 
+/* Solve A x = d with the one-partition Thomas kernel without allocating anything (the paper has
+ * no counterpart; this serves callers that must not allocate device memory while they run, e.g.
+ * a solver loop that fixed its GPU memory at start-up, or a host program whose own memory pool
+ * owns the device heap). No plan and no workspace: the elimination factors go to a fixed
+ * 32 MiB array compiled into the library, present on every GPU that loads it until the
+ * process exits. Takes the same descriptor fields as tdma_plan_create for uniform lines
+ * (n >= 1; precision TDMA_F64 or TDMA_F32; nrhs, coef_broadcast and diag_shift as there;
+ * partitions 0 or 1) and the same device arrays as tdma_solve; enqueues on `stream`.
+ * Returns TDMA_ERR_WORKSPACE when n * n_lines factors (8 bytes each in FP64, 4 in FP32) exceed
+ * the array, TDMA_ERR_INVALID_ARG / TDMA_ERR_UNSUPPORTED as tdma_plan_create and tdma_solve do.
+ * Device-side numerical faults are not recorded (no status block): a zero pivot leaves
+ * non-finite values in x. The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture. All calls share the array: calls that could run at the same time on the GPU
+ * (other streams, other host threads) race on it and must not be issued. */
+tdma_status_t tdma_solve_thomas_static(const tdma_desc_t* desc, const void* a, const void* b,
+                                       const void* c, const void* d, void* x, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -77,6 +77,8 @@ def load_library(build: bool = True) -> ctypes.CDLL:
     lib.tdma_last_device_error.restype = st
     lib.tdma_status_string.argtypes = [ctypes.c_int]
     lib.tdma_status_string.restype = ctypes.c_char_p
+    lib.tdma_solve_thomas_static.argtypes = [ctypes.POINTER(Desc)] + [_VP] * 6
+    lib.tdma_solve_thomas_static.restype = st
     _LIB = lib
     return lib
 
