@@ -133,9 +133,10 @@ tdma_status_t tdma_solve(tdma_plan_t plan, const void* a, const void* b, const v
  * kernels on the transposed diagonals, then writes
  *   grad_d = lambda, grad_b_i = -lambda_i x_i, grad_a_i = -lambda_i x_{i-1} (0 at i = 0),
  *   grad_c_i = -lambda_i x_{i+1} (0 at i = n-1).
- * x is the forward solution. Any grad_* pointer may be NULL to skip that output. With
- * coef_broadcast = 1 the coefficient gradients are summed over lines (length-n arrays).
- * Types follow `precision` (F32_REFINE: grad_a/b/c float, grad_d double). */
+ * x is the forward solution. grad_d is required (it holds lambda); grad_a, grad_b and grad_c
+ * may be NULL to skip them. With coef_broadcast = 1 the coefficient gradients are sums over
+ * lines, ADDED to the length-n arrays given (zero them first). Types follow `precision`
+ * (F32_REFINE: grad_a/b/c float, grad_d double). Ragged batches return TDMA_ERR_UNSUPPORTED. */
 tdma_status_t tdma_solve_backward(tdma_plan_t plan, const void* a, const void* b, const void* c,
                                   const void* x, const void* grad_x, void* grad_a, void* grad_b,
                                   void* grad_c, void* grad_d, void* workspace,

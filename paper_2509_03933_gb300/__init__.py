@@ -282,9 +282,9 @@ def solve_backward(a, b, c, x, grad_x, axis=-1, precision="f64", partitions=0, n
         ga, gb, gc = (torch.zeros_like(t) if f else None for t, f in zip((a, b, c), need[:3]))
     else:
         ga, gb, gc = (torch.empty_like(t) if f else None for t, f in zip((a, b, c), need[:3]))
-    gd = torch.empty_like(x) if need[3] else None
+    gd = torch.empty_like(x)  # lambda = A^{-T} grad_x, always computed
     p.backward(a, b, c, x, grad_x.contiguous() if grad_x.stride() != x.stride() else grad_x, ga, gb, gc, gd)
-    return ga, gb, gc, gd
+    return ga, gb, gc, (gd if need[3] else None)
 
 
 class TDMASolve(torch.autograd.Function):

@@ -30,12 +30,20 @@ template <class CT, int NR> struct Row {
   CT d[NR];
 };
 
-template <class CT, int NR>
+// Row i of the system, or with TR of its transpose A^T (sub-diagonal c_{i-1}, super-diagonal
+// a_{i+1}; the adjoint solve of the backward pass). Reads stay inside the line.
+template <class CT, int NR, bool TR = false>
 TDMA_DEV void load_row(Row<CT, NR>& r, const Args& A, int64_t e, int64_t i, CT shift) {
   const int64_t ci = A.bcast ? i : e;
-  r.a = ldg((const CT*)A.a + ci);
+  if constexpr (TR) {
+    const int64_t st = A.bcast ? 1 : A.lay.es;
+    r.a = i > 0 ? ldg((const CT*)A.c + ci - st) : CT(0);
+    r.c = i < A.lay.n - 1 ? ldg((const CT*)A.a + ci + st) : CT(0);
+  } else {
+    r.a = ldg((const CT*)A.a + ci);
+    r.c = ldg((const CT*)A.c + ci);
+  }
   r.b = ldg((const CT*)A.b + ci) + shift;
-  r.c = ldg((const CT*)A.c + ci);
   if constexpr (NR == 1) {
     r.d[0] = ldg((const CT*)A.d + e);
   } else if constexpr (sizeof(CT) == 8) {
@@ -104,7 +112,7 @@ __host__ __device__ inline size_t dc_smem_bytes(int T, int Lb, int P, int mmax) 
 
 constexpr int kChunk = 4;  // rows loaded ahead of the forward sweep
 
-template <class CT, int NR>
+template <class CT, int NR, bool TR = false>
 __global__ void __launch_bounds__(512) dc_kernel(const Args A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CT* sm = reinterpret_cast<CT*>(smem_raw);
@@ -134,7 +142,7 @@ __global__ void __launch_bounds__(512) dc_kernel(const Args A) {
   // ---------------- Stage A: forward modified-Thomas sweep
   if (active) {
     Row<CT, NR> r0;
-    load_row<CT, NR>(r0, A, base + start * es, start, shift);
+    load_row<CT, NR, TR>(r0, A, base + start * es, start, shift);
     if (k == 0) r0.a = CT(0);                      // a_0 of the line is ignored
     if (m == 1) {                                  // n == 1: a single equation b x = d
       CT v[NR];
@@ -155,13 +163,13 @@ __global__ void __launch_bounds__(512) dc_kernel(const Args A) {
       Row<CT, NR> buf[kChunk];
 #pragma unroll
       for (int u = 0; u < kChunk; ++u)
-        if (1 + u < m) load_row<CT, NR>(buf[u], A, base + (start + 1 + u) * es, start + 1 + u, shift);
+        if (1 + u < m) load_row<CT, NR, TR>(buf[u], A, base + (start + 1 + u) * es, start + 1 + u, shift);
       for (int t0 = 1; t0 < m; t0 += kChunk) {
         Row<CT, NR> nxt[kChunk];
 #pragma unroll
         for (int u = 0; u < kChunk; ++u) {
           const int t = t0 + kChunk + u;
-          if (t < m) load_row<CT, NR>(nxt[u], A, base + (start + t) * es, start + t, shift);
+          if (t < m) load_row<CT, NR, TR>(nxt[u], A, base + (start + t) * es, start + t, shift);
         }
 #pragma unroll
         for (int u = 0; u < kChunk; ++u) {

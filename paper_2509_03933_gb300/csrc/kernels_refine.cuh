@@ -81,10 +81,17 @@ TDMA_DEV float narrow(double v) { return __double2float_rn(v); }
 
 struct Coef { float a, b, c; double d; };
 
-TDMA_DEV void load_coef(Coef& r, const Args& A, int64_t e) {
-  r.a = ldg((const float*)A.a + e);
+// Row i (or with TR the transposed row, as load_row) of the float coefficients and double d.
+template <bool TR = false>
+TDMA_DEV void load_coef(Coef& r, const Args& A, int64_t e, int64_t i) {
+  if constexpr (TR) {
+    r.a = i > 0 ? ldg((const float*)A.c + e - A.lay.es) : 0.f;
+    r.c = i < A.lay.n - 1 ? ldg((const float*)A.a + e + A.lay.es) : 0.f;
+  } else {
+    r.a = ldg((const float*)A.a + e);
+    r.c = ldg((const float*)A.c + e);
+  }
   r.b = ldg((const float*)A.b + e);
-  r.c = ldg((const float*)A.c + e);
   r.d = ldg((const double*)A.d + e);
 }
 
@@ -101,7 +108,7 @@ TDMA_DEV float residual_ff(float a, float b, float c, ff dd, ff xm, ff x0, ff xp
   return __fadd_rn(s3.h, err);
 }
 
-template <class BT>
+template <class BT, bool TR = false>
 __global__ void __launch_bounds__(512) refine_kernel(const Args A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int T = blockDim.x, tid = threadIdx.x;
@@ -161,7 +168,7 @@ __global__ void __launch_bounds__(512) refine_kernel(const Args A) {
       }
       for (int t = 0; t < m; ++t) {
         Coef cf;
-        load_coef(cf, A, base + (start + t) * es);
+        load_coef<TR>(cf, A, base + (start + t) * es, start + t);
         if (k == 0 && t == 0) cf.a = 0.f;
         if (k == P - 1 && t == m - 1) cf.c = 0.f;
         const ff dd = split_f64(cf.d);

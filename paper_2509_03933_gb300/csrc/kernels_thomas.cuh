@@ -18,7 +18,7 @@ namespace tdma {
 constexpr int kThomasBlock = 128;
 constexpr int kThomasAhead = 4;  // rows loaded ahead of the forward sweep
 
-template <class CT, int NR>
+template <class CT, int NR, bool TR = false>
 __global__ void __launch_bounds__(kThomasBlock) thomas_kernel(const Args A, CT* __restrict__ cws) {
   const int64_t line = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (line >= A.lay.n_lines) return;
@@ -30,7 +30,7 @@ __global__ void __launch_bounds__(kThomasBlock) thomas_kernel(const Args A, CT* 
   Row<CT, NR> buf[kThomasAhead];
 #pragma unroll
   for (int u = 0; u < kThomasAhead; ++u)
-    if (u < n) load_row<CT, NR>(buf[u], A, base + u * es, u, shift);
+    if (u < n) load_row<CT, NR, TR>(buf[u], A, base + u * es, u, shift);
   CT cp = CT(0), dp[NR];
 #pragma unroll
   for (int q = 0; q < NR; ++q) dp[q] = CT(0);
@@ -40,7 +40,7 @@ __global__ void __launch_bounds__(kThomasBlock) thomas_kernel(const Args A, CT* 
 #pragma unroll
     for (int u = 0; u < kThomasAhead; ++u) {
       const int64_t i = i0 + kThomasAhead + u;
-      if (i < n) load_row<CT, NR>(nxt[u], A, base + i * es, i, shift);
+      if (i < n) load_row<CT, NR, TR>(nxt[u], A, base + i * es, i, shift);
     }
 #pragma unroll
     for (int u = 0; u < kThomasAhead; ++u) {

@@ -402,6 +402,56 @@ cudaError_t prepare_kernel(const tdma_plan_s* p) {
   return cudaSuccess;
 }
 
+// Adjoint solve A^T lambda = grad_x (forward kernels with transposed row reads) into grad_d,
+// then the gradient epilogue.
+template <class CT, int NR>
+cudaError_t adjoint_solve(const tdma_plan_s* p, const Args& A, cudaStream_t s) {
+  const tdma_config_t& c = p->cfg;
+  const dim3 grid(c.blocks), block(c.threads_per_block);
+  if (c.variant == TDMA_VARIANT_THOMAS) {
+    thomas_kernel<CT, NR, true><<<grid, block, 0, s>>>(A, (CT*)A.ws);
+    return cudaGetLastError();
+  }
+  if (c.variant != TDMA_VARIANT_DC) return cudaErrorNotSupported;
+  const cudaError_t e = set_smem(dc_kernel<CT, NR, true>, (size_t)c.smem_bytes);
+  if (e != cudaSuccess) return e;
+  dc_kernel<CT, NR, true><<<grid, block, (size_t)c.smem_bytes, s>>>(A);
+  return cudaGetLastError();
+}
+
+cudaError_t backward_impl(const tdma_plan_s* p, const void* a, const void* b, const void* c, const void* x,
+                          const void* gx, void* ga, void* gb, void* gc, void* gd, void* ws, cudaStream_t s) {
+  const tdma_desc_t& d = p->desc;
+  if (d.n == 0) return cudaErrorNotSupported;
+  Args A = make_args(p, a, b, c, gx, gd, ws);
+  cudaError_t e;
+  if (d.precision == TDMA_F32_REFINE) {
+    // the adjoint system in float storage with refinement, on the shared-memory refine kernel
+    tdma_config_t bc{};
+    if (!choose_block(d, default_partitions(d), bc)) return cudaErrorNotSupported;
+    A.P = bc.partitions;
+    A.Lb = bc.lines_per_block;
+    A.mmax = bc.rows_per_thread;
+    e = set_smem(refine_kernel<double, true>, (size_t)bc.smem_bytes);
+    if (e != cudaSuccess) return e;
+    refine_kernel<double, true><<<bc.blocks, bc.threads_per_block, (size_t)bc.smem_bytes, s>>>(A);
+    e = cudaGetLastError();
+  } else if (d.precision == TDMA_F64) {
+    e = d.nrhs == 1 ? adjoint_solve<double, 1>(p, A, s) : adjoint_solve<double, 2>(p, A, s);
+  } else {
+    e = d.nrhs == 1 ? adjoint_solve<float, 1>(p, A, s) : adjoint_solve<float, 2>(p, A, s);
+  }
+  if (e != cudaSuccess) return e;
+  if (!ga && !gb && !gc) return cudaSuccess;
+  if (d.precision == TDMA_F64)
+    return d.nrhs == 1 ? launch_epilogue<double, double, 1>(A.lay, d.coef_broadcast, x, gd, ga, gb, gc, s)
+                       : launch_epilogue<double, double, 2>(A.lay, d.coef_broadcast, x, gd, ga, gb, gc, s);
+  if (d.precision == TDMA_F32)
+    return d.nrhs == 1 ? launch_epilogue<float, float, 1>(A.lay, d.coef_broadcast, x, gd, ga, gb, gc, s)
+                       : launch_epilogue<float, float, 2>(A.lay, d.coef_broadcast, x, gd, ga, gb, gc, s);
+  return launch_epilogue<float, double, 1>(A.lay, d.coef_broadcast, x, gd, ga, gb, gc, s);
+}
+
 }  // namespace
 
 extern "C" {
@@ -518,10 +568,9 @@ tdma_status_t tdma_solve_backward(tdma_plan_t p, const void* a, const void* b, c
                                   size_t ws_bytes, void* stream) {
   if (!p) return TDMA_ERR_INVALID_ARG;
   if (p->desc.n_lines == 0) return TDMA_OK;
-  if (!a || !b || !c || !x || !gx) return TDMA_ERR_INVALID_ARG;
+  if (!a || !b || !c || !x || !gx || !gd) return TDMA_ERR_INVALID_ARG;
   if (ws_bytes < p->workspace || (p->workspace > 0 && !ws)) return TDMA_ERR_WORKSPACE;
-  const cudaError_t e = launch_backward(p->desc, p->cfg, p->status, a, b, c, x, gx, ga, gb, gc, gd, ws,
-                                        (cudaStream_t)stream);
+  const cudaError_t e = backward_impl(p, a, b, c, x, gx, ga, gb, gc, gd, ws, (cudaStream_t)stream);
   if (e == cudaErrorNotSupported) return TDMA_ERR_UNSUPPORTED;
   return e == cudaSuccess ? TDMA_OK : TDMA_ERR_CUDA;
 }
