@@ -15,7 +15,7 @@ import torch
 
 from . import _build
 
-__all__ = ["Plan", "solve", "solve_backward", "TDMASolve", "line_layout", "TDMAError", "F64", "F32",
+__all__ = ["Plan", "solve", "solve_ragged", "solve_backward", "TDMASolve", "line_layout", "TDMAError", "F64", "F32",
            "F32_REFINE", "load_library", "declared_symbols", "sweep_graph"]
 
 F64, F32, F32_REFINE = 0, 1, 2
@@ -272,6 +272,27 @@ def solve(a, b, c, d, axis=-1, precision="f64", partitions=0, out=None, nrhs=1, 
         if st != 0:
             raise TDMAError(st, "device")
     return x
+
+
+def solve_ragged(a, b, c, d, offsets, lengths, precision="f64", out=None, max_n=None, max_refine_iters=0,
+                 refine_tol=0.0, check=False, plan=None):
+    """Solve lines of uneven length packed in 1D arrays: line l has lengths[l] unknowns starting at
+    offsets[l] (device int64 / int32 tensors). One persistent launch over a device work queue.
+    Returns (x, plan); pass the plan back to reuse its sorted tables for the same batch."""
+    if not d.is_cuda:
+        raise RuntimeError("tdma.solve_ragged needs CUDA tensors (no CPU fallback)")
+    if plan is None:
+        n_max = int(lengths.max().item()) if max_n is None else int(max_n)
+        plan = Plan(0, int(lengths.numel()), precision=precision, ragged_offsets=offsets, ragged_lengths=lengths,
+                    ragged_max_n=n_max, ragged_total=int(d.numel()), max_refine_iters=max_refine_iters,
+                    refine_tol=refine_tol)
+    x = torch.empty_like(d) if out is None else out
+    plan.solve(a, b, c, d, x)
+    if check:
+        st, _ = plan.last_error()
+        if st != 0:
+            raise TDMAError(st, "device")
+    return x, plan
 
 
 def solve_backward(a, b, c, x, grad_x, axis=-1, precision="f64", partitions=0, nrhs=1, coef_broadcast=False,

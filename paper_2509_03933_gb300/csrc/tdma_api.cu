@@ -8,6 +8,7 @@
 #include <mutex>
 #include <new>
 #include <tuple>
+#include <vector>
 
 #include "tdma.h"
 #include "kernels_dc.cuh"
@@ -29,6 +30,8 @@ struct tdma_plan_s {
   bool refine_sb64 = true;
   bool allow_tma = true;  // TDMA_DISABLE_TMA=1 loads tiles with ordinary loads instead (diagnostics)
   size_t workspace = 0;
+  RaggedTables rt{};       // ragged batches: sorted order, groups, scratch bases, work counter
+  void* rt_mem = nullptr;  // one device allocation holding the tables
 };
 
 namespace {
@@ -114,7 +117,6 @@ bool prefer_thomas(const tdma_desc_t& d) { return d.n > 1 && d.n_lines >= 65536;
 
 size_t workspace_for(const tdma_desc_t& d, const tdma_config_t& c) {
   if (c.variant == TDMA_VARIANT_THOMAS) return thomas_workspace(d);
-  if (c.variant == TDMA_VARIANT_RAGGED) return ragged_workspace(d, c);
   return 0;
 }
 
@@ -351,8 +353,14 @@ cudaError_t launch_forward(const tdma_plan_s* p, const Args& A, cudaStream_t s) 
     }
     case TDMA_VARIANT_THOMAS:
       return launch_thomas(p->desc.precision, p->desc.nrhs, A, c, s);
-    case TDMA_VARIANT_RAGGED:
-      return launch_ragged(p->desc.precision, A, c, s);
+    case TDMA_VARIANT_RAGGED: {
+      cudaError_t e = cudaMemsetAsync(p->rt.queue, 0, sizeof(int32_t), s);
+      if (e != cudaSuccess) return e;
+      if (p->desc.precision == TDMA_F64) ragged_dc_kernel<double><<<grid, block, sm, s>>>(A, p->rt);
+      else if (p->desc.precision == TDMA_F32) ragged_dc_kernel<float><<<grid, block, sm, s>>>(A, p->rt);
+      else ragged_refine_kernel<<<grid, block, sm, s>>>(A, p->rt);
+      break;
+    }
     default:
       return cudaErrorInvalidValue;
   }
@@ -397,7 +405,7 @@ cudaError_t prepare_kernel(const tdma_plan_s* p) {
     case TDMA_VARIANT_THOMAS:
       return prepare_thomas(p->desc.precision, p->desc.nrhs, sm);
     case TDMA_VARIANT_RAGGED:
-      return prepare_ragged(p->desc.precision, sm);
+      return cudaSuccess;
   }
   return cudaSuccess;
 }
@@ -452,6 +460,84 @@ cudaError_t backward_impl(const tdma_plan_s* p, const void* a, const void* b, co
   return launch_epilogue<float, double, 1>(A.lay, d.coef_broadcast, x, gd, ga, gb, gc, s);
 }
 
+// Ragged batch plan: sort lines longest first, cut into groups (P partitions of about 16 rows,
+// up to 256 / P lines of length >= 2P each), lay out per-line scratch, upload the tables.
+tdma_status_t build_ragged(tdma_plan_s* p) {
+  const tdma_desc_t& d = p->desc;
+  const int64_t L = d.n_lines;
+  if (d.nrhs != 1) return TDMA_ERR_UNSUPPORTED;
+  std::vector<int32_t> len((size_t)L);
+  if (L > 0 && cudaMemcpy(len.data(), d.ragged_lengths, sizeof(int32_t) * L, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return TDMA_ERR_CUDA;
+  for (int64_t i = 0; i < L; ++i)
+    if (len[i] < 1 || len[i] > d.ragged_max_n) return TDMA_ERR_INVALID_ARG;
+  std::vector<int32_t> order((size_t)L);
+  for (int64_t i = 0; i < L; ++i) order[i] = (int32_t)i;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return len[x] > len[y]; });
+  auto parts_for = [](int64_t n) {
+    int64_t P = (n + kRaggedRowsPerPart - 1) / kRaggedRowsPerPart;
+    P = std::min<int64_t>(P, kRaggedThreads);
+    P = std::min<int64_t>(P, n / 2);
+    return (int)std::max<int64_t>(P, 1);
+  };
+  std::vector<RaggedGroup> groups;
+  std::vector<int64_t> sbase((size_t)L);
+  int64_t scratch = 0;
+  for (int64_t i = 0; i < L;) {
+    const int P = parts_for(len[order[i]]);
+    const int cmax = std::max(1, kRaggedThreads / P);
+    int cnt = 0;
+    while (cnt < cmax && i + cnt < L && (P == 1 || len[order[i + cnt]] >= 2 * P)) {
+      const int64_t n = len[order[i + cnt]];
+      sbase[order[i + cnt]] = scratch;
+      scratch += (int64_t)P * ((n + P - 1) / P);
+      ++cnt;
+    }
+    groups.push_back(RaggedGroup{(int32_t)i, cnt, P, 0});
+    i += cnt;
+  }
+  const size_t b_order = sizeof(int32_t) * (size_t)std::max<int64_t>(L, 1);
+  const size_t b_sbase = sizeof(int64_t) * (size_t)std::max<int64_t>(L, 1);
+  const size_t b_groups = sizeof(RaggedGroup) * std::max<size_t>(groups.size(), 1);
+  const size_t off_sbase = (b_order + 15) / 16 * 16, off_groups = off_sbase + (b_sbase + 15) / 16 * 16;
+  const size_t off_queue = off_groups + (b_groups + 15) / 16 * 16;
+  if (cudaMalloc(&p->rt_mem, off_queue + 16) != cudaSuccess) return TDMA_ERR_CUDA;
+  unsigned char* m = (unsigned char*)p->rt_mem;
+  if ((L > 0 && cudaMemcpy(m, order.data(), sizeof(int32_t) * L, cudaMemcpyHostToDevice) != cudaSuccess) ||
+      (L > 0 && cudaMemcpy(m + off_sbase, sbase.data(), sizeof(int64_t) * L, cudaMemcpyHostToDevice) != cudaSuccess) ||
+      (!groups.empty() && cudaMemcpy(m + off_groups, groups.data(), sizeof(RaggedGroup) * groups.size(),
+                                     cudaMemcpyHostToDevice) != cudaSuccess))
+    return TDMA_ERR_CUDA;
+  p->rt.order = (const int32_t*)m;
+  p->rt.sbase = (const int64_t*)(m + off_sbase);
+  p->rt.groups = (const RaggedGroup*)(m + off_groups);
+  p->rt.n_groups = (int32_t)groups.size();
+  p->rt.queue = (int32_t*)(m + off_queue);
+  p->rt.scratch_elems = scratch;
+  // persistent grid: as many resident blocks as fit, never more than there are groups
+  tdma_config_t c{};
+  c.variant = TDMA_VARIANT_RAGGED;
+  c.threads_per_block = kRaggedThreads;
+  c.smem_bytes = (int64_t)ragged_smem_bytes(d.precision);
+  int occ = 1, sms = 1, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (d.precision == TDMA_F64)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ragged_dc_kernel<double>, kRaggedThreads, c.smem_bytes);
+  else if (d.precision == TDMA_F32)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ragged_dc_kernel<float>, kRaggedThreads, c.smem_bytes);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ragged_refine_kernel, kRaggedThreads, c.smem_bytes);
+  c.blocks = (int32_t)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(occ, 1), (int64_t)groups.size()));
+  c.partitions = groups.empty() ? 1 : groups.front().P;
+  c.rows_per_thread = kRaggedRowsPerPart;
+  c.lines_per_block = groups.empty() ? 1 : groups.front().count;
+  p->cfg = c;
+  const size_t arrays = d.precision == TDMA_F32_REFINE ? 5 : 3;
+  p->workspace = arrays * (size_t)scratch * (d.precision == TDMA_F64 ? 8 : 4);
+  return TDMA_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -501,12 +587,17 @@ tdma_status_t tdma_plan_create(tdma_plan_t* plan, const tdma_desc_t* desc, size_
       delete p;
       return TDMA_ERR_UNSUPPORTED;
     }
+    p->cfg = c;
+    p->workspace = workspace_for(*desc, c);
   } else {
-    ragged_config(*desc, c);
+    const tdma_status_t r = build_ragged(p);
+    if (r != TDMA_OK) {
+      if (p->rt_mem) cudaFree(p->rt_mem);
+      delete p;
+      return r;
+    }
   }
-  p->cfg = c;
-  p->workspace = workspace_for(*desc, c);
-  if (cudaMalloc(&p->status, sizeof(DevStatus)) != cudaSuccess) { delete p; return TDMA_ERR_CUDA; }
+  if (cudaMalloc(&p->status, sizeof(DevStatus)) != cudaSuccess) { tdma_plan_destroy(p); return TDMA_ERR_CUDA; }
   if (cudaMemset(p->status, 0, sizeof(DevStatus)) != cudaSuccess) { cudaFree(p->status); delete p; return TDMA_ERR_CUDA; }
   if (prepare_kernel(p) != cudaSuccess) { cudaFree(p->status); delete p; return TDMA_ERR_CUDA; }
   if (workspace_bytes) *workspace_bytes = p->workspace;
@@ -518,6 +609,7 @@ tdma_status_t tdma_plan_destroy(tdma_plan_t p) {
   if (!p) return TDMA_OK;
   cudaError_t e = cudaSuccess;
   if (p->status) e = cudaFree(p->status);
+  if (p->rt_mem && cudaFree(p->rt_mem) != cudaSuccess) e = cudaErrorUnknown;
   delete p;
   return e == cudaSuccess ? TDMA_OK : TDMA_ERR_CUDA;
 }
