@@ -136,7 +136,7 @@ tdma_status_t tdma_solve(tdma_plan_t plan, const void* a, const void* b, const v
  * x is the forward solution. grad_d is required (it holds lambda); grad_a, grad_b and grad_c
  * may be NULL to skip them. With coef_broadcast = 1 the coefficient gradients are sums over
  * lines, ADDED to the length-n arrays given (zero them first). Types follow `precision`
- * (F32_REFINE: grad_a/b/c float, grad_d double). Ragged batches return TDMA_ERR_UNSUPPORTED. */
+ * (F32_REFINE: grad_a/b/c float, grad_d double). Ragged batches are supported (per-line arrays). */
 tdma_status_t tdma_solve_backward(tdma_plan_t plan, const void* a, const void* b, const void* c,
                                   const void* x, const void* grad_x, void* grad_a, void* grad_b,
                                   void* grad_c, void* grad_d, void* workspace,

@@ -41,7 +41,7 @@ struct RaggedTables {
   int64_t scratch_elems;   // elements of each scratch array
 };
 
-template <class CT>
+template <class CT, bool TR = false>
 __global__ void __launch_bounds__(kRaggedThreads) ragged_dc_kernel(const Args A, const RaggedTables RT) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CT* red = reinterpret_cast<CT*>(smem_raw);
@@ -77,11 +77,20 @@ __global__ void __launch_bounds__(kRaggedThreads) ragged_dc_kernel(const Args A,
       const CT* pb = (const CT*)A.b + base + start;
       const CT* pc = (const CT*)A.c + base + start;
       const CT* pd = (const CT*)A.d + base + start;
-      CT a0 = (k == 0) ? CT(0) : ldg(pa), b0 = ldg(pb), c0 = ldg(pc), d0 = ldg(pd);
+      // row t of this partition (with TR: of the transpose, sub c_{i-1}, super a_{i+1})
+      auto sub = [&](int t) -> CT {
+        if (k == 0 && t == 0) return CT(0);
+        return TR ? ldg(pc + t - 1) : ldg(pa + t);
+      };
+      auto sup = [&](int t) -> CT {
+        if (k == P - 1 && t == m - 1) return CT(0);
+        return TR ? ldg(pa + t + 1) : ldg(pc + t);
+      };
+      CT a0 = sub(0), b0 = ldg(pb), c0 = sup(0), d0 = ldg(pd);
       CT alpha = CT(-1), gamma = CT(0), delta = CT(0), Q = CT(1), Gs = CT(0), F = CT(0);
       for (int t = 1; t < m; ++t) {
-        const CT a = ldg(pa + t), b = ldg(pb + t), d = ldg(pd + t);
-        const CT c = (k == P - 1 && t == m - 1) ? CT(0) : ldg(pc + t);
+        const CT a = sub(t), b = ldg(pb + t), d = ldg(pd + t);
+        const CT c = sup(t);
         const CT r = rcp(b - a * gamma);
         const CT ar = a * r;
         alpha = -ar * alpha;
@@ -131,6 +140,7 @@ __global__ void __launch_bounds__(kRaggedThreads) ragged_dc_kernel(const Args A,
 // F32 storage + refinement on ragged groups: same passes as refine_kernel (first pass solves
 // fl(d); later passes solve for the correction from the extra-precise residual), with alpha,
 // gamma, delta and both parts of x in the workspace. Partition-row scratch index: sb + t P + k.
+template <bool TR = false>
 __global__ void __launch_bounds__(kRaggedThreads) ragged_refine_kernel(const Args A, const RaggedTables RT) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* red = reinterpret_cast<float*>(smem_raw);
@@ -180,9 +190,9 @@ __global__ void __launch_bounds__(kRaggedThreads) ragged_refine_kernel(const Arg
           pm = ff{s_xh[o], s_xl[o]};
         }
         for (int t = 0; t < m; ++t) {
-          float a = (k == 0 && t == 0) ? 0.f : ldg(pa + t);
+          float a = (k == 0 && t == 0) ? 0.f : (TR ? ldg(pc + t - 1) : ldg(pa + t));
           const float b = ldg(pb + t);
-          float c = (k == P - 1 && t == m - 1) ? 0.f : ldg(pc + t);
+          float c = (k == P - 1 && t == m - 1) ? 0.f : (TR ? ldg(pa + t + 1) : ldg(pc + t));
           const ff dd = split_f64(ldg(pd + t));
           float rhs;
           if (it == 0) {
@@ -292,6 +302,27 @@ __global__ void __launch_bounds__(kRaggedThreads) ragged_refine_kernel(const Arg
       for (int t = 0; t < m; ++t) px[t] = ff_to_f64(ff{s_xh[xo(t)], s_xl[xo(t)]});
     }
     __syncthreads();
+  }
+}
+
+// Gradient epilogue for ragged batches: one warp per line, lanes striding over its rows.
+template <class GT, class XT>
+__global__ void __launch_bounds__(256) ragged_epilogue(const int64_t n_lines, const int64_t* __restrict__ roff,
+                                                       const int32_t* __restrict__ rlen, const XT* __restrict__ x,
+                                                       const XT* __restrict__ lam, GT* __restrict__ ga,
+                                                       GT* __restrict__ gb, GT* __restrict__ gc) {
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t l = warp; l < n_lines; l += nwarps) {
+    const int64_t base = roff[l], n = rlen[l];
+    for (int64_t i = lane; i < n; i += 32) {
+      const int64_t e = base + i;
+      const double lv = (double)lam[e];
+      if (gb) gb[e] = (GT)(-lv * (double)x[e]);
+      if (ga) ga[e] = (GT)(i > 0 ? -lv * (double)x[e - 1] : 0.0);
+      if (gc) gc[e] = (GT)(i < n - 1 ? -lv * (double)x[e + 1] : 0.0);
+    }
   }
 }
 

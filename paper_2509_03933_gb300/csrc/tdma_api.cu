@@ -358,7 +358,7 @@ cudaError_t launch_forward(const tdma_plan_s* p, const Args& A, cudaStream_t s) 
       if (e != cudaSuccess) return e;
       if (p->desc.precision == TDMA_F64) ragged_dc_kernel<double><<<grid, block, sm, s>>>(A, p->rt);
       else if (p->desc.precision == TDMA_F32) ragged_dc_kernel<float><<<grid, block, sm, s>>>(A, p->rt);
-      else ragged_refine_kernel<<<grid, block, sm, s>>>(A, p->rt);
+      else ragged_refine_kernel<false><<<grid, block, sm, s>>>(A, p->rt);
       break;
     }
     default:
@@ -430,9 +430,33 @@ cudaError_t adjoint_solve(const tdma_plan_s* p, const Args& A, cudaStream_t s) {
 cudaError_t backward_impl(const tdma_plan_s* p, const void* a, const void* b, const void* c, const void* x,
                           const void* gx, void* ga, void* gb, void* gc, void* gd, void* ws, cudaStream_t s) {
   const tdma_desc_t& d = p->desc;
-  if (d.n == 0) return cudaErrorNotSupported;
   Args A = make_args(p, a, b, c, gx, gd, ws);
   cudaError_t e;
+  if (d.n == 0) {  // ragged: the same persistent launch on the transposed rows
+    const tdma_config_t& rc = p->cfg;
+    e = cudaMemsetAsync(p->rt.queue, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    const size_t sm = (size_t)rc.smem_bytes;
+    if (d.precision == TDMA_F64) ragged_dc_kernel<double, true><<<rc.blocks, rc.threads_per_block, sm, s>>>(A, p->rt);
+    else if (d.precision == TDMA_F32) ragged_dc_kernel<float, true><<<rc.blocks, rc.threads_per_block, sm, s>>>(A, p->rt);
+    else ragged_refine_kernel<true><<<rc.blocks, rc.threads_per_block, sm, s>>>(A, p->rt);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || (!ga && !gb && !gc)) return e;
+    const int64_t blocks = std::min<int64_t>((d.n_lines + 7) / 8, 65535);
+    if (d.precision == TDMA_F64)
+      ragged_epilogue<double, double><<<(unsigned)blocks, 256, 0, s>>>(d.n_lines, d.ragged_offsets, d.ragged_lengths,
+                                                                     (const double*)x, (const double*)gd, (double*)ga,
+                                                                     (double*)gb, (double*)gc);
+    else if (d.precision == TDMA_F32)
+      ragged_epilogue<float, float><<<(unsigned)blocks, 256, 0, s>>>(d.n_lines, d.ragged_offsets, d.ragged_lengths,
+                                                                   (const float*)x, (const float*)gd, (float*)ga,
+                                                                   (float*)gb, (float*)gc);
+    else
+      ragged_epilogue<float, double><<<(unsigned)blocks, 256, 0, s>>>(d.n_lines, d.ragged_offsets, d.ragged_lengths,
+                                                                    (const double*)x, (const double*)gd, (float*)ga,
+                                                                    (float*)gb, (float*)gc);
+    return cudaGetLastError();
+  }
   if (d.precision == TDMA_F32_REFINE) {
     // the adjoint system in float storage with refinement, on the shared-memory refine kernel
     tdma_config_t bc{};
@@ -527,7 +551,7 @@ tdma_status_t build_ragged(tdma_plan_s* p) {
   else if (d.precision == TDMA_F32)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ragged_dc_kernel<float>, kRaggedThreads, c.smem_bytes);
   else
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ragged_refine_kernel, kRaggedThreads, c.smem_bytes);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ragged_refine_kernel<false>, kRaggedThreads, c.smem_bytes);
   c.blocks = (int32_t)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(occ, 1), (int64_t)groups.size()));
   c.partitions = groups.empty() ? 1 : groups.front().P;
   c.rows_per_thread = kRaggedRowsPerPart;

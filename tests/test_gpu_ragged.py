@@ -55,3 +55,26 @@ def test_many_short_lines_share_blocks():
     err, plan = _run(lengths, 7, "f64")
     assert err <= 1e-12
     assert plan.config["lines_per_block"] > 1
+
+
+@pytest.mark.parametrize("precision", ["f64", "f32r"])
+def test_ragged_backward_matches_oracle_adjoint(precision):
+    lengths = np.array([3, 700, 16, 5000, 33, 2, 129], np.int32)
+    r = synth.ragged_general(lengths, 9, device="cuda", fp32_coefficients=precision != "f64")
+    keys = ("a", "b", "c") if precision == "f64" else ("a32", "b32", "c32")
+    a, b, c = (r[k] for k in keys)
+    d = r["d"]
+    x, plan = tdma.solve_ragged(a, b, c, d, r["offsets"], r["lengths"], precision=precision, check=True)
+    w = torch.randn_like(x)
+    ga, gb, gc, gd = (torch.empty_like(a), torch.empty_like(b), torch.empty_like(c), torch.empty_like(x))
+    plan.backward(a, b, c, x, w, ga, gb, gc, gd)
+    torch.cuda.synchronize()
+    offs, lens = r["offsets"].cpu().numpy(), r["lengths"].cpu().numpy()
+    h = lambda t: t.double().cpu().numpy()
+    for l, (o, n) in enumerate(zip(offs, lens)):
+        s = slice(o, o + n)
+        ref = O.adjoint_grads(h(a)[s], h(b)[s], h(c)[s], h(x)[s], h(w)[s])
+        assert O.rel_l2(h(gd)[s], ref[3]) <= 1e-12
+        tol = 1e-12 if precision == "f64" else 1e-6
+        for got, want in zip((ga, gb, gc), ref[:3]):
+            assert O.rel_l2(h(got)[s], want) <= tol
