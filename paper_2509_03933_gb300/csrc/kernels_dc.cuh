@@ -112,7 +112,9 @@ __host__ __device__ inline size_t dc_smem_bytes(int T, int Lb, int P, int mmax) 
 
 constexpr int kChunk = 4;  // rows loaded ahead of the forward sweep
 
-template <class CT, int NR, bool TR = false>
+// GS: the per-row Stage A scratch lives in the workspace (a [slot][thread] region per block)
+// instead of shared memory, for partitions too long to keep enough threads per SM on chip.
+template <class CT, int NR, bool TR = false, bool GS = false>
 __global__ void __launch_bounds__(512) dc_kernel(const Args A) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CT* sm = reinterpret_cast<CT*>(smem_raw);
@@ -122,10 +124,10 @@ __global__ void __launch_bounds__(512) dc_kernel(const Args A) {
   const int64_t line = (int64_t)blockIdx.x * Lb + j;
   const bool active = line < A.lay.n_lines;
   const int slots = A.mmax > 2 ? A.mmax - 2 : 0;
-  CT* s_alpha = sm;
+  CT* s_alpha = GS ? (CT*)A.ws + (size_t)blockIdx.x * (2 + NR) * slots * T : sm;
   CT* s_gamma = s_alpha + (size_t)slots * T;
   CT* s_delta = s_gamma + (size_t)slots * T;  // NR blocks
-  CT* red = s_delta + (size_t)NR * slots * T;
+  CT* red = GS ? sm : s_delta + (size_t)NR * slots * T;
   const int R2 = 2 * P;
   const int pitch = (2 + NR) * R2 + 1;
   CT* r_sub = red + (size_t)j * pitch;

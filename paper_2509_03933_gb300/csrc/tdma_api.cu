@@ -61,7 +61,20 @@ bool choose_block(const tdma_desc_t& d, int P, tdma_config_t& c) {
   int Lb = std::max(1, 256 / P);
   Lb = (int)std::min<int64_t>(Lb, std::max<int64_t>(1, d.n_lines));
   if (Lb > 32) Lb = 32 * (Lb / 32);
+  const int Lb_full = Lb;
   while (Lb > 1 && dc_bytes(d, Lb * P, Lb, P, mmax) > (size_t)kMaxSmem) Lb /= 2;
+  if (d.precision != TDMA_F32_REFINE && Lb * P < 128 && Lb < Lb_full && Lb_full * P <= 512) {
+    // long partitions: keep full blocks and move the Stage A scratch to the workspace
+    const int T = Lb_full * P;
+    c.partitions = P;
+    c.rows_per_thread = mmax;
+    c.lines_per_block = Lb_full;
+    c.threads_per_block = T;
+    c.smem_bytes = (int64_t)dc_bytes(d, T, Lb_full, P, 2);  // reduced systems only
+    c.blocks = (int32_t)((d.n_lines + Lb_full - 1) / Lb_full);
+    c.variant = TDMA_VARIANT_DC_GLOBAL;
+    return true;
+  }
   const int T = Lb * P;
   if (T > 512) return false;
   const size_t smem = dc_bytes(d, T, Lb, P, mmax);
@@ -117,6 +130,9 @@ bool prefer_thomas(const tdma_desc_t& d) { return d.n > 1 && d.n_lines >= 65536;
 
 size_t workspace_for(const tdma_desc_t& d, const tdma_config_t& c) {
   if (c.variant == TDMA_VARIANT_THOMAS) return thomas_workspace(d);
+  if (c.variant == TDMA_VARIANT_DC_GLOBAL)
+    return (size_t)c.blocks * c.threads_per_block * (size_t)std::max(0, c.rows_per_thread - 2) * (2 + d.nrhs) *
+           (d.precision == TDMA_F64 ? 8 : 4);
   return 0;
 }
 
@@ -281,13 +297,22 @@ bool refine_tma_config(const tdma_desc_t& d, tdma_config_t& c) {
 }
 
 
+// Raise (never lower) a kernel's dynamic shared-memory limit: plans sharing a kernel may need
+// different amounts, and the attribute belongs to the kernel, not to the plan.
 template <class K> cudaError_t set_smem(K kernel, size_t bytes) {
+  static std::mutex mu;
+  std::lock_guard<std::mutex> lock(mu);
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 cudaError_t launch_forward(const tdma_plan_s* p, const Args& A, cudaStream_t s) {
   const tdma_config_t& c = p->cfg;
   if (p->desc.n_lines == 0) return cudaSuccess;
+  (void)cudaGetLastError();  // drop a stale non-sticky error left by another runtime call
   const dim3 grid(c.blocks), block(c.threads_per_block);
   const size_t sm = (size_t)c.smem_bytes;
   switch (c.variant) {
@@ -298,6 +323,15 @@ cudaError_t launch_forward(const tdma_plan_s* p, const Args& A, cudaStream_t s) 
       } else {
         if (p->desc.nrhs == 1) dc_kernel<float, 1><<<grid, block, sm, s>>>(A);
         else dc_kernel<float, 2><<<grid, block, sm, s>>>(A);
+      }
+      break;
+    case TDMA_VARIANT_DC_GLOBAL:
+      if (p->desc.precision == TDMA_F64) {
+        if (p->desc.nrhs == 1) dc_kernel<double, 1, false, true><<<grid, block, sm, s>>>(A);
+        else dc_kernel<double, 2, false, true><<<grid, block, sm, s>>>(A);
+      } else {
+        if (p->desc.nrhs == 1) dc_kernel<float, 1, false, true><<<grid, block, sm, s>>>(A);
+        else dc_kernel<float, 2, false, true><<<grid, block, sm, s>>>(A);
       }
       break;
     case TDMA_VARIANT_REFINE:
@@ -374,6 +408,8 @@ cudaError_t prepare_kernel(const tdma_plan_s* p) {
       if (p->desc.precision == TDMA_F64)
         return p->desc.nrhs == 1 ? set_smem(dc_kernel<double, 1>, sm) : set_smem(dc_kernel<double, 2>, sm);
       return p->desc.nrhs == 1 ? set_smem(dc_kernel<float, 1>, sm) : set_smem(dc_kernel<float, 2>, sm);
+    case TDMA_VARIANT_DC_GLOBAL:
+      return cudaSuccess;  // shared memory holds only the reduced systems (< 48 KB)
     case TDMA_VARIANT_REFINE:
       return p->refine_sb64 ? set_smem(refine_kernel<double>, sm) : set_smem(refine_kernel<float>, sm);
     case TDMA_VARIANT_REFINE_REG:
@@ -420,6 +456,12 @@ cudaError_t adjoint_solve(const tdma_plan_s* p, const Args& A, cudaStream_t s) {
     thomas_kernel<CT, NR, true><<<grid, block, 0, s>>>(A, (CT*)A.ws);
     return cudaGetLastError();
   }
+  if (c.variant == TDMA_VARIANT_DC_GLOBAL) {
+    const cudaError_t e = set_smem(dc_kernel<CT, NR, true, true>, (size_t)c.smem_bytes);
+    if (e != cudaSuccess) return e;
+    dc_kernel<CT, NR, true, true><<<grid, block, (size_t)c.smem_bytes, s>>>(A);
+    return cudaGetLastError();
+  }
   if (c.variant != TDMA_VARIANT_DC) return cudaErrorNotSupported;
   const cudaError_t e = set_smem(dc_kernel<CT, NR, true>, (size_t)c.smem_bytes);
   if (e != cudaSuccess) return e;
@@ -431,6 +473,7 @@ cudaError_t backward_impl(const tdma_plan_s* p, const void* a, const void* b, co
                           const void* gx, void* ga, void* gb, void* gc, void* gd, void* ws, cudaStream_t s) {
   const tdma_desc_t& d = p->desc;
   Args A = make_args(p, a, b, c, gx, gd, ws);
+  (void)cudaGetLastError();  // drop a stale non-sticky error left by another runtime call
   cudaError_t e;
   if (d.n == 0) {  // ragged: the same persistent launch on the transposed rows
     const tdma_config_t& rc = p->cfg;
