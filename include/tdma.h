@@ -101,6 +101,7 @@ typedef struct {
   int32_t variant;         /* kernel family, see TDMA_VARIANT_*                        */
   int32_t blocks;          /* grid size of the main launch                             */
   int64_t smem_bytes;      /* dynamic shared memory of the main launch                 */
+  int64_t workspace_bytes; /* workspace tdma_solve needs with this configuration        */
 } tdma_config_t;
 
 enum {
@@ -143,10 +144,16 @@ tdma_status_t tdma_solve_backward(tdma_plan_t plan, const void* a, const void* b
                                   void* grad_c, void* grad_d, void* workspace,
                                   size_t workspace_bytes, void* stream);
 
-/* Time the candidate launch configurations on the caller's data (runs tdma_solve several
- * times, overwriting x) and keep the fastest in the plan. Synchronises `stream`. The choice
- * is cached per process by problem shape; the workspace must be sized for the largest
- * candidate, which tdma_plan_create already reports when partitions == 0. */
+/* Autotune (the on-device analogue of the batch-size estimator of Section 4.2.3): time the
+ * launch configurations valid for the plan's lines (partitions per line, lines per block,
+ * kernel family) on the caller's data with CUDA events on `stream`, each run several times,
+ * overwriting x, and keep the fastest. Only candidates whose workspace fits `workspace_bytes`
+ * are tried; afterwards tdma_plan_get_config reports the choice and the workspace it needs.
+ * Synchronises `stream`. Choices are cached per process by problem class (precision, n, line
+ * count bucket, unit or strided axis, nrhs, broadcast) and, when the environment variable
+ * TDMA_AUTOTUNE_CACHE names a file, read from and appended to that file; a plan created with
+ * partitions == 0 starts from a cached choice when there is one. Ragged plans keep their
+ * configuration (returns TDMA_OK). */
 tdma_status_t tdma_plan_autotune(tdma_plan_t plan, const void* a, const void* b, const void* c,
                                  const void* d, void* x, void* workspace, size_t workspace_bytes,
                                  void* stream);

@@ -44,7 +44,8 @@ class Desc(ctypes.Structure):
 class Config(ctypes.Structure):
     _fields_ = [("partitions", ctypes.c_int32), ("rows_per_thread", ctypes.c_int32),
                 ("lines_per_block", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
-                ("variant", ctypes.c_int32), ("blocks", ctypes.c_int32), ("smem_bytes", ctypes.c_int64)]
+                ("variant", ctypes.c_int32), ("blocks", ctypes.c_int32), ("smem_bytes", ctypes.c_int64),
+                ("workspace_bytes", ctypes.c_int64)]
 
 
 _LIB = None
@@ -203,13 +204,21 @@ class Plan:
             raise TDMAError(st, "tdma_solve_backward")
 
     def autotune(self, a, b, c, d, x, workspace=None, stream=None):
-        ws = workspace if workspace is not None else (self.workspace(d.device) if self.workspace_bytes else None)
+        """Time the candidate configurations on these buffers and keep the fastest. Without an
+        explicit workspace, one large enough for every candidate (3 words per unknown) is offered."""
+        if workspace is None:
+            unknowns = self.desc.n * self.desc.n_lines * self.desc.nrhs
+            workspace = torch.empty(max(1, unknowns * 8 * 3), dtype=torch.uint8, device=d.device)
+        ws = workspace
         st = self._lib.tdma_plan_autotune(self._h, _ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(x), _ptr(ws),
-                                          ctypes.c_size_t(ws.numel() if ws is not None else 0), _stream(stream))
+                                          ctypes.c_size_t(ws.numel()), _stream(stream))
         if st != 0:
             raise TDMAError(st, "tdma_plan_autotune")
-        self.workspace_bytes = max(self.workspace_bytes, 0)
-        return self.config
+        cfg = self.config
+        self.workspace_bytes = cfg["workspace_bytes"]
+        if self.workspace_bytes and (self._ws is None or self._ws.numel() < self.workspace_bytes):
+            self._ws = ws if ws.numel() >= self.workspace_bytes else None
+        return cfg
 
     def last_error(self, stream=None):
         """(status, max refinement corrections used); synchronises the stream."""

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <string>
 #include <new>
 #include <tuple>
 #include <vector>
@@ -605,6 +606,140 @@ tdma_status_t build_ragged(tdma_plan_s* p) {
   return TDMA_OK;
 }
 
+// ---- autotuning -----------------------------------------------------------------------
+std::vector<tdma_config_t> tune_candidates(const tdma_desc_t& d, bool allow_tma) {
+  std::vector<tdma_config_t> out;
+  if (d.n <= 0) return out;
+  std::vector<int> Ps;
+  for (int P = 1; P <= 256; P *= 2)
+    if (P == 1 || d.n / P >= 2) Ps.push_back(P);
+  tdma_config_t c{};
+  if (d.precision == TDMA_F32_REFINE) {
+    if (allow_tma && refine_cluster_config(d, 0, c)) out.push_back(c);
+    for (int P : Ps) {
+      tdma_config_t r{};
+      if (!refine_reg_config(d, P, r)) continue;
+      out.push_back(r);
+      if (allow_tma && refine_tma_config(d, r)) out.push_back(r);
+    }
+    for (int P : Ps) {
+      tdma_config_t r{};
+      if (P <= 64 && choose_block(d, P, r)) out.push_back(r);
+    }
+  } else {
+    if (use_thomas_variant(d)) {
+      thomas_config(d, c);
+      out.push_back(c);
+    }
+    for (int P : Ps) {
+      tdma_config_t r{};
+      if (P > 1 && choose_block(d, P, r)) out.push_back(r);
+    }
+  }
+  for (auto& x : out) x.workspace_bytes = (int64_t)workspace_for(d, x);
+  return out;
+}
+
+std::string tune_key(const tdma_desc_t& d) {
+  int lb = 0;
+  for (int64_t v = std::max<int64_t>(1, d.n_lines); v > 1; v >>= 1) ++lb;
+  char buf[160];
+  std::snprintf(buf, sizeof(buf), "p%d n%lld l%d u%d r%d b%d s%d", (int)d.precision, (long long)d.n, lb,
+                d.elem_stride == 1 ? 1 : 0, d.nrhs, d.coef_broadcast, d.diag_shift ? 1 : 0);
+  return buf;
+}
+
+struct TuneChoice { int variant, partitions; };
+std::mutex g_tune_mu;
+std::map<std::string, TuneChoice> g_tune;
+bool g_tune_loaded = false;
+
+// The per-process table, seeded from the TDMA_AUTOTUNE_CACHE file ("key|variant|P" lines).
+std::map<std::string, TuneChoice>& tune_table() {
+  if (!g_tune_loaded) {
+    g_tune_loaded = true;
+    if (const char* path = std::getenv("TDMA_AUTOTUNE_CACHE")) {
+      if (FILE* f = std::fopen(path, "r")) {
+        char line[256];
+        while (std::fgets(line, sizeof(line), f)) {
+          char* bar1 = std::strchr(line, '|');
+          if (!bar1) continue;
+          *bar1 = 0;
+          int v = 0, P = 0;
+          if (std::sscanf(bar1 + 1, "%d|%d", &v, &P) == 2) g_tune[line] = TuneChoice{v, P};
+        }
+        std::fclose(f);
+      }
+    }
+  }
+  return g_tune;
+}
+
+bool cached_config(const tdma_desc_t& d, bool allow_tma, tdma_config_t& c) {
+  TuneChoice t{};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto& tab = tune_table();
+    auto it = tab.find(tune_key(d));
+    if (it == tab.end()) return false;
+    t = it->second;
+  }
+  for (const auto& x : tune_candidates(d, allow_tma))
+    if (x.variant == t.variant && x.partitions == t.partitions) { c = x; return true; }
+  return false;
+}
+
+void remember_config(const tdma_desc_t& d, const tdma_config_t& c) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto& tab = tune_table();
+  const std::string key = tune_key(d);
+  tab[key] = TuneChoice{c.variant, c.partitions};
+  if (const char* path = std::getenv("TDMA_AUTOTUNE_CACHE")) {
+    if (FILE* f = std::fopen(path, "a")) {
+      std::fprintf(f, "%s|%d|%d\n", key.c_str(), c.variant, c.partitions);
+      std::fclose(f);
+    }
+  }
+}
+
+tdma_status_t autotune_impl(tdma_plan_s* p, const void* a, const void* b, const void* c, const void* d, void* x,
+                            void* ws, size_t ws_bytes, cudaStream_t s) {
+  if (p->desc.n == 0 || p->desc.n_lines == 0) return TDMA_OK;
+  const auto cands = tune_candidates(p->desc, p->allow_tma);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TDMA_ERR_CUDA;
+  const tdma_config_t keep = p->cfg;
+  float best = 1e30f;
+  tdma_config_t best_cfg = keep;
+  constexpr int kReps = 3;
+  for (const auto& cand : cands) {
+    if ((size_t)cand.workspace_bytes > ws_bytes || (cand.workspace_bytes > 0 && !ws)) continue;
+    p->cfg = cand;
+    if (prepare_kernel(p) != cudaSuccess) continue;
+    const Args A = make_args(p, a, b, c, d, x, ws);
+    if (launch_forward(p, A, s) != cudaSuccess) continue;  // warm-up
+    cudaEventRecord(e0, s);
+    bool ok = true;
+    for (int r = 0; r < kReps && ok; ++r) ok = launch_forward(p, A, s) == cudaSuccess;
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) { ok = false; }
+    float ms = 0.f;
+    if (ok && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best) {
+      best = ms;
+      best_cfg = cand;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->cfg = best_cfg;
+  if (prepare_kernel(p) != cudaSuccess) { p->cfg = keep; return TDMA_ERR_CUDA; }
+  p->workspace = workspace_for(p->desc, best_cfg);
+  remember_config(p->desc, best_cfg);
+  // the timing runs left their numerical status in the plan; start clean
+  cudaMemsetAsync(p->status, 0, sizeof(DevStatus), s);
+  return cudaStreamSynchronize(s) == cudaSuccess ? TDMA_OK : TDMA_ERR_CUDA;
+}
+
 }  // namespace
 
 extern "C" {
@@ -634,7 +769,10 @@ tdma_status_t tdma_plan_create(tdma_plan_t* plan, const tdma_desc_t* desc, size_
   if (const char* e = std::getenv("TDMA_DISABLE_TMA")) p->allow_tma = !(e[0] == '1');
   if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return TDMA_ERR_CUDA; }
   tdma_config_t c{};
-  if (is_uniform(*desc)) {
+  if (is_uniform(*desc) && desc->partitions == 0 && cached_config(*desc, p->allow_tma, c)) {
+    p->cfg = c;
+    p->workspace = workspace_for(*desc, c);
+  } else if (is_uniform(*desc)) {
     bool ok = false;
     if (desc->precision == TDMA_F32_REFINE) {
       ok = p->allow_tma && refine_cluster_config(*desc, desc->partitions, c);
@@ -684,6 +822,7 @@ tdma_status_t tdma_plan_destroy(tdma_plan_t p) {
 tdma_status_t tdma_plan_get_config(tdma_plan_t p, tdma_config_t* c) {
   if (!p || !c) return TDMA_ERR_INVALID_ARG;
   *c = p->cfg;
+  c->workspace_bytes = (int64_t)p->workspace;
   return TDMA_OK;
 }
 
@@ -737,8 +876,8 @@ tdma_status_t tdma_solve_backward(tdma_plan_t p, const void* a, const void* b, c
 tdma_status_t tdma_plan_autotune(tdma_plan_t p, const void* a, const void* b, const void* c, const void* d,
                                  void* x, void* ws, size_t ws_bytes, void* stream) {
   if (!p) return TDMA_ERR_INVALID_ARG;
-  (void)a; (void)b; (void)c; (void)d; (void)x; (void)ws; (void)ws_bytes; (void)stream;
-  return TDMA_OK;
+  if (p->desc.n_lines > 0 && (!a || !b || !c || !d || !x)) return TDMA_ERR_INVALID_ARG;
+  return autotune_impl(p, a, b, c, d, x, ws, ws_bytes, (cudaStream_t)stream);
 }
 
 }  // extern "C"
