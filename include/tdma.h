@@ -40,6 +40,10 @@
  *   TDMA_F32_REFINE  a, b, c float; d, x, diag_shift double. Sweeps in float, then
  *                    iterative refinement with an extra-precise residual r = d - A x
  *                    until the estimated error is below refine_tol (relative, per line).
+ *   TDMA_F64_REFINE  as TDMA_F64, followed by max_refine_iters (default 1) corrections from a
+ *                    double-double residual r = d - A x, for badly conditioned lines where
+ *                    plain FP64 elimination stops a few 1e-12 short. x must not alias d; the
+ *                    workspace holds one extra right-hand-side buffer.
  *
  * Errors
  *   Every call validates its arguments synchronously and returns a status; nothing aborts.
@@ -68,7 +72,7 @@ typedef enum {
   TDMA_ERR_NOT_CONVERGED = 7  /* device: refinement hit max_refine_iters                  */
 } tdma_status_t;
 
-typedef enum { TDMA_F64 = 0, TDMA_F32 = 1, TDMA_F32_REFINE = 2 } tdma_precision_t;
+typedef enum { TDMA_F64 = 0, TDMA_F32 = 1, TDMA_F32_REFINE = 2, TDMA_F64_REFINE = 3 } tdma_precision_t;
 
 typedef struct tdma_plan_s* tdma_plan_t;
 

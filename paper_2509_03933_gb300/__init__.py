@@ -18,8 +18,9 @@ from . import _build
 __all__ = ["Plan", "solve", "solve_ragged", "solve_backward", "TDMASolve", "line_layout", "TDMAError", "F64", "F32",
            "F32_REFINE", "load_library", "declared_symbols", "sweep_graph"]
 
-F64, F32, F32_REFINE = 0, 1, 2
-_PREC = {"f64": F64, "f32": F32, "f32r": F32_REFINE, F64: F64, F32: F32, F32_REFINE: F32_REFINE}
+F64, F32, F32_REFINE, F64_REFINE = 0, 1, 2, 3
+_PREC = {"f64": F64, "f32": F32, "f32r": F32_REFINE, "f64r": F64_REFINE, F64: F64, F32: F32, F32_REFINE: F32_REFINE,
+         F64_REFINE: F64_REFINE}
 STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported configuration", 3: "workspace too small",
           4: "CUDA runtime error", 5: "zero or non-finite pivot", 6: "bounded wait timed out",
           7: "refinement did not converge"}

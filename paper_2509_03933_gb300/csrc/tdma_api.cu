@@ -20,6 +20,7 @@
 #include "kernels_thomas.cuh"
 #include "kernels_ragged.cuh"
 #include "kernels_backward.cuh"
+#include "kernels_refine64.cuh"
 
 using namespace tdma;
 
@@ -31,6 +32,8 @@ struct tdma_plan_s {
   bool refine_sb64 = true;
   bool allow_tma = true;  // TDMA_DISABLE_TMA=1 loads tiles with ordinary loads instead (diagnostics)
   size_t workspace = 0;
+  int refine64 = 0;        // TDMA_F64_REFINE: corrections after the FP64 solve (desc runs as F64)
+  size_t r_offset = 0;     // TDMA_F64_REFINE: byte offset of the residual buffer in the workspace
   RaggedTables rt{};       // ragged batches: sorted order, groups, scratch bases, work counter
   void* rt_mem = nullptr;  // one device allocation holding the tables
 };
@@ -140,8 +143,10 @@ size_t workspace_for(const tdma_desc_t& d, const tdma_config_t& c) {
 tdma_status_t validate(const tdma_desc_t& d) {
   if (d.n < 0 || d.n_lines < 0) return TDMA_ERR_INVALID_ARG;
   if (d.nrhs != 1 && d.nrhs != 2) return TDMA_ERR_INVALID_ARG;
-  if (d.precision != TDMA_F64 && d.precision != TDMA_F32 && d.precision != TDMA_F32_REFINE)
+  if (d.precision != TDMA_F64 && d.precision != TDMA_F32 && d.precision != TDMA_F32_REFINE &&
+      d.precision != TDMA_F64_REFINE)
     return TDMA_ERR_INVALID_ARG;
+  if (d.precision == TDMA_F64_REFINE && (d.n == 0 || d.max_refine_iters < 0)) return TDMA_ERR_UNSUPPORTED;
   if (d.partitions < 0) return TDMA_ERR_INVALID_ARG;
   if (d.n == 0) {  // ragged
     if (d.n_lines > 0 && (!d.ragged_offsets || !d.ragged_lengths || d.ragged_max_n < 1))
@@ -740,6 +745,42 @@ tdma_status_t autotune_impl(tdma_plan_s* p, const void* a, const void* b, const 
   return cudaStreamSynchronize(s) == cudaSuccess ? TDMA_OK : TDMA_ERR_CUDA;
 }
 
+// TDMA_F64_REFINE: layout of the residual buffer R (compact when coefficients are broadcast).
+Layout refine64_layout(const tdma_desc_t& d) {
+  if (d.coef_broadcast) return Layout{d.n, d.n_lines, d.n_lines, std::max<int64_t>(1, d.n_lines), 1, 0};
+  return Layout{d.n, d.n_lines, d.elem_stride, d.inner_count, d.inner_stride, d.outer_stride};
+}
+size_t refine64_buffer_bytes(const tdma_desc_t& d) {
+  if (d.n_lines == 0) return 0;
+  const Layout L = refine64_layout(d);
+  const int64_t last = d.n_lines - 1;
+  const int64_t max_off = (last / L.ic) * L.os + std::min<int64_t>(last, L.ic - 1) * L.is + (L.n - 1) * L.es;
+  return (size_t)(max_off + 1) * d.nrhs * 8;
+}
+
+cudaError_t solve_refine64(const tdma_plan_s* p, const Args& A, cudaStream_t s) {
+  cudaError_t e = launch_forward(p, A, s);
+  if (e != cudaSuccess) return e;
+  const Layout lr = refine64_layout(p->desc);
+  double* R = (double*)((unsigned char*)A.ws + p->r_offset);
+  const int64_t total = A.lay.n * A.lay.n_lines;
+  const unsigned blocks = (unsigned)((total + 255) / 256);
+  for (int it = 0; it < p->refine64; ++it) {
+    if (p->desc.nrhs == 1) residual64_kernel<1><<<blocks, 256, 0, s>>>(A, lr, R);
+    else residual64_kernel<2><<<blocks, 256, 0, s>>>(A, lr, R);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    Args C = A;  // correction: solve A c = r in place in R
+    C.d = R;
+    C.x = R;
+    C.lay = lr;
+    if ((e = launch_forward(p, C, s)) != cudaSuccess) return e;
+    if (p->desc.nrhs == 1) update64_kernel<1><<<blocks, 256, 0, s>>>(A.lay, lr, (double*)A.x, R);
+    else update64_kernel<2><<<blocks, 256, 0, s>>>(A.lay, lr, (double*)A.x, R);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 }  // namespace
 
 extern "C" {
@@ -766,6 +807,11 @@ tdma_status_t tdma_plan_create(tdma_plan_t* plan, const tdma_desc_t* desc, size_
   tdma_plan_s* p = new (std::nothrow) tdma_plan_s();
   if (!p) return TDMA_ERR_INVALID_ARG;
   p->desc = *desc;
+  if (desc->precision == TDMA_F64_REFINE) {  // configured and launched as FP64, then corrected
+    p->refine64 = desc->max_refine_iters > 0 ? desc->max_refine_iters : 1;
+    p->desc.precision = TDMA_F64;
+    desc = &p->desc;
+  }
   if (const char* e = std::getenv("TDMA_DISABLE_TMA")) p->allow_tma = !(e[0] == '1');
   if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return TDMA_ERR_CUDA; }
   tdma_config_t c{};
@@ -801,6 +847,10 @@ tdma_status_t tdma_plan_create(tdma_plan_t* plan, const tdma_desc_t* desc, size_
       delete p;
       return r;
     }
+  }
+  if (p->refine64) {  // residual / correction buffer after the solver's own workspace
+    p->r_offset = (p->workspace + 255) / 256 * 256;
+    p->workspace = p->r_offset + refine64_buffer_bytes(p->desc);
   }
   if (cudaMalloc(&p->status, sizeof(DevStatus)) != cudaSuccess) { tdma_plan_destroy(p); return TDMA_ERR_CUDA; }
   if (cudaMemset(p->status, 0, sizeof(DevStatus)) != cudaSuccess) { cudaFree(p->status); delete p; return TDMA_ERR_CUDA; }
@@ -845,7 +895,9 @@ tdma_status_t tdma_solve(tdma_plan_t p, const void* a, const void* b, const void
   const tdma_status_t v = check_ptrs(p, a, b, c, d, x, ws, ws_bytes);
   if (v != TDMA_OK) return v;
   const Args A = make_args(p, a, b, c, d, x, ws);
-  const cudaError_t e = launch_forward(p, A, (cudaStream_t)stream);
+  if (p->refine64 && d == x) return TDMA_ERR_INVALID_ARG;  // the residual needs d after the solve
+  const cudaError_t e = p->refine64 ? solve_refine64(p, A, (cudaStream_t)stream)
+                                    : launch_forward(p, A, (cudaStream_t)stream);
   return e == cudaSuccess ? TDMA_OK : TDMA_ERR_CUDA;
 }
 

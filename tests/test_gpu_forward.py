@@ -157,3 +157,28 @@ def test_refine_tile_kernels_z_lines(n, lines):
     assert O.rel_l2(x, ref) <= TOL["f32r"]
     x, ref = _grid_case((n, lines), 0, 17 + n, "f32", 0)
     assert O.rel_l2(x, ref) <= TOL["f32"]
+
+
+@pytest.mark.parametrize("partitions", [1, 4])
+def test_fp64_refine_mode_general_and_badly_conditioned(partitions):
+    # general lines: at least as accurate as plain FP64
+    x, ref = _grid_case((64, 8, 24), 0, 61, "f64", partitions)
+    g = synth.grid_general((64, 8, 24), 0, 61)
+    a, b, c, d = (g[k].cuda() for k in ("a", "b", "c", "d"))
+    xr = tdma.solve(a, b, c, d, axis=0, precision="f64r", partitions=partitions, check=True)
+    assert O.rel_l2(_np_lines(xr, 0), ref) <= 1e-14
+    # the pinned Poisson zero mode (condition number ~1e9) against extended precision
+    pz = synth.poisson_lines(2, 2, 1024, seed=2, device="cuda", rhs=True)
+    dz = pz["d"].view(1024, 4, 2)[:, :1, :]
+    xz = tdma.solve(pz["pin_a"], pz["pin_b"], pz["pin_c"], dz, axis=0, nrhs=2, coef_broadcast=True,
+                    precision="f64r", partitions=partitions, check=True)
+    ref = O.thomas_ext(pz["pin_a"].cpu().numpy(), pz["pin_b"].cpu().numpy(), pz["pin_c"].cpu().numpy(),
+                       dz[:, 0, :].cpu().numpy())
+    assert O.rel_l2(xz[:, 0, :].cpu().numpy(), ref) <= 1e-13
+
+
+def test_fp64_refine_rejects_in_place():
+    g = synth.grid_general((16, 4, 4), 0, 62)
+    a, b, c, d = (g[k].cuda() for k in ("a", "b", "c", "d"))
+    with pytest.raises(tdma.TDMAError):
+        tdma.solve(a, b, c, d, axis=0, precision="f64r", out=d)
