@@ -38,6 +38,9 @@ SEED = 3
 BYTES_F32R = 28.0   # a, b, c float (12) + d double (8) in, x double (8) out
 BYTES_F64 = 40.0    # a, b, c, d double in, x double out
 FP64_OPS_PEAK = 152 * 2 * 2.07e9  # FP64 pipe: 152 SMs x 2 ops/clk x 2.07 GHz (1.25 TFLOP/s, FMA = 2)
+KERNEL_OF_VARIANT = {0: "dc_kernel", 1: "thomas_kernel", 2: "refine_kernel", 3: "ragged_refine_kernel",
+                     4: "refine_reg_kernel", 5: "refine_tma_fixed_kernel", 6: "refine_cluster_kernel",
+                     7: "dc_kernel"}
 
 
 def dist_env():
@@ -132,9 +135,12 @@ def source_sha() -> str:
     return h.hexdigest()[:16]
 
 
-def make_workload(n: int, device):
+def make_workload(n: int, device, ny=None):
+    """The n^3 grid, or its first ny y-rows (same lines, fewer of them) for small profiling runs."""
     import synth
-    g = synth.grid_general((n, n, n), 0, SEED, device=device, fp32_coefficients=True)
+    ny = n if ny is None else ny
+    g = synth.grid_general((n, ny, n), 0, SEED, device=device, fp32_coefficients=True, full_shape=(n, n, n),
+                           origin=(0, 0, 0))
     g.pop("x_true")
     return g
 
@@ -163,6 +169,177 @@ def time_steps(fn, steps, warmup, stream):
     total = t0.elapsed_time(t1)
     per = [s.elapsed_time(e) for s, e in ev]
     return total, per
+
+
+# ---------------------------------------------------------------------------------------------
+# the other workloads (reported under "suite"); each: throughput, plan, error on sampled lines
+
+def _flush_l2(buf):
+    buf.add_(1.0)  # a write larger than L2 between timed launches of small workloads
+
+
+def _timed(fn, steps, warmup, stream, flush=None):
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for s0, s1 in ev:
+        if flush is not None:
+            flush()
+        s0.record(stream)
+        fn()
+        s1.record(stream)
+    torch.cuda.synchronize()
+    per = sorted(a.elapsed_time(b) for a, b in ev)
+    return per[len(per) // 2]
+
+
+def suite_small_grid(stream, hbm_peak, flush):
+    """64^3 grid, 4096 lines of n = 64 along z, FP64, one partition (Thomas) and four."""
+    import oracle
+    import synth
+    import paper_2509_03933_gb300 as tdma
+    g = synth.grid_general((64, 64, 64), 0, 0, device="cuda")
+    a, b, c, d = g["a"], g["b"], g["c"], g["d"]
+    # CPU-baseline leg: the oracle on all 4096 lines (timed), its output also the reference
+    inp = [synth.line_view(t.cpu(), 0).numpy() for t in (a, b, c, d)]
+    t0 = time.perf_counter()
+    ref = oracle.thomas(*inp)
+    dt = time.perf_counter() - t0
+    out = {"cpu_baseline": {"value": 64 ** 3 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": "all 4096 lines"}}
+    for P in (1, 4):
+        plan = tdma.Plan(*tdma.line_layout(d, 0), partitions=P)
+        x = torch.empty_like(d)
+        ms = _timed(lambda: plan.solve(a, b, c, d, x), 50, 5, stream, flush)
+        err = oracle.rel_l2(synth.line_view(x.cpu(), 0).numpy(), ref)
+        U = 64 ** 3
+        out[f"P{P}"] = {"us_per_solve": ms * 1e3, "unknowns_per_s": U / (ms * 1e-3),
+                        "hbm_frac": BYTES_F64 * U / (ms * 1e-3) / 1e9 / hbm_peak, "rel_l2_error": err,
+                        "plan": plan.config, "l2": "flushed between launches"}
+    return out
+
+
+def suite_adi(stream, hbm_peak):
+    """512^3 ADI viscous sweeps x -> y -> z, 8 partitions per line, one CUDA graph per step."""
+    import oracle
+    import synth
+    import paper_2509_03933_gb300 as tdma
+    from scipy.fft import dstn, idstn
+    n, r = 512, 0.5
+    g = synth.grid_adi((n, n, n), seed=1, r=r, device="cuda")
+    a, b, c, d = g["a"], g["b"], g["c"], g["d"]
+    u = d.clone()
+    plans = [tdma.Plan(*tdma.line_layout(u, ax), partitions=8) for ax in (2, 1, 0)]
+    graph = tdma.sweep_graph([(p, (a, b, c, u, u)) for p in plans])
+    per_axis = {}
+    for name, p in zip("xyz", plans):
+        per_axis[name] = _timed(lambda: p.solve(a, b, c, u, u), 10, 3, stream)
+    ms = _timed(graph.replay, 10, 3, stream)
+    u.copy_(d)
+    graph.replay()
+    torch.cuda.synchronize()
+    lam = 1 + 4 * r * np.sin(np.pi * np.arange(1, n + 1) / (2 * (n + 1))) ** 2
+    L = lam[:, None, None] * lam[None, :, None] * lam[None, None, :]
+    ref = idstn(dstn(d.cpu().numpy(), type=1, workers=-1) / L, type=1, workers=-1)
+    U = 3 * n ** 3
+    return {"ms_per_xyz_step": ms, "ms_per_sweep": per_axis, "unknowns_per_s": U / (ms * 1e-3),
+            "hbm_frac": BYTES_F64 * U / (ms * 1e-3) / 1e9 / hbm_peak,
+            "rel_l2_error_vs_closed_form": oracle.rel_l2(u.cpu().numpy(), ref),
+            "plans": [p.config for p in plans], "launches_per_step": 3}
+
+
+def suite_poisson(stream, hbm_peak):
+    """1024^3 wavenumber lines along z: broadcast coefficients + per-line shift, complex RHS
+    (2 interleaved real RHS), zero mode pinned and solved by its own one-line plan."""
+    import oracle
+    import synth
+    import paper_2509_03933_gb300 as tdma
+    n = 1024
+    p = synth.poisson_lines(n, n, n, seed=2, device="cuda")
+    d = p["d"]
+    x = torch.empty_like(d)
+    d3, x3 = d.view(n, n * n, 2), x.view(n, n * n, 2)
+    shift = p["shift"][1:].contiguous()
+    rng = np.random.default_rng(2)
+    modes = np.unique(np.concatenate([[0, 1, n, n + 1, n * n - 1], rng.choice(n * n, 59, False)]))
+    ha, hc, hb0, hs = (p[k].cpu().numpy() for k in ("a", "c", "b0", "shift"))
+    # CPU-baseline leg: the extended-precision oracle on the sampled modes (timed)
+    t0 = time.perf_counter()
+    refs = []
+    for m in modes:
+        if m == 0:
+            A, B, C = (p[k].cpu().numpy() for k in ("pin_a", "pin_b", "pin_c"))
+        else:
+            A, B, C = ha, hb0 + hs[m], hc
+        refs.append(oracle.thomas_ext(A, B, C, d3[:, m, :].cpu().numpy()))
+    refs = np.concatenate(refs)
+    dt = time.perf_counter() - t0
+    out = {"cpu_baseline": {"value": len(modes) * n / dt, "unit": "complex unknowns/s", "cores": 1,
+                            "kind": "oracle (extended precision)", "sample": f"{len(modes)} modes x {n}"}}
+    for prec in ("f64", "f64r"):
+        main = tdma.Plan(*tdma.line_layout(d3[:, 1:, :], 0, nrhs=2), nrhs=2, coef_broadcast=True, diag_shift=shift,
+                         precision=prec)
+        zero = tdma.Plan(*tdma.line_layout(d3[:, :1, :], 0, nrhs=2), nrhs=2, coef_broadcast=True, precision=prec)
+
+        def step():
+            main.solve(p["a"], p["b0"], p["c"], d3[:, 1:, :], x3[:, 1:, :])
+            zero.solve(p["pin_a"], p["pin_b"], p["pin_c"], d3[:, :1, :], x3[:, :1, :])
+        ms = _timed(step, 8, 3, stream)
+        got = np.concatenate([x3[:, m, :].cpu().numpy() for m in modes])
+        U = n ** 3  # complex unknowns
+        out[prec] = {"ms_per_step": ms, "complex_unknowns_per_s": U / (ms * 1e-3),
+                     "hbm_frac": 32.0 * U / (ms * 1e-3) / 1e9 / hbm_peak,
+                     "rel_l2_error_vs_extended": oracle.rel_l2(got, refs), "modes_checked": int(len(modes)),
+                     "plan": main.config}
+        del main, zero
+    return out
+
+
+def suite_ragged(stream, hbm_peak):
+    """20000 lines, n log-uniform in [16, 16384], packed; FP32+refinement and FP64 in one
+    persistent launch each; backward for loss = sum(w * x), w ~ N(0, 1)."""
+    import oracle
+    import synth
+    import paper_2509_03933_gb300 as tdma
+    lengths = synth.ragged_lengths(20000, 16, 16384, seed=4)
+    r = synth.ragged_general(lengths, 4, device="cuda", fp32_coefficients=True)
+    U = r["total"]
+    rng = np.random.default_rng(4)
+    lines = np.unique(np.concatenate([np.argsort(-lengths)[:10], rng.choice(20000, 300, replace=False)]))
+    offs, lens = r["offsets"].cpu().numpy(), r["lengths"].cpu().numpy()
+    ha, hb, hc, hd = (r[k].cpu().numpy() for k in ("a", "b", "c", "d"))
+    # CPU-baseline leg: the oracle on the sampled lines (timed), its output also the reference
+    t0 = time.perf_counter()
+    ref = oracle.thomas_ragged(ha, hb, hc, hd, offs, lens, lines=lines)
+    dt = time.perf_counter() - t0
+    want = np.concatenate([ref[l] for l in sorted(ref)])
+    w = synth.normal(4, synth.AID["w"], torch.arange(U, device="cuda"))
+    out = {"lines": 20000, "unknowns": int(U),
+           "cpu_baseline": {"value": int(want.size) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": f"{len(ref)} lines ({int(want.size)} unknowns), longest 10 + random"}}
+    for prec, keys, fbytes, bbytes in (("f32r", ("a32", "b32", "c32"), BYTES_F32R, 8.0 * 3 + 4 * 3 + 8 * 2),
+                                       ("f64", ("a", "b", "c"), BYTES_F64, 72.0)):
+        a, b, c = (r[k] for k in keys)
+        d = r["d"]
+        x, plan = tdma.solve_ragged(a, b, c, d, r["offsets"], r["lengths"], precision=prec)
+        ms = _timed(lambda: plan.solve(a, b, c, d, x), 10, 3, stream)
+        st, iters = plan.last_error()
+        xs = x.cpu().numpy()
+        got = np.concatenate([xs[offs[l]:offs[l] + lens[l]] for l in sorted(ref)])
+        ga, gb, gc, gd = (torch.empty_like(a), torch.empty_like(b), torch.empty_like(c), torch.empty_like(x))
+        msb = _timed(lambda: plan.backward(a, b, c, x, w, ga, gb, gc, gd), 10, 3, stream)
+        gdh, wh = gd.cpu().numpy(), w.cpu().numpy()
+        l0 = sorted(ref)[:50]
+        rg = [oracle.adjoint_grads(ha[o:o + n_], hb[o:o + n_], hc[o:o + n_], xs[o:o + n_], wh[o:o + n_])[3]
+              for o, n_ in ((offs[l], lens[l]) for l in l0)]
+        lam_err = oracle.rel_l2(np.concatenate([gdh[offs[l]:offs[l] + lens[l]] for l in l0]), np.concatenate(rg))
+        out[prec] = {"forward_ms": ms, "unknowns_per_s": U / (ms * 1e-3),
+                     "hbm_frac": fbytes * U / (ms * 1e-3) / 1e9 / hbm_peak, "rel_l2_error": oracle.rel_l2(got, want),
+                     "status": st, "corrections_max": iters, "backward_ms": msb,
+                     "backward_unknowns_per_s": U / (msb * 1e-3),
+                     "backward_lambda_rel_l2_error": lam_err, "plan": plan.config}
+    return out
 
 
 def run_reference(args):
@@ -204,11 +381,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1024)
+    ap.add_argument("--ny", type=int, default=0, help="solve only the first ny y-rows (profiling runs)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-lines", type=int, default=32768, help="lines in the CPU oracle sample")
     ap.add_argument("--ref-lines", type=int, default=4096, help="lines per reference-arm step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-suite", action="store_true", help="skip the other workloads")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -225,13 +404,15 @@ def main():
 
     dev = torch.device("cuda", local if ws > 1 else 0)
     n = args.n
-    U = n ** 3
-    g = make_workload(n, dev)
+    ny = args.ny if args.ny > 0 else n
+    U = n * ny * n
+    g = make_workload(n, dev, ny)
     a32, b32, c32, d = g["a32"], g["b32"], g["c32"], g["d"]
     x = torch.empty_like(d)
     stream = torch.cuda.current_stream()
-    plan_r = tdma.Plan(n, n * n, n * n, n * n, 1, 0, precision="f32r")
-    plan_d = tdma.Plan(n, n * n, n * n, n * n, 1, 0, precision="f64")
+    lay = tdma.line_layout(d, 0)
+    plan_r = tdma.Plan(*lay, precision="f32r")
+    plan_d = tdma.Plan(*lay, precision="f64")
 
     def barrier():
         if ws > 1:
@@ -264,17 +445,18 @@ def main():
     hbm_peak, peak_kind = peaks()
     kern_ms = sorted(per_r)[len(per_r) // 2]
     achieved = BYTES_F32R * U / (kern_ms * 1e-3) / 1e9
-    trec = traffic_record("refine_kernel")
+    kname = KERNEL_OF_VARIANT.get(plan_r.config["variant"], "refine_kernel")
+    trec = traffic_record(kname)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
             "traffic": (trec["dram_bytes"] * (U / trec["unknowns"])) if trec else None,
             "peak_kind": f"{peak_kind} (STREAM-style copy)", "algorithmic_bytes_per_unknown": BYTES_F32R,
-            "kernel": "refine_kernel", "kernel_ms": kern_ms}
+            "kernel": kname, "kernel_ms": kern_ms}
 
     # ---------------- CPU oracle on a bounded sample (also the per-result error check)
     cpu = None
     err = {}
     import oracle
-    ys = max(1, args.cpu_lines // n)
+    ys = min(ny, max(1, args.cpu_lines // n))
     oa, ob, oc, od = sample_oracle_lines(g, ys)
     if not args.no_cpu:
         t0 = time.perf_counter()
@@ -314,16 +496,34 @@ def main():
                "d2h_bytes_per_step": x.numel() * x.element_size(), "steps": args.e2e_steps,
                "ms_per_step": tot / args.e2e_steps}
 
+    cfg_d = plan_d.config
+    suite = None
+    if not args.no_suite:
+        plan_d = x_d = g = a = b = c = a32 = b32 = c32 = d = x = x_r = None  # release the 1024^3 arrays
+        torch.cuda.empty_cache()
+        flushbuf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
+        suite = {}
+        for name, fn in (("grid64_z_f64", lambda: suite_small_grid(stream, hbm_peak, lambda: _flush_l2(flushbuf))),
+                         ("adi512_xyz_f64_P8", lambda: suite_adi(stream, hbm_peak)),
+                         ("poisson1024_z_complex", lambda: suite_poisson(stream, hbm_peak)),
+                         ("ragged20000", lambda: suite_ragged(stream, hbm_peak))):
+            try:
+                suite[name] = fn()
+            except Exception as exc:  # report, keep the headline line
+                suite[name] = {"error": f"{type(exc).__name__}: {exc}"}
+            torch.cuda.empty_cache()
+
     cfg_r = plan_r.config
-    fp64_ops = 15.0  # FP64-pipe instructions per unknown of the fused FP64 kernel
+    # FP64-pipe instructions per unknown: Thomas 9 (5 + reciprocal), partitioned sweep 15
+    fp64_ops = 9.0 if cfg_d["variant"] == 1 else 15.0
     out = {
         "metric": METRIC, "value": ws * U / (ms_r * 1e-3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_r, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32 sweeps + extra-precise residual, f64 in/out", "data": "synthetic",
-        "config": {"workload": f"general-coefficient {n}^3 grid, {n * n} lines of n={n} along z (stride {n * n}), "
-                               f"seed {SEED}, FP32-representable coefficients", "lines": n * n, "n": n,
+        "config": {"workload": f"general-coefficient {n}x{ny}x{n} grid, {n * ny} lines of n={n} along z "
+                               f"(stride {n * ny}), seed {SEED}, FP32-representable coefficients", "lines": n * ny, "n": n,
                    "l2": "inputs (30 GB) larger than L2", "plan": cfg_r},
-        "fp64": {"value": ws * U / (ms_d * 1e-3), "unit": UNIT, "ms_per_step": ms_d, "plan": plan_d.config,
+        "fp64": {"value": ws * U / (ms_d * 1e-3), "unit": UNIT, "ms_per_step": ms_d, "plan": cfg_d,
                  "roofline": {"bound": "alu", "achieved": fp64_ops * U / (ms_d * 1e-3) / 1e9,
                               "peak": FP64_OPS_PEAK / 1e9, "unit": "Gop/s (FP64 pipe)",
                               "frac": fp64_ops * U / (ms_d * 1e-3) / FP64_OPS_PEAK,
@@ -334,6 +534,7 @@ def main():
         "e2e": e2e,
         "clocks": clk.summary(),
         "gpu_launches": args.steps,
+        "suite": suite,
         "impl": "ours",
     }
     print(json.dumps(out), flush=True)
