@@ -50,6 +50,22 @@ def dist_env():
     return ws, rank, local
 
 
+def shard_range(n_units: int, rank: int, world: int):
+    """Contiguous share [lo, hi) of n_units independent units (lines, or whole grids) for a rank."""
+    return n_units * rank // world, n_units * (rank + 1) // world
+
+
+def reduce_max(value: float, device) -> float:
+    """Maximum of a per-rank value over all ranks (any torch.distributed backend); the value itself
+    when not distributed."""
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(value)
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -424,18 +440,14 @@ def main():
         total_r, per_r = time_steps(lambda: plan_r.solve(a32, b32, c32, d, x), args.steps, args.warmup, stream)
     barrier()
     st, iters = plan_r.last_error()
-    ms_r = total_r / args.steps
-    if ws > 1:
-        t = torch.tensor([ms_r], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_r = float(t.item())
+    ms_r = reduce_max(total_r / args.steps, dev)  # the slowest rank sets the job's time
     x_r = x.clone() if rank == 0 else None
 
     # ---------------- the plain FP64 solve of the same problem
     a, b, c = g["a"], g["b"], g["c"]
     total_d, per_d = time_steps(lambda: plan_d.solve(a, b, c, d, x), max(3, args.steps // 3), args.warmup, stream)
     st_d, _ = plan_d.last_error()
-    ms_d = total_d / max(3, args.steps // 3)
+    ms_d = reduce_max(total_d / max(3, args.steps // 3), dev)
     x_d = x
 
     if rank != 0:
