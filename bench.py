@@ -40,7 +40,7 @@ BYTES_F64 = 40.0    # a, b, c, d double in, x double out
 FP64_OPS_PEAK = 152 * 2 * 2.07e9  # FP64 pipe: 152 SMs x 2 ops/clk x 2.07 GHz (1.25 TFLOP/s, FMA = 2)
 KERNEL_OF_VARIANT = {0: "dc_kernel", 1: "thomas_kernel", 2: "refine_kernel", 3: "ragged_refine_kernel",
                      4: "refine_reg_kernel", 5: "refine_tma_fixed_kernel", 6: "refine_cluster_kernel",
-                     7: "dc_kernel"}
+                     7: "dc_kernel", 8: "refine_tree_kernel"}
 
 
 def dist_env():

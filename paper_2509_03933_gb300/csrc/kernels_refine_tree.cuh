@@ -1,0 +1,489 @@
+// FP32 storage + refinement with each line spread over a thread-block cluster; Stage B as a
+// log-depth merge tree over warp lanes and then over the cluster's CTAs.
+//
+// Geometry. A cluster of C CTAs owns 32 adjacent lines. CTA r holds rows [r n/C, (r+1) n/C) of
+// all of them as 8 partitions of M rows (n = 8 C M). Warp w holds lines 4w..4w+3 and lane
+// 4p + jj holds partition p of line 4w + jj: the 8 partitions of a line sit in 8 lanes of one
+// warp, so the CTA-level part of the reduced solve needs shuffles only, no CTA barrier.
+// The tile {32 lines, 8 partitions, M rows} of a, b, c (float) and d (double, two boxes of 16
+// lines) arrives by TMA with the 128-byte swizzle: for a fixed row, the 32 lanes of a warp then
+// read 32 distinct banks.
+//
+// Stage A (Section 2.1, Algorithm 1) per partition is the modified Thomas sweep used by the other
+// kernels; it leaves, for the partition's first and last unknowns x_s and x_e, the two rows
+//     x_s + S u + U x_e = H,        alpha x_s + x_e + Gamma v = Delta,
+// with u = x_{s-1} and v = x_{e+1} the outside neighbours. Solving the 2 x 2 system gives the
+// block form  x_s = p1 + q1 u + r1 v,  x_e = p2 + q2 u + r2 v.  Two adjacent blocks L, R merge
+// into one by eliminating the unknowns on either side of their boundary, y = x_{e(L)} and
+// z = x_{s(R)}:  y = L.p2 + L.q2 u + L.r2 z,  z = R.p1 + R.q1 y + R.r1 v.  Three merge levels
+// over the lanes of a line give the CTA's block (the paper's A2B); each CTA pushes it into the
+// shared memory of every CTA of the cluster (DSMEM stores), one cluster barrier, and every CTA
+// merges the C blocks of the line the same way. The line ends have no outside neighbours
+// (u = v = 0), so the down-sweep of the two trees hands every partition its own u and v (the
+// paper's B2C), and Stage C is x_t = delta_t - alpha_t x_s - gamma_t x_{t+1}.
+//
+// Refinement (the FP32 + refinement path): pass 0 solves with the float part of d; pass 1
+// recomputes the same factors and solves for the extra-precise residual r = d - A x_0 (float
+// pairs); x = x_0 + dx goes to global memory in FP64. The stop rule (per line, on the line's
+// max norms) needs one more exchange; later passes, rare, re-read x from global memory.
+// Per tile there are three cluster barriers: pass 0 blocks, pass 1 blocks, pass 1 norms.
+#pragma once
+#include <cooperative_groups.h>
+#include "layout.cuh"
+#include "tma.cuh"
+#include "kernels_refine.cuh"
+
+namespace tdma {
+
+constexpr int kTreeLines = 32;               // lines per cluster
+constexpr int kTreeParts = 8;                // partitions per CTA
+constexpr int kTreeSlotPitch = 7 * 32 + 4;   // per source CTA: 7 fields x 32 lines (+4: banks)
+constexpr int kTreeNormPitch = 2 * 32 + 4;   // per source CTA: 2 fields x 32 lines
+
+// x_s = p1 + q1 u + r1 v and x_e = p2 + q2 u + r2 v for a row range [s, e] of a line.
+struct Blk { float p1, q1, r1, p2, q2, r2; };
+// one interior unknown of a merge as an affine function of the merged block's (u, v)
+struct Aff { float p, q, r; };
+
+TDMA_DEV Blk shfl_xor_blk(const Blk& b, int m) {
+  return {__shfl_xor_sync(~0u, b.p1, m), __shfl_xor_sync(~0u, b.q1, m), __shfl_xor_sync(~0u, b.r1, m),
+          __shfl_xor_sync(~0u, b.p2, m), __shfl_xor_sync(~0u, b.q2, m), __shfl_xor_sync(~0u, b.r2, m)};
+}
+
+// Block form of one partition from its two Stage A rows (see the header).
+TDMA_DEV Blk part_block(float S, float U, float H, float al, float Ga, float De) {
+  const float id = rcp(fmaf(-U, al, 1.f));
+  return {id * fmaf(-U, De, H), -S * id, id * (U * Ga), id * fmaf(-al, H, De), id * (al * S), -Ga * id};
+}
+
+// Merge L = [s1, e1] and R = [e1 + 1, e2]. From y = L.p2 + L.q2 u + L.r2 z and
+// z = R.p1 + R.q1 y + R.r1 v: y (1 - L.r2 R.q1) = L.p2 + L.r2 R.p1 + L.q2 u + L.r2 R.r1 v, then
+// z from y; the merged rows are L's first row with z and R's last row with y substituted.
+// `keep` receives the unknown that becomes this lane's neighbour on the way down: y for a lane
+// inside R (its u), z for a lane inside L (its v).
+TDMA_DEV Blk merge(const Blk& L, const Blk& R, bool in_right, Aff& keep) {
+  const float D = rcp(fmaf(-L.r2, R.q1, 1.f));
+  const float py = D * fmaf(L.r2, R.p1, L.p2);
+  const float qy = D * L.q2;
+  const float ry = D * (L.r2 * R.r1);
+  const float pz = fmaf(R.q1, py, R.p1);
+  const float qz = R.q1 * qy;
+  const float rz = fmaf(R.q1, ry, R.r1);
+  keep = in_right ? Aff{py, qy, ry} : Aff{pz, qz, rz};
+  return {fmaf(L.r1, pz, L.p1), fmaf(L.r1, qz, L.q1), L.r1 * rz, fmaf(R.q2, py, R.p2), R.q2 * qy, fmaf(R.q2, ry, R.r2)};
+}
+
+// Up-sweep over 2^LV consecutive blocks held by lanes whose index bits 2.. carry the block
+// number g; every lane of a group ends with the group's merged block.
+template <int LV>
+TDMA_DEV Blk tree_up(Blk b, int g, Aff (&keep)[3]) {
+#pragma unroll
+  for (int l = 0; l < LV; ++l) {
+    const Blk o = shfl_xor_blk(b, 4 << l);
+    const bool in_right = (g >> l) & 1;
+    b = merge(in_right ? o : b, in_right ? b : o, in_right, keep[l]);
+  }
+  return b;
+}
+// Down-sweep: (u, v) of the whole group in, (u, v) of this lane's block out.
+template <int LV>
+TDMA_DEV void tree_down(float& u, float& v, int g, const Aff (&keep)[3]) {
+#pragma unroll
+  for (int l = LV - 1; l >= 0; --l) {
+    const float val = fmaf(keep[l].q, u, fmaf(keep[l].r, v, keep[l].p));
+    if ((g >> l) & 1) u = val; else v = val;
+  }
+}
+
+// Cluster level: the merges keep both interior unknowns, so that the down-sweep also gives each
+// block the values of its own first and last unknowns exactly as its neighbours see them (the
+// lowest level that sets u = y also gives x_s = z; the one that sets v = z gives x_e = y).
+struct Mrg { Aff y, z; };
+template <int LV>
+TDMA_DEV void tree_up_full(Blk b, int g, Mrg (&keep)[3]) {
+#pragma unroll
+  for (int l = 0; l < LV; ++l) {
+    const Blk o = shfl_xor_blk(b, 4 << l);
+    const bool in_right = (g >> l) & 1;
+    const Blk& L = in_right ? o : b;
+    const Blk& R = in_right ? b : o;
+    const float D = rcp(fmaf(-L.r2, R.q1, 1.f));
+    Aff y, z;
+    y.p = D * fmaf(L.r2, R.p1, L.p2);
+    y.q = D * L.q2;
+    y.r = D * (L.r2 * R.r1);
+    z.p = fmaf(R.q1, y.p, R.p1);
+    z.q = R.q1 * y.q;
+    z.r = fmaf(R.q1, y.r, R.r1);
+    keep[l] = Mrg{y, z};
+    b = Blk{fmaf(L.r1, z.p, L.p1), fmaf(L.r1, z.q, L.q1), L.r1 * z.r, fmaf(R.q2, y.p, R.p2), R.q2 * y.q, fmaf(R.q2, y.r, R.r2)};
+  }
+}
+template <int LV>
+TDMA_DEV void tree_down_full(float& u, float& v, float& xs, float& xe, int g, const Mrg (&keep)[3]) {
+#pragma unroll
+  for (int l = LV - 1; l >= 0; --l) {
+    const float y = fmaf(keep[l].y.q, u, fmaf(keep[l].y.r, v, keep[l].y.p));
+    const float z = fmaf(keep[l].z.q, u, fmaf(keep[l].z.r, v, keep[l].z.p));
+    if ((g >> l) & 1) { u = y; xs = z; } else { v = z; xe = y; }
+  }
+}
+
+// ---- cluster helpers (inline PTX) ------------------------------------------------------
+TDMA_DEV uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+TDMA_DEV void cluster_arrive_relaxed() { asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory"); }
+TDMA_DEV void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+TDMA_DEV void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+// shared::cluster address of `p` in the shared memory of CTA `rank`
+TDMA_DEV uint32_t map_rank(const void* p, int rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+TDMA_DEV void st_cluster(uint32_t addr, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+}
+TDMA_DEV void st_cluster(uint32_t addr, unsigned v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+// Norms travel as the bit patterns of |v|: for non-negative floats the unsigned order is the
+// numeric order, and NaN (above +inf) survives a max reduction, so one test after the reduction
+// (bits >= 0x7f800000) finds any non-finite value.
+TDMA_DEV unsigned abs_bits(float v) { return __float_as_uint(v) & 0x7fffffffu; }
+TDMA_DEV bool bits_finite(unsigned b) { return b < 0x7f800000u; }
+// maximum over the 8 lanes (bits 2..4 of the lane index) that hold one line
+TDMA_DEV unsigned line_max(unsigned v) {
+#pragma unroll
+  for (int l = 0; l < 3; ++l) v = max(v, __shfl_xor_sync(~0u, v, 4 << l));
+  return v;
+}
+
+template <int M, int C>
+__host__ __device__ constexpr size_t refine_tree_smem_bytes() {
+  // a, b, c tiles (M x 8 x 32 floats each), d (two M x 8 x 16 double boxes), block slots and
+  // norm slots (double-buffered by pass parity), 1 KB for the swizzle alignment
+  return 1024 + 5 * (size_t)M * 1024 + 2 * (size_t)C * kTreeSlotPitch * 4 + 2 * (size_t)C * kTreeNormPitch * 4;
+}
+
+// Stage B for one pass: CTA tree, exchange of the CTA blocks, cluster tree, down-sweeps.
+// `extra` (a per-line norm of this CTA, as abs_bits) travels with the block; `extra_max` is its
+// maximum over the cluster. Returns this partition's (u, v) and this CTA's first and last
+// unknowns of the line as the neighbouring CTAs see them (xs_c, xe_c; every CTA computes the
+// cluster tree from the same data in the same order, so the values agree bit for bit).
+template <int C>
+TDMA_DEV void tree_stage_b(const Blk& b, unsigned extra, float* slots, int rank, int p, int jj, int j, float& u,
+                           float& v, float& xs_c, float& xe_c, unsigned& extra_max) {
+  constexpr int LC = C == 8 ? 3 : (C == 4 ? 2 : 1);
+  Aff kc[3];
+  const Blk B = tree_up<3>(b, p, kc);
+  if (p < C) {
+    const uint32_t dst = map_rank(slots + rank * kTreeSlotPitch + j, p);
+    st_cluster(dst, B.p1);
+    st_cluster(dst + 128, B.q1);
+    st_cluster(dst + 256, B.r1);
+    st_cluster(dst + 384, B.p2);
+    st_cluster(dst + 512, B.q2);
+    st_cluster(dst + 640, B.r2);
+    st_cluster(dst + 768, extra);
+  }
+  cluster_arrive();
+  cluster_wait();
+  const float* s = slots + (p & (C - 1)) * kTreeSlotPitch + j;
+  extra_max = line_max(__float_as_uint(s[192]));
+  float uq = 0.f, vq = 0.f, xsq = 0.f, xeq = 0.f;
+  {
+    Mrg kq[3];
+    tree_up_full<LC>(Blk{s[0], s[32], s[64], s[96], s[128], s[160]}, p, kq);
+    tree_down_full<LC>(uq, vq, xsq, xeq, p, kq);  // the line ends have u = v = 0
+  }
+  const int src = (rank << 2) | jj;
+  u = __shfl_sync(~0u, uq, src);
+  v = __shfl_sync(~0u, vq, src);
+  xs_c = __shfl_sync(~0u, xsq, src);
+  xe_c = __shfl_sync(~0u, xeq, src);
+  tree_down<3>(u, v, p, kc);
+}
+
+// Per-line maxima over the cluster, in two halves so that work can go between the barrier's
+// arrive and wait: push this CTA's (dx, xm) of line j (already reduced over the line's lanes)
+// to every CTA and arrive; then wait and reduce over the C sources.
+template <int C>
+TDMA_DEV void tree_norms_push(unsigned dx, unsigned xm, unsigned* norms, int rank, int p, int j) {
+  if (p < C) {
+    const uint32_t dst = map_rank(norms + rank * kTreeNormPitch + j, p);
+    st_cluster(dst, dx);
+    st_cluster(dst + 128, xm);
+  }
+  cluster_arrive();
+}
+template <int C>
+TDMA_DEV void tree_norms_read(unsigned& dx, unsigned& xm, const unsigned* norms, int p, int j) {
+  cluster_wait();
+  const unsigned* s = norms + (p & (C - 1)) * kTreeNormPitch + j;
+  dx = line_max(s[0]);
+  xm = line_max(s[32]);
+}
+
+// r = d - (a xm + b x + c xp) for float x values and d = dh + dl, as if in twice the float
+// precision: FMA TwoProduct of the three products and TwoSum of the first two subtractions,
+// whose results are of the size of x. The last subtraction is either exact (Sterbenz: both
+// operands within a factor two) or already of the size of the residual, so it is rounded once.
+TDMA_DEV float residual_f(float a, float b, float c, float dh, float dl, float xm, float x, float xp) {
+  const ff p1 = two_prod(b, x), p2 = two_prod(a, xm), p3 = two_prod(c, xp);
+  const ff s1 = two_sum(dh, -p1.h);
+  const ff s2 = two_sum(s1.h, -p2.h);
+  const float s3 = __fsub_rn(s2.h, p3.h);
+  const float err = __fsub_rn(__fadd_rn(__fadd_rn(dl, s1.l), s2.l), __fadd_rn(__fadd_rn(p1.l, p2.l), p3.l));
+  return __fadd_rn(s3, err);
+}
+
+// Stage A state of one partition of M rows (modified Thomas, row-1 relation summed forward).
+template <int M>
+struct Sweep {
+  float al[M], ga[M], de[M];  // rows 1..M-2
+  float alpha = -1.f, gamma = 0.f, delta = 0.f, F = 0.f, G = 0.f, Q = 1.f;
+  float a0 = 0.f, b0 = 1.f, c0 = 0.f, h0 = 0.f;
+  // row t (a compile-time constant after unrolling) with right-hand side rhs
+  TDMA_DEV void row(int t, float a, float b, float c, float rhs) {
+    if (t == 0) {
+      a0 = a; b0 = b; c0 = c; h0 = rhs;
+      return;
+    }
+    const float r = rcp(fmaf(-a, gamma, b));
+    const float ar = a * r;
+    alpha = -ar * alpha;
+    gamma = c * r;
+    delta = fmaf(r, rhs, -ar * delta);
+    if (t <= M - 2) {
+      al[t] = alpha; ga[t] = gamma; de[t] = delta;
+      G = fmaf(Q, alpha, G);
+      F = fmaf(Q, delta, F);
+      Q = -Q * gamma;
+    }
+  }
+  // row 0 becomes x_s + S u + U x_e = H with x_1 = F - G x_s + Q x_e substituted
+  TDMA_DEV Blk block() const {
+    const float rho = rcp(fmaf(-c0, G, b0));
+    return part_block(rho * a0, rho * (c0 * Q), rho * fmaf(-c0, F, h0), alpha, gamma, delta);
+  }
+  // the partition's first and last unknowns for its outside neighbours (u, v)
+  TDMA_DEV static float first(const Blk& b, float u, float v) { return fmaf(b.q1, u, fmaf(b.r1, v, b.p1)); }
+  TDMA_DEV static float last(const Blk& b, float u, float v) { return fmaf(b.q2, u, fmaf(b.r2, v, b.p2)); }
+  // Stage C from the partition's first and last unknowns
+  TDMA_DEV void solve(float xs, float xe, float (&x)[M]) const {
+    x[0] = xs;
+    x[M - 1] = xe;
+    float xn = xe;
+#pragma unroll
+    for (int t = M - 2; t >= 1; --t) {
+      xn = fmaf(-ga[t], xn, fmaf(-al[t], xs, de[t]));
+      x[t] = xn;
+    }
+  }
+};
+
+// Per-line stop rule of the refinement: rho |dx|_inf <= tol |x|_inf with the contraction
+// estimate rho = |dx| / |dx_prev| (|dx_0| = |x_0|). A non-finite norm ends the line with status 5.
+TDMA_DEV bool tree_line_done(unsigned gdx, unsigned gxm, unsigned& prev, bool active, float tol, bool reporter,
+                             DevStatus* st) {
+  if (!active) return true;
+  if (!(bits_finite(gdx) && bits_finite(gxm))) {
+    if (reporter) report_error(st, 5);
+    return true;
+  }
+  const float dxn = __uint_as_float(gdx), xn = __uint_as_float(gxm), pv = __uint_as_float(prev);
+  prev = gdx;
+  const float ratio = pv > 0.f ? dxn / pv : 0.f;
+  return ratio * dxn <= tol * xn || dxn == 0.f;
+}
+
+template <int M, int C>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
+    refine_tree_kernel(const Args A, const __grid_constant__ TmaMaps maps) {
+  static_assert(C == 2 || C == 4 || C == 8, "cluster size");
+  static_assert(M >= 3, "rows per partition");
+  extern __shared__ __align__(16) unsigned char smem_raw[];  // aligned to 1 KB below
+  __shared__ __align__(8) uint64_t bar;
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, p = lane >> 2, jj = lane & 3;
+  const int j = 4 * w + jj;  // line within the cluster's 32
+  const int rank = (int)cluster_rank();
+  const int64_t line0 = (int64_t)(blockIdx.x / C) * kTreeLines;
+  const bool active = line0 + j < A.lay.n_lines;
+  const int kg = rank * kTreeParts + p;  // partition index within the line
+  const bool first_part = kg == 0, last_part = kg == C * kTreeParts - 1;
+  const bool reporter = rank == 0 && p == 0 && active;  // one thread per line reports
+
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                                         ~static_cast<uintptr_t>(1023));
+  float* ta = reinterpret_cast<float*>(base);
+  float* tb = ta + M * 256;
+  float* tc = tb + M * 256;
+  double* td = reinterpret_cast<double*>(tc + M * 256);
+  float* slots = reinterpret_cast<float*>(td + M * 256);
+  unsigned* norms = reinterpret_cast<unsigned*>(slots + 2 * C * kTreeSlotPitch);
+  // This thread's element of row 0 in each tile under the 128-byte swizzle (16-byte chunk index
+  // XOR 128-byte row index mod 8; the row index mod 8 is the partition p). Row t is 1 KB further.
+  const int fo = p * 32 + (((w ^ p) & 7) << 2) + jj;
+  const float* ra = ta + fo;
+  const float* rb = tb + fo;
+  const float* rc = tc + fo;
+  double* rd = td + (w >> 2) * (M * 128) + p * 16 + ((((w & 3) * 2 + (jj >> 1)) ^ p) << 1) + (jj & 1);
+  float2* rd2 = reinterpret_cast<float2*>(rd);  // d as a float pair, written in place by pass 0
+
+  const int64_t es = A.lay.es;
+  double* px = (double*)A.x + A.lay.off(active ? line0 + j : 0) + (int64_t)kg * M * es;
+  const int64_t ic = A.lay.ic;
+  const int c_in = (int)(line0 % ic), c_out = (int)(line0 / ic);
+
+  if (tid == 0) {
+    mbar_init(&bar, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  cluster_arrive_relaxed();  // this CTA runs; the matching wait precedes the first DSMEM store
+  if (tid == 0) {
+    mbar_arrive_expect_tx(&bar, 5u * M * 1024u);
+    tma_load_4d(ta, &maps.a, &bar, c_in, c_out, rank * kTreeParts, 0);
+    tma_load_4d(tb, &maps.b, &bar, c_in, c_out, rank * kTreeParts, 0);
+    tma_load_4d(tc, &maps.c, &bar, c_in, c_out, rank * kTreeParts, 0);
+    tma_load_4d(td, &maps.d, &bar, c_in, c_out, rank * kTreeParts, 0);
+    tma_load_4d(td + M * 128, &maps.d, &bar, c_in + 16, c_out, rank * kTreeParts, 0);
+  }
+  if (!mbar_wait_bounded(&bar, 0, kTmaWaitPolls)) report_error(A.st, 6);
+
+  // ---------------- pass 0: float solve with the float part of d
+  float x0[M];
+  float u0, v0;
+  unsigned nx;
+  {
+    Sweep<M> S;
+#pragma unroll
+    for (int t = 0; t < M; ++t) {
+      float a = ra[t * 256], b = rb[t * 256], c = rc[t * 256];
+      if (t == 0 && first_part) a = 0.f;
+      if (t == M - 1 && last_part) c = 0.f;
+      const ff dd = split_f64(rd[t * 128]);
+      rd2[t * 128] = make_float2(dd.h, dd.l);  // same thread, same 8 bytes: read before write
+      S.row(t, a, b, c, dd.h);
+    }
+    const Blk blk = S.block();
+    cluster_wait();  // every CTA of the cluster has started
+    unsigned unused;
+    float xs_c, xe_c;
+    tree_stage_b<C>(blk, 0u, slots, rank, p, jj, j, u0, v0, xs_c, xe_c, unused);
+    // Boundary unknowns exactly as the neighbours will see them in the residual: at a CTA edge
+    // the cluster tree's values, elsewhere the partition's own block form.
+    const float xs = (p == 0 && rank > 0) ? xs_c : Sweep<M>::first(blk, u0, v0);
+    const float xe = (p == kTreeParts - 1 && rank < C - 1) ? xe_c : Sweep<M>::last(blk, u0, v0);
+    S.solve(xs, xe, x0);
+    // inside the CTA the neighbours' values come from the neighbouring lanes
+    const float from_prev = __shfl_up_sync(~0u, x0[M - 1], 4), from_next = __shfl_down_sync(~0u, x0[0], 4);
+    if (p > 0) u0 = from_prev;
+    if (p < kTreeParts - 1) v0 = from_next;
+    nx = 0u;
+#pragma unroll
+    for (int t = 0; t < M; ++t) nx = max(nx, abs_bits(x0[t]));
+    nx = line_max(nx);  // this CTA's rows of the line
+  }
+  if (A.max_iters <= 0) {  // no correction: the float solution is the answer
+    if (active && !bits_finite(nx)) report_error(A.st, 5);
+    if (active) {
+#pragma unroll
+      for (int t = 0; t < M; ++t) px[t * es] = f2d(x0[t]);
+    }
+    return;  // nothing reads this CTA's shared memory after the last barrier
+  }
+
+  // ---------------- pass 1: correction for r = d - A x_0, x = x_0 + dx
+  unsigned prev, gdx, gxm;
+  {
+    Sweep<M> S;
+#pragma unroll
+    for (int t = 0; t < M; ++t) {
+      float a = ra[t * 256], b = rb[t * 256], c = rc[t * 256];
+      if (t == 0 && first_part) a = 0.f;
+      if (t == M - 1 && last_part) c = 0.f;
+      const float2 dd = rd2[t * 128];
+      const float xm = t == 0 ? u0 : x0[t > 0 ? t - 1 : 0];
+      const float xp = t == M - 1 ? v0 : x0[t < M - 1 ? t + 1 : 0];
+      S.row(t, a, b, c, residual_f(a, b, c, dd.x, dd.y, xm, x0[t], xp));
+    }
+    const Blk blk = S.block();
+    float u, v, xs_c, xe_c;
+    tree_stage_b<C>(blk, nx, slots + C * kTreeSlotPitch, rank, p, jj, j, u, v, xs_c, xe_c, prev);  // prev: max |x_0|
+    float dx[M];
+    S.solve(Sweep<M>::first(blk, u, v), Sweep<M>::last(blk, u, v), dx);
+    unsigned ndx = 0u;
+#pragma unroll
+    for (int t = 0; t < M; ++t) ndx = max(ndx, abs_bits(dx[t]));
+    tree_norms_push<C>(line_max(ndx), nx, norms + C * kTreeNormPitch, rank, p, j);
+    if (active) {  // the stores overlap the norm barrier
+#pragma unroll
+      for (int t = 0; t < M; ++t) px[t * es] = f2d(x0[t]) + f2d(dx[t]);
+    }
+    tree_norms_read<C>(gdx, gxm, norms + C * kTreeNormPitch, p, j);
+  }
+  bool line_done = tree_line_done(gdx, gxm, prev, active, A.tol, reporter, A.st);
+  bool all_done = __syncthreads_and(line_done) != 0;
+
+  // ---------------- later corrections (rare): x re-read from global memory
+  int it = 1;
+  while (!all_done && it < A.max_iters) {
+    ++it;
+    cluster_arrive();  // x of the previous pass, written by every CTA, visible to all
+    cluster_wait();
+    Sweep<M> S;
+    ff xm{0.f, 0.f}, xc{0.f, 0.f}, xe{0.f, 0.f};
+    if (active) {
+      if (!first_part) xm = split_f64(px[-es]);
+      if (!last_part) xe = split_f64(px[M * es]);
+      xc = split_f64(px[0]);
+    }
+#pragma unroll
+    for (int t = 0; t < M; ++t) {
+      float a = ra[t * 256], b = rb[t * 256], c = rc[t * 256];
+      if (t == 0 && first_part) a = 0.f;
+      if (t == M - 1 && last_part) c = 0.f;
+      const float2 dd = rd2[t * 128];
+      const ff xn = t == M - 1 ? xe : (active ? split_f64(px[(t + 1) * es]) : ff{0.f, 0.f});
+      S.row(t, a, b, c, residual_ff(a, b, c, ff{dd.x, dd.y}, xm, xc, xn));
+      xm = xc;
+      xc = xn;
+    }
+    const Blk blk = S.block();
+    float u, v, xs_c, xe_c;
+    unsigned unused;
+    tree_stage_b<C>(blk, 0u, slots + (it & 1) * C * kTreeSlotPitch, rank, p, jj, j, u, v, xs_c, xe_c, unused);
+    float dx[M];
+    S.solve(Sweep<M>::first(blk, u, v), Sweep<M>::last(blk, u, v), dx);
+    unsigned ndx = 0u, nxm = 0u;
+    if (active) {
+#pragma unroll
+      for (int t = 0; t < M; ++t) {
+        const double xn = px[t * es] + f2d(dx[t]);
+        px[t * es] = xn;
+        ndx = max(ndx, abs_bits(dx[t]));
+        nxm = max(nxm, abs_bits(__double2float_rn(xn)));
+      }
+    }
+    unsigned* nb = norms + (it & 1) * C * kTreeNormPitch;
+    tree_norms_push<C>(line_max(ndx), line_max(nxm), nb, rank, p, j);
+    tree_norms_read<C>(gdx, gxm, nb, p, j);
+    line_done = tree_line_done(gdx, gxm, prev, active, A.tol, reporter, A.st);
+    all_done = __syncthreads_and(line_done) != 0;
+  }
+  if (reporter) {
+    report_iters(A.st, it);
+    if (!line_done) report_error(A.st, 7);
+  }
+}
+
+// compiled geometries: (rows per partition M, cluster size C); a line spans n = 8 C M rows.
+#define TDMA_REFINE_TREE_SHAPES(X) X(16, 8) X(16, 4) X(16, 2)
+
+}  // namespace tdma

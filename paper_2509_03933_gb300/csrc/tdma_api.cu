@@ -17,6 +17,7 @@
 #include "kernels_refine_reg.cuh"
 #include "kernels_refine_tma.cuh"
 #include "kernels_refine_cluster.cuh"
+#include "kernels_refine_tree.cuh"
 #include "kernels_thomas.cuh"
 #include "kernels_ragged.cuh"
 #include "kernels_backward.cuh"
@@ -218,7 +219,7 @@ bool tma_layout_ok(const tdma_desc_t& d, const tdma_config_t& c) {
 }
 
 bool encode_map(CUtensorMap* map, const void* ptr, bool f64, const tdma_desc_t& d, const tdma_config_t& c,
-                int box_partitions = 0) {
+                int box_partitions = 0, int box_lines = 0, bool swizzle128 = false) {
   EncodeTiledFn fn = encode_fn();
   if (!fn || !aligned(ptr, 16)) return false;
   const cuuint64_t eb = f64 ? 8 : 4;
@@ -228,12 +229,13 @@ bool encode_map(CUtensorMap* map, const void* ptr, bool f64, const tdma_desc_t& 
   cuuint64_t dims[4] = {(cuuint64_t)inner, (cuuint64_t)outer, (cuuint64_t)c.partitions, (cuuint64_t)m};
   cuuint64_t os = outer > 1 ? (cuuint64_t)d.outer_stride * eb : ((cuuint64_t)inner * eb + 15) / 16 * 16;
   cuuint64_t strides[3] = {os, (cuuint64_t)(m * d.elem_stride) * eb, (cuuint64_t)d.elem_stride * eb};
-  cuuint32_t box[4] = {(cuuint32_t)c.lines_per_block, 1,
+  cuuint32_t box[4] = {(cuuint32_t)(box_lines > 0 ? box_lines : c.lines_per_block), 1,
                        (cuuint32_t)(box_partitions > 0 ? box_partitions : c.partitions), (cuuint32_t)m};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   const CUresult r = fn(map, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
                         const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
 }
@@ -283,6 +285,39 @@ bool refine_cluster_config(const tdma_desc_t& d, int P_req, tdma_config_t& c) {
   t.variant = TDMA_VARIANT_REFINE_CLUSTER;
   if (!tma_layout_ok(d, t)) return false;
   if (d.n_lines < t.lines_per_block) return false;  // a cluster needs a full line group
+  c = t;
+  return true;
+}
+
+// Merge-tree cluster refinement: lines of n = 8 C M rows, 32 lines per cluster, swizzled tile.
+bool tree_shape(int64_t n, int& M, int& C) {
+#define TDMA_TR_MATCH(MM, CC) if (n == (int64_t)8 * MM * CC) { M = MM; C = CC; return true; }
+  TDMA_REFINE_TREE_SHAPES(TDMA_TR_MATCH)
+#undef TDMA_TR_MATCH
+  return false;
+}
+size_t tree_smem(int M, int C) {
+#define TDMA_TR_SMEM(MM, CC) if (M == MM && C == CC) return refine_tree_smem_bytes<MM, CC>();
+  TDMA_REFINE_TREE_SHAPES(TDMA_TR_SMEM)
+#undef TDMA_TR_SMEM
+  return 0;
+}
+bool refine_tree_config(const tdma_desc_t& d, int P_req, tdma_config_t& c) {
+  // TDMA_DISABLE_TREE=1 leaves these shapes to the cluster kernel with serial Stage B
+  if (const char* e = std::getenv("TDMA_DISABLE_TREE")) if (e[0] == '1') return false;
+  int M, C;
+  if (!tree_shape(d.n, M, C)) return false;
+  if (P_req > 0 && P_req != C * kTreeParts) return false;
+  tdma_config_t t{};
+  t.partitions = C * kTreeParts;
+  t.rows_per_thread = M;
+  t.lines_per_block = kTreeLines;
+  t.threads_per_block = 256;
+  t.blocks = (int32_t)(C * ((d.n_lines + kTreeLines - 1) / kTreeLines));
+  t.smem_bytes = (int64_t)tree_smem(M, C);
+  t.variant = TDMA_VARIANT_REFINE_TREE;
+  if (!tma_layout_ok(d, t)) return false;
+  if (d.n_lines < kTreeLines) return false;  // a cluster needs a full line group
   c = t;
   return true;
 }
@@ -374,6 +409,24 @@ cudaError_t launch_forward(const tdma_plan_s* p, const Args& A, cudaStream_t s) 
       }
       break;
     }
+    case TDMA_VARIANT_REFINE_TREE: {
+      TmaMaps maps;
+      std::memset(&maps, 0, sizeof(maps));
+      const int C = c.partitions / kTreeParts;
+      const bool ok = encode_map(&maps.a, A.a, false, p->desc, c, kTreeParts, 32, true) &&
+                      encode_map(&maps.b, A.b, false, p->desc, c, kTreeParts, 32, true) &&
+                      encode_map(&maps.c, A.c, false, p->desc, c, kTreeParts, 32, true) &&
+                      encode_map(&maps.d, A.d, true, p->desc, c, kTreeParts, 16, true);
+      if (!ok) return cudaErrorInvalidValue;
+#define TDMA_LAUNCH_TR(MM, CC)                                        \
+  if (c.rows_per_thread == MM && C == CC) {                            \
+    refine_tree_kernel<MM, CC><<<grid, block, sm, s>>>(A, maps);       \
+    return cudaGetLastError();                                          \
+  }
+      TDMA_REFINE_TREE_SHAPES(TDMA_LAUNCH_TR)
+#undef TDMA_LAUNCH_TR
+      return cudaErrorInvalidValue;
+    }
     case TDMA_VARIANT_REFINE_CLUSTER: {
       TmaMaps maps;
       std::memset(&maps, 0, sizeof(maps));
@@ -436,6 +489,14 @@ cudaError_t prepare_kernel(const tdma_plan_s* p) {
         case 16: return set_smem(refine_tma_kernel<16, 2>, sm);
         default: return set_smem(refine_tma_kernel<32, 1>, sm);
       }
+    case TDMA_VARIANT_REFINE_TREE: {
+      const int C = p->cfg.partitions / kTreeParts;
+#define TDMA_PREP_TR(MM, CC) \
+  if (p->cfg.rows_per_thread == MM && C == CC) return set_smem(refine_tree_kernel<MM, CC>, sm);
+      TDMA_REFINE_TREE_SHAPES(TDMA_PREP_TR)
+#undef TDMA_PREP_TR
+      return cudaErrorInvalidValue;
+    }
     case TDMA_VARIANT_REFINE_CLUSTER: {
       const int PC = 256 / p->cfg.lines_per_block, C = p->cfg.partitions / PC;
 #define TDMA_PREP_CL(MM, PP, CC) \
@@ -620,6 +681,7 @@ std::vector<tdma_config_t> tune_candidates(const tdma_desc_t& d, bool allow_tma)
     if (P == 1 || d.n / P >= 2) Ps.push_back(P);
   tdma_config_t c{};
   if (d.precision == TDMA_F32_REFINE) {
+    if (allow_tma && refine_tree_config(d, 0, c)) out.push_back(c);
     if (allow_tma && refine_cluster_config(d, 0, c)) out.push_back(c);
     for (int P : Ps) {
       tdma_config_t r{};
@@ -821,7 +883,8 @@ tdma_status_t tdma_plan_create(tdma_plan_t* plan, const tdma_desc_t* desc, size_
   } else if (is_uniform(*desc)) {
     bool ok = false;
     if (desc->precision == TDMA_F32_REFINE) {
-      ok = p->allow_tma && refine_cluster_config(*desc, desc->partitions, c);
+      ok = p->allow_tma && (refine_tree_config(*desc, desc->partitions, c) ||
+                            refine_cluster_config(*desc, desc->partitions, c));
       if (!ok) {
         ok = refine_reg_config(*desc, desc->partitions, c);
         if (ok) refine_tma_config(*desc, c);

@@ -159,6 +159,26 @@ def test_refine_tile_kernels_z_lines(n, lines):
     assert O.rel_l2(x, ref) <= TOL["f32"]
 
 
+@pytest.mark.parametrize("tree", [True, False])
+@pytest.mark.parametrize("n,lines", [(1024, 96), (512, 40), (256, 32)])
+def test_cluster_refine_kernels(monkeypatch, tree, n, lines):
+    # lines of n = 8 C M rows spread over a CTA cluster: the merge-tree kernel (default) and,
+    # with it switched off, the kernel with a serial Stage B; 40 lines leave a partial cluster
+    if not tree:
+        monkeypatch.setenv("TDMA_DISABLE_TREE", "1")
+    g = synth.grid_general((n, lines), 0, 23 + n, device="cpu", fp32_coefficients=True)
+    a, b, c = (g[k + "32"].cuda() for k in ("a", "b", "c"))
+    d = g["d"].cuda()
+    plan = tdma.Plan(*tdma.line_layout(d, 0), precision="f32r")
+    assert plan.config["variant"] == (8 if tree else 6)
+    x = torch.empty_like(d)
+    plan.solve(a, b, c, d, x)
+    st, iters = plan.last_error()
+    assert st == 0 and iters == 1
+    ref = O.thomas(*(_np_lines(t, 0) for t in (a, b, c, d)))
+    assert O.rel_l2(_np_lines(x, 0), ref) <= TOL["f32r"]
+
+
 @pytest.mark.parametrize("partitions", [1, 4])
 def test_fp64_refine_mode_general_and_badly_conditioned(partitions):
     # general lines: at least as accurate as plain FP64
