@@ -17,7 +17,7 @@
 // into one by eliminating the unknowns on either side of their boundary, y = x_{e(L)} and
 // z = x_{s(R)}:  y = L.p2 + L.q2 u + L.r2 z,  z = R.p1 + R.q1 y + R.r1 v.  Three merge levels
 // over the lanes of a line give the CTA's block (the paper's A2B); each CTA pushes it into the
-// shared memory of every CTA of the cluster (DSMEM stores), one cluster barrier, and every CTA
+// shared memory of every CTA of the cluster (DSMEM stores), waits for the others', and every CTA
 // merges the C blocks of the line the same way. The line ends have no outside neighbours
 // (u = v = 0), so the down-sweep of the two trees hands every partition its own u and v (the
 // paper's B2C), and Stage C is x_t = delta_t - alpha_t x_s - gamma_t x_{t+1}.
@@ -26,7 +26,8 @@
 // recomputes the same factors and solves for the extra-precise residual r = d - A x_0 (float
 // pairs); x = x_0 + dx goes to global memory in FP64. The stop rule (per line, on the line's
 // max norms) needs one more exchange; later passes, rare, re-read x from global memory.
-// Per tile there are three cluster barriers: pass 0 blocks, pass 1 blocks, pass 1 norms.
+// Exchanges are point to point (st.async into the other CTAs' shared memory, completing on
+// their mbarriers): a CTA waits only for the data it needs, never for another CTA's threads.
 #pragma once
 #include <cooperative_groups.h>
 #include "layout.cuh"
@@ -37,8 +38,21 @@ namespace tdma {
 
 constexpr int kTreeLines = 32;               // lines per cluster
 constexpr int kTreeParts = 8;                // partitions per CTA
-constexpr int kTreeSlotPitch = 7 * 32 + 4;   // per source CTA: 7 fields x 32 lines (+4: banks)
-constexpr int kTreeNormPitch = 2 * 32 + 4;   // per source CTA: 2 fields x 32 lines
+constexpr int kTreeSlotPitch = 32 * 8 + 4;   // per source CTA: 32 lines x 8 floats (+4: banks)
+constexpr int kTreeNormPitch = 32 * 2 + 4;   // per source CTA: 32 lines x 2 words
+// Polls of an exchange wait (about 6 ms with the back-off of mbar_wait_bounded; a tile's CTAs
+// live for tens of microseconds). After one wait gives up the thread stops waiting for the rest
+// of the tile, but it still sends everything, so its peers are not held up and no CTA leaves
+// while others may still store into its shared memory.
+constexpr uint32_t kTreeWaitPolls = 1u << 16;
+
+TDMA_DEV void tree_wait(uint64_t* bar, uint32_t phase, bool& alive, DevStatus* st) {
+  if (!alive) return;
+  if (!mbar_wait_bounded(bar, phase, kTreeWaitPolls)) {
+    alive = false;
+    report_error(st, 6);
+  }
+}
 
 // x_s = p1 + q1 u + r1 v and x_e = p2 + q2 u + r2 v for a row range [s, e] of a line.
 struct Blk { float p1, q1, r1, p2, q2, r2; };
@@ -135,7 +149,6 @@ TDMA_DEV uint32_t cluster_rank() {
   asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
   return r;
 }
-TDMA_DEV void cluster_arrive_relaxed() { asm volatile("barrier.cluster.arrive.relaxed.aligned;" ::: "memory"); }
 TDMA_DEV void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
 TDMA_DEV void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
 // shared::cluster address of `p` in the shared memory of CTA `rank`
@@ -144,11 +157,17 @@ TDMA_DEV uint32_t map_rank(const void* p, int rank) {
   asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
   return r;
 }
-TDMA_DEV void st_cluster(uint32_t addr, float v) {
-  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(addr), "f"(v) : "memory");
+// Asynchronous stores into another CTA's shared memory; each completes `bytes` of the
+// transaction count of the mbarrier at `bar` in that CTA (st.async, sm_90+).
+TDMA_DEV void st_async4(uint32_t addr, float a, float b, float c, float d, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.f32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(addr),
+               "f"(a), "f"(b), "f"(c), "f"(d), "r"(bar)
+               : "memory");
 }
-TDMA_DEV void st_cluster(uint32_t addr, unsigned v) {
-  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+TDMA_DEV void st_async2(uint32_t addr, unsigned a, unsigned b, uint32_t bar) {
+  asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v2.u32 [%0], {%1, %2}, [%3];" ::"r"(addr), "r"(a),
+               "r"(b), "r"(bar)
+               : "memory");
 }
 
 // Norms travel as the bit patterns of |v|: for non-negative floats the unsigned order is the
@@ -171,34 +190,35 @@ __host__ __device__ constexpr size_t refine_tree_smem_bytes() {
 }
 
 // Stage B for one pass: CTA tree, exchange of the CTA blocks, cluster tree, down-sweeps.
-// `extra` (a per-line norm of this CTA, as abs_bits) travels with the block; `extra_max` is its
-// maximum over the cluster. Returns this partition's (u, v) and this CTA's first and last
-// unknowns of the line as the neighbouring CTAs see them (xs_c, xe_c; every CTA computes the
-// cluster tree from the same data in the same order, so the values agree bit for bit).
+// The exchange is point to point: lane p sends this CTA's block of line j (and `extra`, a
+// per-line norm of this CTA as abs_bits) into slot [rank][j] of CTA p with st.async, which
+// completes on CTA p's mbarrier `bar` for this buffer; every CTA waits on its own mbarrier for
+// the C x 32 slots (phase `phase`), so no CTA waits for another CTA's threads, only for data.
+// `extra_max` is the maximum of `extra` over the cluster. Returns this partition's (u, v) and
+// this CTA's first and last unknowns of the line as the neighbouring CTAs see them (every CTA
+// computes the cluster tree from the same data in the same order, so the values agree bit for
+// bit).
 template <int C>
-TDMA_DEV void tree_stage_b(const Blk& b, unsigned extra, float* slots, int rank, int p, int jj, int j, float& u,
-                           float& v, float& xs_c, float& xe_c, unsigned& extra_max) {
+TDMA_DEV void tree_stage_b(const Blk& b, unsigned extra, float* slots, uint64_t* bar, uint32_t phase, int rank, int p,
+                           int jj, int j, float& u, float& v, float& xs_c, float& xe_c, unsigned& extra_max,
+                           bool& alive, DevStatus* st) {
   constexpr int LC = C == 8 ? 3 : (C == 4 ? 2 : 1);
   Aff kc[3];
   const Blk B = tree_up<3>(b, p, kc);
+  if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, (uint32_t)C * kTreeLines * 32u);
   if (p < C) {
-    const uint32_t dst = map_rank(slots + rank * kTreeSlotPitch + j, p);
-    st_cluster(dst, B.p1);
-    st_cluster(dst + 128, B.q1);
-    st_cluster(dst + 256, B.r1);
-    st_cluster(dst + 384, B.p2);
-    st_cluster(dst + 512, B.q2);
-    st_cluster(dst + 640, B.r2);
-    st_cluster(dst + 768, extra);
+    const uint32_t dst = map_rank(slots + rank * kTreeSlotPitch + j * 8, p), rb = map_rank(bar, p);
+    st_async4(dst, B.p1, B.q1, B.r1, B.p2, rb);
+    st_async4(dst + 16, B.q2, B.r2, __uint_as_float(extra), 0.f, rb);
   }
-  cluster_arrive();
-  cluster_wait();
-  const float* s = slots + (p & (C - 1)) * kTreeSlotPitch + j;
-  extra_max = line_max(__float_as_uint(s[192]));
+  tree_wait(bar, phase, alive, st);
+  const float4* s = reinterpret_cast<const float4*>(slots + (p & (C - 1)) * kTreeSlotPitch + j * 8);
+  const float4 s0 = s[0], s1 = s[1];
+  extra_max = line_max(__float_as_uint(s1.z));
   float uq = 0.f, vq = 0.f, xsq = 0.f, xeq = 0.f;
   {
     Mrg kq[3];
-    tree_up_full<LC>(Blk{s[0], s[32], s[64], s[96], s[128], s[160]}, p, kq);
+    tree_up_full<LC>(Blk{s0.x, s0.y, s0.z, s0.w, s1.x, s1.y}, p, kq);
     tree_down_full<LC>(uq, vq, xsq, xeq, p, kq);  // the line ends have u = v = 0
   }
   const int src = (rank << 2) | jj;
@@ -209,24 +229,21 @@ TDMA_DEV void tree_stage_b(const Blk& b, unsigned extra, float* slots, int rank,
   tree_down<3>(u, v, p, kc);
 }
 
-// Per-line maxima over the cluster, in two halves so that work can go between the barrier's
-// arrive and wait: push this CTA's (dx, xm) of line j (already reduced over the line's lanes)
-// to every CTA and arrive; then wait and reduce over the C sources.
+// Per-line maxima over the cluster, in two halves so that work can go between sending and
+// waiting: send this CTA's (dx, xm) of line j (already reduced over the line's lanes) to every
+// CTA; then wait for the C sources and reduce.
 template <int C>
-TDMA_DEV void tree_norms_push(unsigned dx, unsigned xm, unsigned* norms, int rank, int p, int j) {
-  if (p < C) {
-    const uint32_t dst = map_rank(norms + rank * kTreeNormPitch + j, p);
-    st_cluster(dst, dx);
-    st_cluster(dst + 128, xm);
-  }
-  cluster_arrive();
+TDMA_DEV void tree_norms_push(unsigned dx, unsigned xm, unsigned* norms, uint64_t* bar, int rank, int p, int j) {
+  if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, (uint32_t)C * kTreeLines * 8u);
+  if (p < C) st_async2(map_rank(norms + rank * kTreeNormPitch + j * 2, p), dx, xm, map_rank(bar, p));
 }
 template <int C>
-TDMA_DEV void tree_norms_read(unsigned& dx, unsigned& xm, const unsigned* norms, int p, int j) {
-  cluster_wait();
-  const unsigned* s = norms + (p & (C - 1)) * kTreeNormPitch + j;
-  dx = line_max(s[0]);
-  xm = line_max(s[32]);
+TDMA_DEV void tree_norms_read(unsigned& dx, unsigned& xm, const unsigned* norms, uint64_t* bar, uint32_t phase, int p,
+                              int j, bool& alive, DevStatus* st) {
+  tree_wait(bar, phase, alive, st);
+  const uint2 v = *reinterpret_cast<const uint2*>(norms + (p & (C - 1)) * kTreeNormPitch + j * 2);
+  dx = line_max(v.x);
+  xm = line_max(v.y);
 }
 
 // r = d - (a xm + b x + c xp) for float x values and d = dh + dl, as if in twice the float
@@ -309,6 +326,8 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
   static_assert(M >= 3, "rows per partition");
   extern __shared__ __align__(16) unsigned char smem_raw[];  // aligned to 1 KB below
   __shared__ __align__(8) uint64_t bar;
+  // exchange mbarriers: [0], [1] block slots of even / odd passes, [2], [3] norm slots
+  __shared__ __align__(8) uint64_t xbar[4];
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, p = lane >> 2, jj = lane & 3;
   const int j = 4 * w + jj;  // line within the cluster's 32
   const int rank = (int)cluster_rank();
@@ -342,10 +361,14 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
 
   if (tid == 0) {
     mbar_init(&bar, 1);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) mbar_init(&xbar[i], 1);
     mbar_fence_init();
   }
   __syncthreads();
-  cluster_arrive_relaxed();  // this CTA runs; the matching wait precedes the first DSMEM store
+  // the barriers are initialised and this CTA runs; the matching wait precedes the first
+  // store into another CTA's shared memory
+  cluster_arrive();
   if (tid == 0) {
     mbar_arrive_expect_tx(&bar, 5u * M * 1024u);
     tma_load_4d(ta, &maps.a, &bar, c_in, c_out, rank * kTreeParts, 0);
@@ -354,7 +377,8 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
     tma_load_4d(td, &maps.d, &bar, c_in, c_out, rank * kTreeParts, 0);
     tma_load_4d(td + M * 128, &maps.d, &bar, c_in + 16, c_out, rank * kTreeParts, 0);
   }
-  if (!mbar_wait_bounded(&bar, 0, kTmaWaitPolls)) report_error(A.st, 6);
+  bool alive = mbar_wait_bounded(&bar, 0, kTmaWaitPolls);
+  if (!alive) report_error(A.st, 6);
 
   // ---------------- pass 0: float solve with the float part of d
   float x0[M];
@@ -375,7 +399,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
     cluster_wait();  // every CTA of the cluster has started
     unsigned unused;
     float xs_c, xe_c;
-    tree_stage_b<C>(blk, 0u, slots, rank, p, jj, j, u0, v0, xs_c, xe_c, unused);
+    tree_stage_b<C>(blk, 0u, slots, &xbar[0], 0u, rank, p, jj, j, u0, v0, xs_c, xe_c, unused, alive, A.st);
     // Boundary unknowns exactly as the neighbours will see them in the residual: at a CTA edge
     // the cluster tree's values, elsewhere the partition's own block form.
     const float xs = (p == 0 && rank > 0) ? xs_c : Sweep<M>::first(blk, u0, v0);
@@ -396,7 +420,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
 #pragma unroll
       for (int t = 0; t < M; ++t) px[t * es] = f2d(x0[t]);
     }
-    return;  // nothing reads this CTA's shared memory after the last barrier
+    return;  // every store into this CTA's shared memory has arrived (pass 0 waited for them)
   }
 
   // ---------------- pass 1: correction for r = d - A x_0, x = x_0 + dx
@@ -415,18 +439,19 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
     }
     const Blk blk = S.block();
     float u, v, xs_c, xe_c;
-    tree_stage_b<C>(blk, nx, slots + C * kTreeSlotPitch, rank, p, jj, j, u, v, xs_c, xe_c, prev);  // prev: max |x_0|
+    tree_stage_b<C>(blk, nx, slots + C * kTreeSlotPitch, &xbar[1], 0u, rank, p, jj, j, u, v, xs_c, xe_c, prev,
+                    alive, A.st);  // prev: line max |x_0|
     float dx[M];
     S.solve(Sweep<M>::first(blk, u, v), Sweep<M>::last(blk, u, v), dx);
     unsigned ndx = 0u;
 #pragma unroll
     for (int t = 0; t < M; ++t) ndx = max(ndx, abs_bits(dx[t]));
-    tree_norms_push<C>(line_max(ndx), nx, norms + C * kTreeNormPitch, rank, p, j);
-    if (active) {  // the stores overlap the norm barrier
+    tree_norms_push<C>(line_max(ndx), nx, norms + C * kTreeNormPitch, &xbar[3], rank, p, j);
+    if (active) {  // the stores overlap the norm exchange
 #pragma unroll
       for (int t = 0; t < M; ++t) px[t * es] = f2d(x0[t]) + f2d(dx[t]);
     }
-    tree_norms_read<C>(gdx, gxm, norms + C * kTreeNormPitch, p, j);
+    tree_norms_read<C>(gdx, gxm, norms + C * kTreeNormPitch, &xbar[3], 0u, p, j, alive, A.st);
   }
   bool line_done = tree_line_done(gdx, gxm, prev, active, A.tol, reporter, A.st);
   bool all_done = __syncthreads_and(line_done) != 0;
@@ -458,7 +483,9 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
     const Blk blk = S.block();
     float u, v, xs_c, xe_c;
     unsigned unused;
-    tree_stage_b<C>(blk, 0u, slots + (it & 1) * C * kTreeSlotPitch, rank, p, jj, j, u, v, xs_c, xe_c, unused);
+    // pass `it` uses the buffers of its parity; each mbarrier's phase counts its uses
+    tree_stage_b<C>(blk, 0u, slots + (it & 1) * C * kTreeSlotPitch, &xbar[it & 1], (uint32_t)(it >> 1) & 1u, rank, p,
+                    jj, j, u, v, xs_c, xe_c, unused, alive, A.st);
     float dx[M];
     S.solve(Sweep<M>::first(blk, u, v), Sweep<M>::last(blk, u, v), dx);
     unsigned ndx = 0u, nxm = 0u;
@@ -472,8 +499,8 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
       }
     }
     unsigned* nb = norms + (it & 1) * C * kTreeNormPitch;
-    tree_norms_push<C>(line_max(ndx), line_max(nxm), nb, rank, p, j);
-    tree_norms_read<C>(gdx, gxm, nb, p, j);
+    tree_norms_push<C>(line_max(ndx), line_max(nxm), nb, &xbar[2 + (it & 1)], rank, p, j);
+    tree_norms_read<C>(gdx, gxm, nb, &xbar[2 + (it & 1)], (uint32_t)((it - 1) >> 1) & 1u, p, j, alive, A.st);
     line_done = tree_line_done(gdx, gxm, prev, active, A.tol, reporter, A.st);
     all_done = __syncthreads_and(line_done) != 0;
   }
