@@ -319,6 +319,9 @@ TDMA_DEV bool tree_line_done(unsigned gdx, unsigned gxm, unsigned& prev, bool ac
   return ratio * dxn <= tol * xn || dxn == 0.f;
 }
 
+// Persistent: the grid holds the clusters that fit on the GPU at once, and cluster k takes line
+// groups k, k + K, k + 2K, ... (K clusters). While it works on one group it prefetches the next
+// group's tile into L2, so the TMA load of the next tile finds its data there.
 template <int M, int C>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
     refine_tree_kernel(const Args A, const __grid_constant__ TmaMaps maps) {
@@ -331,11 +334,10 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, p = lane >> 2, jj = lane & 3;
   const int j = 4 * w + jj;  // line within the cluster's 32
   const int rank = (int)cluster_rank();
-  const int64_t line0 = (int64_t)(blockIdx.x / C) * kTreeLines;
-  const bool active = line0 + j < A.lay.n_lines;
   const int kg = rank * kTreeParts + p;  // partition index within the line
   const bool first_part = kg == 0, last_part = kg == C * kTreeParts - 1;
-  const bool reporter = rank == 0 && p == 0 && active;  // one thread per line reports
+  const int64_t n_groups = (A.lay.n_lines + kTreeLines - 1) / kTreeLines;
+  const int64_t n_clusters = gridDim.x / C;
 
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                                          ~static_cast<uintptr_t>(1023));
@@ -353,11 +355,11 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
   const float* rc = tc + fo;
   double* rd = td + (w >> 2) * (M * 128) + p * 16 + ((((w & 3) * 2 + (jj >> 1)) ^ p) << 1) + (jj & 1);
   float2* rd2 = reinterpret_cast<float2*>(rd);  // d as a float pair, written in place by pass 0
-
-  const int64_t es = A.lay.es;
-  double* px = (double*)A.x + A.lay.off(active ? line0 + j : 0) + (int64_t)kg * M * es;
-  const int64_t ic = A.lay.ic;
-  const int c_in = (int)(line0 % ic), c_out = (int)(line0 / ic);
+  // x leaves through the a and b tiles (32 KB, the layout of the d tile) by TMA store once pass 1
+  // no longer reads them
+  double* const tx = reinterpret_cast<double*>(ta);
+  double* rx = tx + (rd - td);
+  const int64_t es = A.lay.es, ic = A.lay.ic;
 
   if (tid == 0) {
     mbar_init(&bar, 1);
@@ -369,145 +371,197 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
   // the barriers are initialised and this CTA runs; the matching wait precedes the first
   // store into another CTA's shared memory
   cluster_arrive();
-  if (tid == 0) {
-    mbar_arrive_expect_tx(&bar, 5u * M * 1024u);
-    tma_load_4d(ta, &maps.a, &bar, c_in, c_out, rank * kTreeParts, 0);
-    tma_load_4d(tb, &maps.b, &bar, c_in, c_out, rank * kTreeParts, 0);
-    tma_load_4d(tc, &maps.c, &bar, c_in, c_out, rank * kTreeParts, 0);
-    tma_load_4d(td, &maps.d, &bar, c_in, c_out, rank * kTreeParts, 0);
-    tma_load_4d(td + M * 128, &maps.d, &bar, c_in + 16, c_out, rank * kTreeParts, 0);
-  }
-  bool alive = mbar_wait_bounded(&bar, 0, kTmaWaitPolls);
-  if (!alive) report_error(A.st, 6);
+  bool started = false, alive = true;
+  uint32_t tph = 0, xph0 = 0, xph1 = 0, xph2 = 0, xph3 = 0;  // phases of bar and xbar[0..3]
 
-  // ---------------- pass 0: float solve with the float part of d
-  float x0[M];
-  float u0, v0;
-  unsigned nx;
-  {
-    Sweep<M> S;
-#pragma unroll
-    for (int t = 0; t < M; ++t) {
-      float a = ra[t * 256], b = rb[t * 256], c = rc[t * 256];
-      if (t == 0 && first_part) a = 0.f;
-      if (t == M - 1 && last_part) c = 0.f;
-      const ff dd = split_f64(rd[t * 128]);
-      rd2[t * 128] = make_float2(dd.h, dd.l);  // same thread, same 8 bytes: read before write
-      S.row(t, a, b, c, dd.h);
-    }
-    const Blk blk = S.block();
-    cluster_wait();  // every CTA of the cluster has started
-    unsigned unused;
-    float xs_c, xe_c;
-    tree_stage_b<C>(blk, 0u, slots, &xbar[0], 0u, rank, p, jj, j, u0, v0, xs_c, xe_c, unused, alive, A.st);
-    // Boundary unknowns exactly as the neighbours will see them in the residual: at a CTA edge
-    // the cluster tree's values, elsewhere the partition's own block form.
-    const float xs = (p == 0 && rank > 0) ? xs_c : Sweep<M>::first(blk, u0, v0);
-    const float xe = (p == kTreeParts - 1 && rank < C - 1) ? xe_c : Sweep<M>::last(blk, u0, v0);
-    S.solve(xs, xe, x0);
-    // inside the CTA the neighbours' values come from the neighbouring lanes
-    const float from_prev = __shfl_up_sync(~0u, x0[M - 1], 4), from_next = __shfl_down_sync(~0u, x0[0], 4);
-    if (p > 0) u0 = from_prev;
-    if (p < kTreeParts - 1) v0 = from_next;
-    nx = 0u;
-#pragma unroll
-    for (int t = 0; t < M; ++t) nx = max(nx, abs_bits(x0[t]));
-    nx = line_max(nx);  // this CTA's rows of the line
-  }
-  if (A.max_iters <= 0) {  // no correction: the float solution is the answer
-    if (active && !bits_finite(nx)) report_error(A.st, 5);
-    if (active) {
-#pragma unroll
-      for (int t = 0; t < M; ++t) px[t * es] = f2d(x0[t]);
-    }
-    return;  // every store into this CTA's shared memory has arrived (pass 0 waited for them)
-  }
-
-  // ---------------- pass 1: correction for r = d - A x_0, x = x_0 + dx
-  unsigned prev, gdx, gxm;
-  {
-    Sweep<M> S;
-#pragma unroll
-    for (int t = 0; t < M; ++t) {
-      float a = ra[t * 256], b = rb[t * 256], c = rc[t * 256];
-      if (t == 0 && first_part) a = 0.f;
-      if (t == M - 1 && last_part) c = 0.f;
-      const float2 dd = rd2[t * 128];
-      const float xm = t == 0 ? u0 : x0[t > 0 ? t - 1 : 0];
-      const float xp = t == M - 1 ? v0 : x0[t < M - 1 ? t + 1 : 0];
-      S.row(t, a, b, c, residual_f(a, b, c, dd.x, dd.y, xm, x0[t], xp));
-    }
-    const Blk blk = S.block();
-    float u, v, xs_c, xe_c;
-    tree_stage_b<C>(blk, nx, slots + C * kTreeSlotPitch, &xbar[1], 0u, rank, p, jj, j, u, v, xs_c, xe_c, prev,
-                    alive, A.st);  // prev: line max |x_0|
-    float dx[M];
-    S.solve(Sweep<M>::first(blk, u, v), Sweep<M>::last(blk, u, v), dx);
-    unsigned ndx = 0u;
-#pragma unroll
-    for (int t = 0; t < M; ++t) ndx = max(ndx, abs_bits(dx[t]));
-    tree_norms_push<C>(line_max(ndx), nx, norms + C * kTreeNormPitch, &xbar[3], rank, p, j);
-    if (active) {  // the stores overlap the norm exchange
-#pragma unroll
-      for (int t = 0; t < M; ++t) px[t * es] = f2d(x0[t]) + f2d(dx[t]);
-    }
-    tree_norms_read<C>(gdx, gxm, norms + C * kTreeNormPitch, &xbar[3], 0u, p, j, alive, A.st);
-  }
-  bool line_done = tree_line_done(gdx, gxm, prev, active, A.tol, reporter, A.st);
-  bool all_done = __syncthreads_and(line_done) != 0;
-
-  // ---------------- later corrections (rare): x re-read from global memory
-  int it = 1;
-  while (!all_done && it < A.max_iters) {
-    ++it;
-    cluster_arrive();  // x of the previous pass, written by every CTA, visible to all
-    cluster_wait();
-    Sweep<M> S;
-    ff xm{0.f, 0.f}, xc{0.f, 0.f}, xe{0.f, 0.f};
-    if (active) {
-      if (!first_part) xm = split_f64(px[-es]);
-      if (!last_part) xe = split_f64(px[M * es]);
-      xc = split_f64(px[0]);
-    }
-#pragma unroll
-    for (int t = 0; t < M; ++t) {
-      float a = ra[t * 256], b = rb[t * 256], c = rc[t * 256];
-      if (t == 0 && first_part) a = 0.f;
-      if (t == M - 1 && last_part) c = 0.f;
-      const float2 dd = rd2[t * 128];
-      const ff xn = t == M - 1 ? xe : (active ? split_f64(px[(t + 1) * es]) : ff{0.f, 0.f});
-      S.row(t, a, b, c, residual_ff(a, b, c, ff{dd.x, dd.y}, xm, xc, xn));
-      xm = xc;
-      xc = xn;
-    }
-    const Blk blk = S.block();
-    float u, v, xs_c, xe_c;
-    unsigned unused;
-    // pass `it` uses the buffers of its parity; each mbarrier's phase counts its uses
-    tree_stage_b<C>(blk, 0u, slots + (it & 1) * C * kTreeSlotPitch, &xbar[it & 1], (uint32_t)(it >> 1) & 1u, rank, p,
-                    jj, j, u, v, xs_c, xe_c, unused, alive, A.st);
-    float dx[M];
-    S.solve(Sweep<M>::first(blk, u, v), Sweep<M>::last(blk, u, v), dx);
-    unsigned ndx = 0u, nxm = 0u;
-    if (active) {
-#pragma unroll
-      for (int t = 0; t < M; ++t) {
-        const double xn = px[t * es] + f2d(dx[t]);
-        px[t * es] = xn;
-        ndx = max(ndx, abs_bits(dx[t]));
-        nxm = max(nxm, abs_bits(__double2float_rn(xn)));
+  for (int64_t g = blockIdx.x / C; g < n_groups; g += n_clusters) {
+    const int64_t line0 = g * kTreeLines;
+    const bool active = line0 + j < A.lay.n_lines;
+    const bool reporter = rank == 0 && p == 0 && active;  // one thread per line reports
+    double* px = (double*)A.x + A.lay.off(active ? line0 + j : 0) + (int64_t)kg * M * es;
+    const int c_in = (int)(line0 % ic), c_out = (int)(line0 / ic), c_p = rank * kTreeParts;
+    if (tid == 0) {
+      bulk_wait_read_all();  // the previous tile's x store has read the a and b tiles
+      mbar_arrive_expect_tx(&bar, 5u * M * 1024u);
+      tma_load_4d(ta, &maps.a, &bar, c_in, c_out, c_p, 0);
+      tma_load_4d(tb, &maps.b, &bar, c_in, c_out, c_p, 0);
+      tma_load_4d(tc, &maps.c, &bar, c_in, c_out, c_p, 0);
+      tma_load_4d(td, &maps.d, &bar, c_in, c_out, c_p, 0);
+      tma_load_4d(td + M * 128, &maps.d, &bar, c_in + 16, c_out, c_p, 0);
+      if (g + n_clusters < n_groups) {  // the next group of this cluster, into L2
+        const int64_t l1 = (g + n_clusters) * kTreeLines;
+        const int n_in = (int)(l1 % ic), n_out = (int)(l1 / ic);
+        tma_prefetch_4d(&maps.a, n_in, n_out, c_p, 0);
+        tma_prefetch_4d(&maps.b, n_in, n_out, c_p, 0);
+        tma_prefetch_4d(&maps.c, n_in, n_out, c_p, 0);
+        tma_prefetch_4d(&maps.d, n_in, n_out, c_p, 0);
+        tma_prefetch_4d(&maps.d, n_in + 16, n_out, c_p, 0);
       }
     }
-    unsigned* nb = norms + (it & 1) * C * kTreeNormPitch;
-    tree_norms_push<C>(line_max(ndx), line_max(nxm), nb, &xbar[2 + (it & 1)], rank, p, j);
-    tree_norms_read<C>(gdx, gxm, nb, &xbar[2 + (it & 1)], (uint32_t)((it - 1) >> 1) & 1u, p, j, alive, A.st);
-    line_done = tree_line_done(gdx, gxm, prev, active, A.tol, reporter, A.st);
-    all_done = __syncthreads_and(line_done) != 0;
+    if (!mbar_wait_bounded(&bar, tph, kTmaWaitPolls) && alive) {
+      alive = false;
+      report_error(A.st, 6);
+    }
+    tph ^= 1u;
+
+    // ---------------- pass 0: float solve with the float part of d
+    float x0[M];
+    float u0, v0;
+    unsigned nx;
+    {
+      Sweep<M> S;
+#pragma unroll
+      for (int t = 0; t < M; ++t) {
+        float a = ra[t * 256], b = rb[t * 256], c = rc[t * 256];
+        if (t == 0 && first_part) a = 0.f;
+        if (t == M - 1 && last_part) c = 0.f;
+        const ff dd = split_f64(rd[t * 128]);
+        rd2[t * 128] = make_float2(dd.h, dd.l);  // same thread, same 8 bytes: read before write
+        S.row(t, a, b, c, dd.h);
+      }
+      const Blk blk = S.block();
+      if (!started) {
+        cluster_wait();  // every CTA of the cluster has started
+        started = true;
+      }
+      unsigned unused;
+      float xs_c, xe_c;
+      tree_stage_b<C>(blk, 0u, slots, &xbar[0], xph0 & 1u, rank, p, jj, j, u0, v0, xs_c, xe_c, unused, alive, A.st);
+      ++xph0;
+      // Boundary unknowns exactly as the neighbours will see them in the residual: at a CTA edge
+      // the cluster tree's values, elsewhere the partition's own block form.
+      const float xs = (p == 0 && rank > 0) ? xs_c : Sweep<M>::first(blk, u0, v0);
+      const float xe = (p == kTreeParts - 1 && rank < C - 1) ? xe_c : Sweep<M>::last(blk, u0, v0);
+      S.solve(xs, xe, x0);
+      // inside the CTA the neighbours' values come from the neighbouring lanes
+      const float from_prev = __shfl_up_sync(~0u, x0[M - 1], 4), from_next = __shfl_down_sync(~0u, x0[0], 4);
+      if (p > 0) u0 = from_prev;
+      if (p < kTreeParts - 1) v0 = from_next;
+      nx = 0u;
+#pragma unroll
+      for (int t = 0; t < M; ++t) nx = max(nx, abs_bits(x0[t]));
+      nx = line_max(nx);  // this CTA's rows of the line
+    }
+    // at least one correction always runs (the host passes max_iters >= 1): every tile makes the
+    // same three exchanges, so no CTA can send into a buffer another CTA is still reading
+    {
+      // ---------------- pass 1: correction for r = d - A x_0, x = x_0 + dx
+      unsigned prev, gdx, gxm;
+      {
+        Sweep<M> S;
+#pragma unroll
+        for (int t = 0; t < M; ++t) {
+          float a = ra[t * 256], b = rb[t * 256], c = rc[t * 256];
+          if (t == 0 && first_part) a = 0.f;
+          if (t == M - 1 && last_part) c = 0.f;
+          const float2 dd = rd2[t * 128];
+          const float xm = t == 0 ? u0 : x0[t > 0 ? t - 1 : 0];
+          const float xp = t == M - 1 ? v0 : x0[t < M - 1 ? t + 1 : 0];
+          S.row(t, a, b, c, residual_f(a, b, c, dd.x, dd.y, xm, x0[t], xp));
+        }
+        const Blk blk = S.block();
+        float u, v, xs_c, xe_c;
+        tree_stage_b<C>(blk, nx, slots + C * kTreeSlotPitch, &xbar[1], xph1 & 1u, rank, p, jj, j, u, v, xs_c, xe_c,
+                        prev, alive, A.st);  // prev: line max |x_0|
+        ++xph1;
+        float dx[M];
+        S.solve(Sweep<M>::first(blk, u, v), Sweep<M>::last(blk, u, v), dx);
+        unsigned ndx = 0u;
+#pragma unroll
+        for (int t = 0; t < M; ++t) ndx = max(ndx, abs_bits(dx[t]));
+        tree_norms_push<C>(line_max(ndx), nx, norms + C * kTreeNormPitch, &xbar[3], rank, p, j);
+        // Every thread of the CTA has sent its block (the exchange wait above needed all of
+        // them), so all reads of the a and b tiles in this pass are done: x goes there.
+#pragma unroll
+        for (int t = 0; t < M; ++t) rx[t * 128] = f2d(x0[t]) + f2d(dx[t]);  // exact widenings, one FP64 add
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {  // out-of-range lines of a partial group are not written
+          tma_store_4d(&maps.x, tx, c_in, c_out, c_p, 0);
+          tma_store_4d(&maps.x, tx + M * 128, c_in + 16, c_out, c_p, 0);
+          bulk_commit();
+        }
+        tree_norms_read<C>(gdx, gxm, norms + C * kTreeNormPitch, &xbar[3], xph3 & 1u, p, j, alive, A.st);
+        ++xph3;
+      }
+      bool line_done = tree_line_done(gdx, gxm, prev, active, A.tol, reporter, A.st);
+      bool all_done = __syncthreads_and(line_done) != 0;
+
+      // ---------------- later corrections (rare): x re-read from global memory
+      int it = 1;
+      while (!all_done && it < A.max_iters) {
+        ++it;
+        if (tid == 0) {
+          bulk_wait_all();  // x of pass 1 is in global memory
+          fence_proxy_async_global();
+          mbar_arrive_expect_tx(&bar, 2u * M * 1024u);  // a and b again (x went through their tiles)
+          tma_load_4d(ta, &maps.a, &bar, c_in, c_out, c_p, 0);
+          tma_load_4d(tb, &maps.b, &bar, c_in, c_out, c_p, 0);
+        }
+        if (!mbar_wait_bounded(&bar, tph, kTmaWaitPolls) && alive) {
+          alive = false;
+          report_error(A.st, 6);
+        }
+        tph ^= 1u;
+        cluster_arrive();  // x of the previous pass, written by every CTA, visible to all
+        cluster_wait();
+        Sweep<M> S;
+        ff xm{0.f, 0.f}, xc{0.f, 0.f}, xe{0.f, 0.f};
+        if (active) {
+          if (!first_part) xm = split_f64(px[-es]);
+          if (!last_part) xe = split_f64(px[M * es]);
+          xc = split_f64(px[0]);
+        }
+#pragma unroll
+        for (int t = 0; t < M; ++t) {
+          float a = ra[t * 256], b = rb[t * 256], c = rc[t * 256];
+          if (t == 0 && first_part) a = 0.f;
+          if (t == M - 1 && last_part) c = 0.f;
+          const float2 dd = rd2[t * 128];
+          const ff xn = t == M - 1 ? xe : (active ? split_f64(px[(t + 1) * es]) : ff{0.f, 0.f});
+          S.row(t, a, b, c, residual_ff(a, b, c, ff{dd.x, dd.y}, xm, xc, xn));
+          xm = xc;
+          xc = xn;
+        }
+        const Blk blk = S.block();
+        float u, v, xs_c, xe_c;
+        unsigned unused;
+        // pass `it` uses the buffers of its parity; the phase counters follow each mbarrier
+        const int q = it & 1;
+        tree_stage_b<C>(blk, 0u, slots + q * C * kTreeSlotPitch, &xbar[q], (q ? xph1 : xph0) & 1u, rank, p, jj, j, u,
+                        v, xs_c, xe_c, unused, alive, A.st);
+        if (q) ++xph1; else ++xph0;
+        float dx[M];
+        S.solve(Sweep<M>::first(blk, u, v), Sweep<M>::last(blk, u, v), dx);
+        unsigned ndx = 0u, nxm = 0u;
+        if (active) {
+#pragma unroll
+          for (int t = 0; t < M; ++t) {
+            const double xn = px[t * es] + f2d(dx[t]);
+            px[t * es] = xn;
+            ndx = max(ndx, abs_bits(dx[t]));
+            nxm = max(nxm, abs_bits(__double2float_rn(xn)));
+          }
+        }
+        unsigned* nb = norms + q * C * kTreeNormPitch;
+        tree_norms_push<C>(line_max(ndx), line_max(nxm), nb, &xbar[2 + q], rank, p, j);
+        tree_norms_read<C>(gdx, gxm, nb, &xbar[2 + q], (q ? xph3 : xph2) & 1u, p, j, alive, A.st);
+        if (q) ++xph3; else ++xph2;
+        line_done = tree_line_done(gdx, gxm, prev, active, A.tol, reporter, A.st);
+        all_done = __syncthreads_and(line_done) != 0;
+      }
+      if (reporter) {
+        report_iters(A.st, it);
+        if (!line_done) report_error(A.st, 7);
+      }
+    }
+    // the next TMA load rewrites the tile: order this tile's generic-proxy accesses before it
+    fence_proxy_async_smem();
+    __syncthreads();
   }
-  if (reporter) {
-    report_iters(A.st, it);
-    if (!line_done) report_error(A.st, 7);
-  }
+  if (!started) cluster_wait();  // a CTA without a group still completes the start-up barrier
+  if (tid == 0) bulk_wait_all();  // the last x store has been written
+  // every store into this CTA's shared memory has arrived: each exchange was waited for
 }
 
 // compiled geometries: (rows per partition M, cluster size C); a line spans n = 8 C M rows.

@@ -302,6 +302,7 @@ size_t tree_smem(int M, int C) {
 #undef TDMA_TR_SMEM
   return 0;
 }
+int64_t tree_resident_clusters(int M, int C, size_t smem);
 bool refine_tree_config(const tdma_desc_t& d, int P_req, tdma_config_t& c) {
   // TDMA_DISABLE_TREE=1 leaves these shapes to the cluster kernel with serial Stage B
   if (const char* e = std::getenv("TDMA_DISABLE_TREE")) if (e[0] == '1') return false;
@@ -313,8 +314,11 @@ bool refine_tree_config(const tdma_desc_t& d, int P_req, tdma_config_t& c) {
   t.rows_per_thread = M;
   t.lines_per_block = kTreeLines;
   t.threads_per_block = 256;
-  t.blocks = (int32_t)(C * ((d.n_lines + kTreeLines - 1) / kTreeLines));
   t.smem_bytes = (int64_t)tree_smem(M, C);
+  // persistent grid: the clusters that fit on the GPU at once, at most one per line group
+  const int64_t groups = (d.n_lines + kTreeLines - 1) / kTreeLines;
+  const int64_t resident = tree_resident_clusters(M, C, (size_t)t.smem_bytes);
+  t.blocks = (int32_t)(C * (resident > 0 ? std::min(groups, resident) : groups));
   t.variant = TDMA_VARIANT_REFINE_TREE;
   if (!tma_layout_ok(d, t)) return false;
   if (d.n_lines < kTreeLines) return false;  // a cluster needs a full line group
@@ -348,6 +352,34 @@ template <class K> cudaError_t set_smem(K kernel, size_t bytes) {
   if (e != cudaSuccess) return e;
   if ((size_t)fa.maxDynamicSharedSizeBytes >= bytes) return cudaSuccess;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Clusters of the merge-tree kernel that fit on the current device at once (0 if unknown).
+int64_t tree_resident_clusters(int M, int C, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int>, int64_t> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  const auto key = std::make_tuple(dev, M, C);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  int n = 0;
+#define TDMA_OCC_TR(MM, CC)                                                         \
+  if (M == MM && C == CC && set_smem(refine_tree_kernel<MM, CC>, smem) == cudaSuccess) \
+    if (cudaOccupancyMaxActiveClusters(&n, refine_tree_kernel<MM, CC>, &cfg) != cudaSuccess) n = 0;
+  TDMA_REFINE_TREE_SHAPES(TDMA_OCC_TR)
+#undef TDMA_OCC_TR
+  (void)cudaGetLastError();
+  std::lock_guard<std::mutex> lock(mu);
+  cache[key] = n;
+  return n;
 }
 
 cudaError_t launch_forward(const tdma_plan_s* p, const Args& A, cudaStream_t s) {
@@ -416,7 +448,8 @@ cudaError_t launch_forward(const tdma_plan_s* p, const Args& A, cudaStream_t s) 
       const bool ok = encode_map(&maps.a, A.a, false, p->desc, c, kTreeParts, 32, true) &&
                       encode_map(&maps.b, A.b, false, p->desc, c, kTreeParts, 32, true) &&
                       encode_map(&maps.c, A.c, false, p->desc, c, kTreeParts, 32, true) &&
-                      encode_map(&maps.d, A.d, true, p->desc, c, kTreeParts, 16, true);
+                      encode_map(&maps.d, A.d, true, p->desc, c, kTreeParts, 16, true) &&
+                      encode_map(&maps.x, A.x, true, p->desc, c, kTreeParts, 16, true);
       if (!ok) return cudaErrorInvalidValue;
 #define TDMA_LAUNCH_TR(MM, CC)                                        \
   if (c.rows_per_thread == MM && C == CC) {                            \

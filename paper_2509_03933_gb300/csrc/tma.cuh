@@ -44,6 +44,13 @@ TDMA_DEV void tma_load_4d(void* dst, const CUtensorMap* map, uint64_t* bar, int 
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
       : "memory");
 }
+// Prefetch a 4D tile into L2 (no shared-memory destination, no completion to wait for).
+TDMA_DEV void tma_prefetch_4d(const CUtensorMap* map, int c0, int c1, int c2, int c3) {
+  asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+               : "memory");
+}
 // 4D tiled TMA store from shared memory (bulk-group completion).
 TDMA_DEV void tma_store_4d(const CUtensorMap* map, const void* src, int c0, int c1, int c2, int c3) {
   asm volatile(
@@ -54,6 +61,10 @@ TDMA_DEV void tma_store_4d(const CUtensorMap* map, const void* src, int c0, int 
 }
 TDMA_DEV void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 TDMA_DEV void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// Wait until every committed bulk store of this thread has been performed (written).
+TDMA_DEV void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Order completed async-proxy (TMA) writes to global memory before later generic-proxy accesses.
+TDMA_DEV void fence_proxy_async_global() { asm volatile("fence.proxy.async.global;" ::: "memory"); }
 // Order generic-proxy shared-memory writes before a following async-proxy (TMA) read.
 TDMA_DEV void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 

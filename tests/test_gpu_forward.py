@@ -160,10 +160,12 @@ def test_refine_tile_kernels_z_lines(n, lines):
 
 
 @pytest.mark.parametrize("tree", [True, False])
-@pytest.mark.parametrize("n,lines", [(1024, 96), (512, 40), (256, 32)])
+@pytest.mark.parametrize("n,lines", [(1024, 96), (512, 40), (256, 32), (512, 4100), (256, 6400)])
 def test_cluster_refine_kernels(monkeypatch, tree, n, lines):
     # lines of n = 8 C M rows spread over a CTA cluster: the merge-tree kernel (default) and,
-    # with it switched off, the kernel with a serial Stage B; 40 lines leave a partial cluster
+    # with it switched off, the kernel with a serial Stage B; 40 and 4100 lines leave a partial
+    # group; 4100 and 6400 lines give more groups than clusters fit on the GPU, so the persistent
+    # clusters of the merge-tree kernel take several groups each
     if not tree:
         monkeypatch.setenv("TDMA_DISABLE_TREE", "1")
     g = synth.grid_general((n, lines), 0, 23 + n, device="cpu", fp32_coefficients=True)
@@ -176,6 +178,38 @@ def test_cluster_refine_kernels(monkeypatch, tree, n, lines):
     st, iters = plan.last_error()
     assert st == 0 and iters == 1
     ref = O.thomas(*(_np_lines(t, 0) for t in (a, b, c, d)))
+    assert O.rel_l2(_np_lines(x, 0), ref) <= TOL["f32r"]
+
+
+@pytest.mark.parametrize("tree", [True, False])
+def test_cluster_refine_more_corrections_and_in_place(monkeypatch, tree):
+    # weak diagonal dominance (b = |a| + |c| + 0.02) needs several corrections; an unreachable
+    # tolerance runs max_refine_iters of them and reports TDMA_ERR_NOT_CONVERGED; x may alias d
+    if not tree:
+        monkeypatch.setenv("TDMA_DISABLE_TREE", "1")
+    n, lines = 1024, 4100
+    a = (synth.uniform(29, synth.AID["a"], torch.arange(n * lines)) - 1.0).float().view(n, lines)
+    c = (synth.uniform(29, synth.AID["c"], torch.arange(n * lines)) - 1.0).float().view(n, lines)
+    b = (a.abs() + c.abs() + 0.02).float()
+    xt = 2.0 * synth.uniform(29, synth.AID["x_true"], torch.arange(n * lines)).view(n, lines) - 1.0
+    d = synth.apply_tridiag(a.double(), b.double(), c.double(), xt, 0)
+    a, b, c, d = a.cuda(), b.cuda(), c.cuda(), d.cuda()
+    ref = O.thomas(*(_np_lines(t, 0) for t in (a, b, c, d)))
+    plan = tdma.Plan(*tdma.line_layout(d, 0), precision="f32r")
+    assert plan.config["variant"] == (8 if tree else 6)
+    x = torch.empty_like(d)
+    plan.solve(a, b, c, d, x)
+    st, iters = plan.last_error()
+    assert st == 0 and iters >= 2
+    assert O.rel_l2(_np_lines(x, 0), ref) <= TOL["f32r"]
+    dd = d.clone()
+    plan.solve(a, b, c, dd, dd)  # in place
+    assert plan.last_error()[0] == 0
+    assert O.rel_l2(_np_lines(dd, 0), ref) <= TOL["f32r"]
+    stiff = tdma.Plan(*tdma.line_layout(d, 0), precision="f32r", max_refine_iters=3, refine_tol=1e-30)
+    stiff.solve(a, b, c, d, x)
+    st, iters = stiff.last_error()
+    assert st == 7 and iters == 3
     assert O.rel_l2(_np_lines(x, 0), ref) <= TOL["f32r"]
 
 
