@@ -326,9 +326,11 @@ template <int M, int C>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
     refine_tree_kernel(const Args A, const __grid_constant__ TmaMaps maps) {
   static_assert(C == 2 || C == 4 || C == 8, "cluster size");
-  static_assert(M >= 3, "rows per partition");
+  static_assert(M >= 4 && M % 2 == 0, "rows per partition");
+  constexpr int H = M / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];  // aligned to 1 KB below
-  __shared__ __align__(8) uint64_t bar;
+  // tile mbarriers: rows [0, M/2) and [M/2, M) of every array arrive on bar[0] and bar[1]
+  __shared__ __align__(8) uint64_t bar[2];
   // exchange mbarriers: [0], [1] block slots of even / odd passes, [2], [3] norm slots
   __shared__ __align__(8) uint64_t xbar[4];
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, p = lane >> 2, jj = lane & 3;
@@ -362,7 +364,8 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
   const int64_t es = A.lay.es, ic = A.lay.ic;
 
   if (tid == 0) {
-    mbar_init(&bar, 1);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
 #pragma unroll
     for (int i = 0; i < 4; ++i) mbar_init(&xbar[i], 1);
     mbar_fence_init();
@@ -372,7 +375,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
   // store into another CTA's shared memory
   cluster_arrive();
   bool started = false, alive = true;
-  uint32_t tph = 0, xph0 = 0, xph1 = 0, xph2 = 0, xph3 = 0;  // phases of bar and xbar[0..3]
+  uint32_t tph0 = 0, tph1 = 0, xph0 = 0, xph1 = 0, xph2 = 0, xph3 = 0;  // phases of bar[0..1], xbar[0..3]
 
   for (int64_t g = blockIdx.x / C; g < n_groups; g += n_clusters) {
     const int64_t line0 = g * kTreeLines;
@@ -382,27 +385,33 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
     const int c_in = (int)(line0 % ic), c_out = (int)(line0 / ic), c_p = rank * kTreeParts;
     if (tid == 0) {
       bulk_wait_read_all();  // the previous tile's x store has read the a and b tiles
-      mbar_arrive_expect_tx(&bar, 5u * M * 1024u);
-      tma_load_4d(ta, &maps.a, &bar, c_in, c_out, c_p, 0);
-      tma_load_4d(tb, &maps.b, &bar, c_in, c_out, c_p, 0);
-      tma_load_4d(tc, &maps.c, &bar, c_in, c_out, c_p, 0);
-      tma_load_4d(td, &maps.d, &bar, c_in, c_out, c_p, 0);
-      tma_load_4d(td + M * 128, &maps.d, &bar, c_in + 16, c_out, c_p, 0);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {  // row half h: rows [h H, (h + 1) H), 1 KB per row
+        mbar_arrive_expect_tx(&bar[h], 5u * H * 1024u);
+        tma_load_4d(ta + h * H * 256, &maps.a, &bar[h], c_in, c_out, c_p, h * H);
+        tma_load_4d(tb + h * H * 256, &maps.b, &bar[h], c_in, c_out, c_p, h * H);
+        tma_load_4d(tc + h * H * 256, &maps.c, &bar[h], c_in, c_out, c_p, h * H);
+        tma_load_4d(td + h * H * 128, &maps.d, &bar[h], c_in, c_out, c_p, h * H);
+        tma_load_4d(td + M * 128 + h * H * 128, &maps.d, &bar[h], c_in + 16, c_out, c_p, h * H);
+      }
       if (g + n_clusters < n_groups) {  // the next group of this cluster, into L2
         const int64_t l1 = (g + n_clusters) * kTreeLines;
         const int n_in = (int)(l1 % ic), n_out = (int)(l1 / ic);
-        tma_prefetch_4d(&maps.a, n_in, n_out, c_p, 0);
-        tma_prefetch_4d(&maps.b, n_in, n_out, c_p, 0);
-        tma_prefetch_4d(&maps.c, n_in, n_out, c_p, 0);
-        tma_prefetch_4d(&maps.d, n_in, n_out, c_p, 0);
-        tma_prefetch_4d(&maps.d, n_in + 16, n_out, c_p, 0);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          tma_prefetch_4d(&maps.a, n_in, n_out, c_p, h * H);
+          tma_prefetch_4d(&maps.b, n_in, n_out, c_p, h * H);
+          tma_prefetch_4d(&maps.c, n_in, n_out, c_p, h * H);
+          tma_prefetch_4d(&maps.d, n_in, n_out, c_p, h * H);
+          tma_prefetch_4d(&maps.d, n_in + 16, n_out, c_p, h * H);
+        }
       }
     }
-    if (!mbar_wait_bounded(&bar, tph, kTmaWaitPolls) && alive) {
+    if (!mbar_wait_bounded(&bar[0], tph0, kTmaWaitPolls) && alive) {
       alive = false;
       report_error(A.st, 6);
     }
-    tph ^= 1u;
+    tph0 ^= 1u;
 
     // ---------------- pass 0: float solve with the float part of d
     float x0[M];
@@ -412,6 +421,13 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
       Sweep<M> S;
 #pragma unroll
       for (int t = 0; t < M; ++t) {
+        if (t == H) {  // the second half of the rows (the first half is being swept meanwhile)
+          if (!mbar_wait_bounded(&bar[1], tph1, kTmaWaitPolls) && alive) {
+            alive = false;
+            report_error(A.st, 6);
+          }
+          tph1 ^= 1u;
+        }
         float a = ra[t * 256], b = rb[t * 256], c = rc[t * 256];
         if (t == 0 && first_part) a = 0.f;
         if (t == M - 1 && last_part) c = 0.f;
@@ -494,15 +510,18 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
         if (tid == 0) {
           bulk_wait_all();  // x of pass 1 is in global memory
           fence_proxy_async_global();
-          mbar_arrive_expect_tx(&bar, 2u * M * 1024u);  // a and b again (x went through their tiles)
-          tma_load_4d(ta, &maps.a, &bar, c_in, c_out, c_p, 0);
-          tma_load_4d(tb, &maps.b, &bar, c_in, c_out, c_p, 0);
+          mbar_arrive_expect_tx(&bar[0], 2u * M * 1024u);  // a and b again (x went through their tiles)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            tma_load_4d(ta + h * H * 256, &maps.a, &bar[0], c_in, c_out, c_p, h * H);
+            tma_load_4d(tb + h * H * 256, &maps.b, &bar[0], c_in, c_out, c_p, h * H);
+          }
         }
-        if (!mbar_wait_bounded(&bar, tph, kTmaWaitPolls) && alive) {
+        if (!mbar_wait_bounded(&bar[0], tph0, kTmaWaitPolls) && alive) {
           alive = false;
           report_error(A.st, 6);
         }
-        tph ^= 1u;
+        tph0 ^= 1u;
         cluster_arrive();  // x of the previous pass, written by every CTA, visible to all
         cluster_wait();
         Sweep<M> S;
@@ -555,9 +574,8 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
         if (!line_done) report_error(A.st, 7);
       }
     }
-    // the next TMA load rewrites the tile: order this tile's generic-proxy accesses before it
-    fence_proxy_async_smem();
-    __syncthreads();
+    // The next TMA load rewrites the tile. The generic-proxy writes to it (d split in place, x)
+    // were fenced before the x store; the last __syncthreads_and above ordered every read.
   }
   if (!started) cluster_wait();  // a CTA without a group still completes the start-up barrier
   if (tid == 0) bulk_wait_all();  // the last x store has been written

@@ -219,7 +219,7 @@ bool tma_layout_ok(const tdma_desc_t& d, const tdma_config_t& c) {
 }
 
 bool encode_map(CUtensorMap* map, const void* ptr, bool f64, const tdma_desc_t& d, const tdma_config_t& c,
-                int box_partitions = 0, int box_lines = 0, bool swizzle128 = false) {
+                int box_partitions = 0, int box_lines = 0, bool swizzle128 = false, int box_rows = 0) {
   EncodeTiledFn fn = encode_fn();
   if (!fn || !aligned(ptr, 16)) return false;
   const cuuint64_t eb = f64 ? 8 : 4;
@@ -230,7 +230,8 @@ bool encode_map(CUtensorMap* map, const void* ptr, bool f64, const tdma_desc_t& 
   cuuint64_t os = outer > 1 ? (cuuint64_t)d.outer_stride * eb : ((cuuint64_t)inner * eb + 15) / 16 * 16;
   cuuint64_t strides[3] = {os, (cuuint64_t)(m * d.elem_stride) * eb, (cuuint64_t)d.elem_stride * eb};
   cuuint32_t box[4] = {(cuuint32_t)(box_lines > 0 ? box_lines : c.lines_per_block), 1,
-                       (cuuint32_t)(box_partitions > 0 ? box_partitions : c.partitions), (cuuint32_t)m};
+                       (cuuint32_t)(box_partitions > 0 ? box_partitions : c.partitions),
+                       (cuuint32_t)(box_rows > 0 ? box_rows : m)};
   cuuint32_t estr[4] = {1, 1, 1, 1};
   const CUresult r = fn(map, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
                         const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -445,10 +446,11 @@ cudaError_t launch_forward(const tdma_plan_s* p, const Args& A, cudaStream_t s) 
       TmaMaps maps;
       std::memset(&maps, 0, sizeof(maps));
       const int C = c.partitions / kTreeParts;
-      const bool ok = encode_map(&maps.a, A.a, false, p->desc, c, kTreeParts, 32, true) &&
-                      encode_map(&maps.b, A.b, false, p->desc, c, kTreeParts, 32, true) &&
-                      encode_map(&maps.c, A.c, false, p->desc, c, kTreeParts, 32, true) &&
-                      encode_map(&maps.d, A.d, true, p->desc, c, kTreeParts, 16, true) &&
+      const int H = c.rows_per_thread / 2;  // tiles travel in two halves of rows
+      const bool ok = encode_map(&maps.a, A.a, false, p->desc, c, kTreeParts, 32, true, H) &&
+                      encode_map(&maps.b, A.b, false, p->desc, c, kTreeParts, 32, true, H) &&
+                      encode_map(&maps.c, A.c, false, p->desc, c, kTreeParts, 32, true, H) &&
+                      encode_map(&maps.d, A.d, true, p->desc, c, kTreeParts, 16, true, H) &&
                       encode_map(&maps.x, A.x, true, p->desc, c, kTreeParts, 16, true);
       if (!ok) return cudaErrorInvalidValue;
 #define TDMA_LAUNCH_TR(MM, CC)                                        \
