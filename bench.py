@@ -20,6 +20,7 @@ import hashlib
 import json
 import math
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -130,24 +131,44 @@ class ClockSampler:
 
 
 def traffic_record(kernel: str):
-    """DRAM bytes per launch from a committed ncu summary, valid only for the current kernel sources."""
+    """DRAM bytes per launch from a committed ncu summary, valid only while the kernel's own sources
+    (its header and everything it includes) are unchanged."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         j = json.load(f)
     rec = j.get(kernel)
-    if not rec or rec.get("source_sha") != source_sha():
+    if not rec or rec.get("source_sha") != source_sha(kernel):
         return None
     return rec
 
 
-def source_sha() -> str:
+KERNEL_SOURCE = {"dc_kernel": "kernels_dc.cuh", "thomas_kernel": "kernels_thomas.cuh",
+                 "refine_kernel": "kernels_refine.cuh", "ragged_refine_kernel": "kernels_ragged.cuh",
+                 "refine_reg_kernel": "kernels_refine_reg.cuh", "refine_tma_fixed_kernel": "kernels_refine_tma.cuh",
+                 "refine_cluster_kernel": "kernels_refine_cluster.cuh", "refine_tree_kernel": "kernels_refine_tree.cuh"}
+
+
+def source_sha(kernel: str) -> str:
+    """Hash of the header that defines ``kernel`` and of the headers it includes, recursively."""
+    dirs = [os.path.join(ROOT, "paper_2509_03933_gb300", "csrc"), os.path.join(ROOT, "include")]
+    todo, seen = [KERNEL_SOURCE.get(kernel, "kernels_refine.cuh")], []
+    while todo:
+        name = todo.pop()
+        if name in seen:
+            continue
+        path = next((os.path.join(d, name) for d in dirs if os.path.exists(os.path.join(d, name))), None)
+        if path is None:
+            continue
+        seen.append(name)
+        with open(path) as fh:
+            todo += re.findall(r'^#include "([^"]+)"', fh.read(), flags=re.M)
     h = hashlib.sha256()
-    cdir = os.path.join(ROOT, "paper_2509_03933_gb300", "csrc")
-    for f in sorted(os.listdir(cdir)):
-        with open(os.path.join(cdir, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+    for name in sorted(seen):
+        path = next(os.path.join(d, name) for d in dirs if os.path.exists(os.path.join(d, name)))
+        with open(path, "rb") as fh:
+            h.update(name.encode() + fh.read())
     return h.hexdigest()[:16]
 
 
