@@ -41,7 +41,7 @@ BYTES_F64 = 40.0    # a, b, c, d double in, x double out
 FP64_OPS_PEAK = 152 * 2 * 2.07e9  # FP64 pipe: 152 SMs x 2 ops/clk x 2.07 GHz (1.25 TFLOP/s, FMA = 2)
 KERNEL_OF_VARIANT = {0: "dc_kernel", 1: "thomas_kernel", 2: "refine_kernel", 3: "ragged_refine_kernel",
                      4: "refine_reg_kernel", 5: "refine_tma_fixed_kernel", 6: "refine_cluster_kernel",
-                     7: "dc_kernel", 8: "refine_tree_kernel"}
+                     7: "dc_kernel", 8: "refine_tree_kernel", 9: "packed_refine_kernel"}
 
 
 def dist_env():
@@ -147,7 +147,8 @@ def traffic_record(kernel: str):
 KERNEL_SOURCE = {"dc_kernel": "kernels_dc.cuh", "thomas_kernel": "kernels_thomas.cuh",
                  "refine_kernel": "kernels_refine.cuh", "ragged_refine_kernel": "kernels_ragged.cuh",
                  "refine_reg_kernel": "kernels_refine_reg.cuh", "refine_tma_fixed_kernel": "kernels_refine_tma.cuh",
-                 "refine_cluster_kernel": "kernels_refine_cluster.cuh", "refine_tree_kernel": "kernels_refine_tree.cuh"}
+                 "refine_cluster_kernel": "kernels_refine_cluster.cuh", "refine_tree_kernel": "kernels_refine_tree.cuh",
+                 "packed_refine_kernel": "kernels_packed.cuh"}
 
 
 def source_sha(kernel: str) -> str:

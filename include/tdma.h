@@ -117,7 +117,8 @@ enum {
   TDMA_VARIANT_REFINE_TMA = 5, /* refinement on a TMA-staged shared-memory tile          */
   TDMA_VARIANT_REFINE_CLUSTER = 6, /* refinement with each line spread over a CTA cluster */
   TDMA_VARIANT_DC_GLOBAL = 7, /* fused Stage A/B/C, Stage A scratch in the workspace        */
-  TDMA_VARIANT_REFINE_TREE = 8 /* refinement over a CTA cluster, Stage B as a merge tree     */
+  TDMA_VARIANT_REFINE_TREE = 8, /* refinement over a CTA cluster, Stage B as a merge tree    */
+  TDMA_VARIANT_PACKED = 9     /* ragged refinement: chunks of packed lines per CTA cluster */
 };
 
 /* Validate `desc`, choose a launch configuration and report the workspace it needs.

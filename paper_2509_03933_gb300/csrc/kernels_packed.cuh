@@ -1,0 +1,628 @@
+// Packed unit-stride lines (ragged batches) with FP32 storage + refinement: one chunk of whole
+// lines per thread-block cluster, Stage B as merge trees over lanes, warps and cluster ranks.
+//
+// Lines packed one after another with unit stride form one long tridiagonal system whose
+// coupling across a line boundary is zero (a_0 = c_{n-1} = 0 of every line). A divide-and-conquer
+// solve of that long system is therefore exactly the set of per-line solves: when the merge of
+// two blocks meets a line boundary, the terms that couple them vanish and the merge only copies.
+// At plan time the lines, in memory order, are cut into chunks of whole, contiguous lines of at
+// most kPackChunk rows; chunk g is solved by one cluster of kPackC CTAs with 256 partitions each
+// (M = ceil(rows / 1024) rows per partition, the last partitions partial or empty), so a chunk
+// of any mix of lengths keeps all threads busy. The paper batches lines of one direction into
+// composite systems (Section 4.2.1); here the batch is a chunk and the composite system is the
+// chunk's rows.
+//
+// Data path per chunk: every CTA copies its segment of a, b, c (float) and d (double) into
+// shared memory with coalesced asynchronous copies, transposed to [row in partition][partition]
+// (pitch 257) so that the 32 lanes of a warp read 32 consecutive words; the next chunk is
+// prefetched into L2 meanwhile. Pass 0 solves with the float part of d; pass 1 solves for the
+// extra-precise residual (float pairs) and corrects; x = x_0 + dx leaves in FP64 through the
+// shared-memory space of a and b, copied out coalesced. Per-line maxima of |x_0| and |dx| go to
+// a per-line table by atomics; after a cluster barrier the thread holding each line's first row
+// applies the stop rule of the other refinement kernels, and a second barrier shares the
+// verdict. Lines that need more corrections (rare) take further passes that read x back from
+// global memory.
+#pragma once
+#include <cooperative_groups.h>
+#include "layout.cuh"
+#include "tma.cuh"
+#include "kernels_refine.cuh"
+#include "merge_tree.cuh"
+
+namespace tdma {
+
+constexpr int kPackC = 4;                    // CTAs per cluster
+constexpr int kPackW = 7;                    // compute warps per CTA
+constexpr int kPackT = 32 * kPackW;          // compute threads (partitions) per CTA
+constexpr int kPackThreads = kPackT + 32;    // + one coordinator warp
+constexpr int kPackM = 20;                   // rows per partition at most
+constexpr int kPackPitch = kPackT + 1;       // shared-memory pitch of one row position
+constexpr int kPackChunk = kPackC * kPackT * kPackM;  // rows per chunk at most (17920)
+constexpr uint32_t kPackWaitPolls = 1u << 16;
+
+struct PackedChunk {
+  int64_t base;   // element index of the chunk's first row
+  int32_t rows;   // rows in the chunk (1..kPackChunk)
+  int32_t M;      // rows per partition: partition k holds rows [k M, min((k + 1) M, rows))
+  int32_t line0;  // position, in memory order, of the chunk's first line (its norm slot)
+  int32_t pad;
+};
+
+// Partition metadata (one pair of words per partition of every chunk):
+//   x bits 0..19  bit t: row t of the partition starts a line
+//   x bit 20      the row after the partition's last row starts a line or lies past the chunk
+//   y             line of the partition's first row, counted from the chunk's first line
+struct PackedTables {
+  const PackedChunk* chunks;
+  const uint2* meta;      // kPackC * kPackT pairs per chunk
+  uint32_t* norms;        // per line in memory order: max |dx|, max |x| (float bits), previous max |dx|
+  int32_t n_chunks;
+};
+
+TDMA_DEV void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+TDMA_DEV void cp_async8(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+TDMA_DEV void cp_async_wait_all() { asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory"); }
+// L2 prefetch of the 16-byte-aligned part of [p, p + bytes)
+TDMA_DEV void prefetch_l2_range(const void* p, int64_t bytes) {
+  const uint64_t s = ((uint64_t)p + 15) & ~(uint64_t)15, e = ((uint64_t)p + bytes) & ~(uint64_t)15;
+  if (e > s)
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(s), "r"((uint32_t)(e - s)) : "memory");
+}
+TDMA_DEV uint32_t ld_relaxed_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+TDMA_DEV void st_cluster_u32(uint32_t addr, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
+
+// Row index i of a CTA segment -> (partition k, row t within it) for M <= 20 and i < 4480:
+// k = floor(i / M) from a 20-bit reciprocal (exact there: i (2^20 / M rounded up) / 2^20
+// overshoots i / M by less than 4480 / 2^20 < 1 / 20).
+TDMA_DEV void seg_row(int i, int M, uint32_t inv, int& k, int& t) {
+  k = (int)(((uint32_t)i * inv) >> 20);
+  t = i - k * M;
+}
+
+// Stage A of one partition of m <= MM rows (runtime m, rows unrolled): the modified Thomas sweep
+// of the merge-tree kernel with the row-1 relation summed in the forward pass.
+template <int MM>
+struct SweepR {
+  float al[MM], ga[MM], de[MM];  // rows 1..m-2
+  float alpha = -1.f, gamma = 0.f, delta = 0.f, F = 0.f, G = 0.f, Q = 1.f;
+  float a0 = 0.f, b0 = 1.f, c0 = 0.f, h0 = 0.f;
+  TDMA_DEV void row(int t, int m, float a, float b, float c, float rhs) {
+    if (t == 0) {
+      a0 = a; b0 = b; c0 = c; h0 = rhs;
+      return;
+    }
+    if (t >= m) return;
+    const float r = rcp(fmaf(-a, gamma, b));
+    const float ar = a * r;
+    alpha = -ar * alpha;
+    gamma = c * r;
+    delta = fmaf(r, rhs, -ar * delta);
+    if (t <= m - 2) {
+      al[t] = alpha; ga[t] = gamma; de[t] = delta;
+      G = fmaf(Q, alpha, G);
+      F = fmaf(Q, delta, F);
+      Q = -Q * gamma;
+    }
+  }
+  // Row t of a further solve with the same matrix: the factors alpha, gamma of the interior rows
+  // (and of the last row, in alpha / gamma) are those of the first solve and stay; only delta and
+  // F are recomputed, with Q regenerated from the kept gammas.
+  TDMA_DEV void row_rhs(int t, int m, float a, float b, float rhs) {
+    if (t == 0) {
+      h0 = rhs;
+      delta = 0.f;
+      F = 0.f;
+      Q = 1.f;
+      return;
+    }
+    if (t >= m) return;
+    const float gp = t >= 2 ? ga[t >= 2 ? t - 1 : 1] : 0.f;  // gamma of row t - 1 (0 before row 1)
+    const float r = rcp(fmaf(-a, gp, b));
+    delta = fmaf(r, rhs, -(a * r) * delta);
+    if (t <= m - 2) {
+      de[t] = delta;
+      F = fmaf(Q, delta, F);
+      Q = -Q * ga[t];
+    }
+  }
+  // Block form of the partition (all zero for an empty one: a decoupled unknown x = 0, which
+  // merges with its neighbours without changing them).
+  TDMA_DEV Blk block(int m) const {
+    if (m <= 0) return Blk{0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (m == 1) {
+      const float ib = rcp(b0);
+      return Blk{h0 * ib, -a0 * ib, -c0 * ib, h0 * ib, -a0 * ib, -c0 * ib};
+    }
+    const float rho = rcp(fmaf(-c0, G, b0));
+    return part_block(rho * a0, rho * (c0 * Q), rho * fmaf(-c0, F, h0), alpha, gamma, delta);
+  }
+  TDMA_DEV static float first(const Blk& b, float u, float v) { return fmaf(b.q1, u, fmaf(b.r1, v, b.p1)); }
+  TDMA_DEV static float last(const Blk& b, float u, float v) { return fmaf(b.q2, u, fmaf(b.r2, v, b.p2)); }
+  // Stage C from the partition's first and last unknowns, handing each row's value to f(t, x_t)
+  // from row m-1 down to row 0 (x_0 = xs; x_{m-1} = xe for m >= 2).
+  template <class Fn>
+  TDMA_DEV void solve_visit(int m, float xs, float xe, Fn&& f) const {
+    float xn = xe;
+#pragma unroll
+    for (int t = MM - 1; t >= 0; --t) {
+      if (t < m) {
+        float v;
+        if (t == 0) v = xs;
+        else if (t == m - 1) v = xe;
+        else v = fmaf(-ga[t > 0 ? t : 1], xn, fmaf(-al[t > 0 ? t : 1], xs, de[t > 0 ? t : 1]));
+        xn = v;
+        f(t, v);
+      }
+    }
+  }
+  // Stage C from the partition's first and last unknowns (x[0] = xs; x[m-1] = xe for m >= 2)
+  TDMA_DEV void solve(int m, float xs, float xe, float (&x)[MM]) const {
+    x[0] = xs;
+    float xn = xe;
+#pragma unroll
+    for (int t = MM - 1; t >= 1; --t) {
+      if (t == m - 1) {
+        x[t] = xe;
+      } else if (t < m - 1) {
+        xn = fmaf(-ga[t], xn, fmaf(-al[t], xs, de[t]));
+        x[t] = xn;
+      }
+    }
+  }
+};
+
+// Stage B of one pass, split between the compute warps and the coordinator warp of the CTA.
+//   1. compute warps: 5-level merge tree over each warp's 32 partitions (shuffles); lane 0 puts
+//      the warp's block into shared memory and arrives on named barrier 1;
+//   2. coordinator: merges the 7 warp blocks, sends the CTA block into the shared memory of
+//      every CTA of the cluster (st.async completing on the receiver's mbarrier), merges the C
+//      CTA blocks (every CTA computes the same values in the same order), walks both trees back
+//      down and leaves, per warp, its outside neighbours (u, v) and its first and last unknowns
+//      exactly as the neighbouring warp or CTA sees them; arrives on named barrier 2;
+//   3. compute warps: the warp's values, then the lane tree back down to the partition.
+// tree_up_full over the 8 slots g = 0..7 of the coordinator's lanes, where slot 7 holds no
+// rows (the CTA has 7 compute warps): it is the identity of the merge, so the level-0 merge of
+// slots 6 and 7 copies block 6, and the down-sweep stops above level 0 for that pair.
+TDMA_DEV Blk tree_up_full_ident7(Blk b, int g, Mrg (&keep)[3]) {
+  // level 0 by hand
+  {
+    const Blk o = shfl_xor_blk(b, 1);
+    const bool in_right = g & 1;
+    const Blk& L = in_right ? o : b;
+    const Blk& R = in_right ? b : o;
+    const float D = rcp(fmaf(-L.r2, R.q1, 1.f));
+    Aff y, z;
+    y.p = D * fmaf(L.r2, R.p1, L.p2);
+    y.q = D * L.q2;
+    y.r = D * (L.r2 * R.r1);
+    z.p = fmaf(R.q1, y.p, R.p1);
+    z.q = R.q1 * y.q;
+    z.r = fmaf(R.q1, y.r, R.r1);
+    Blk nb{fmaf(L.r1, z.p, L.p1), fmaf(L.r1, z.q, L.q1), L.r1 * z.r, fmaf(R.q2, y.p, R.p2), R.q2 * y.q,
+           fmaf(R.q2, y.r, R.r2)};
+    if ((g >> 1) == 3) nb = L;  // slots 6 and 7: the pair is block 6 alone (no level-0 descent)
+    keep[0] = Mrg{y, z};
+    b = nb;
+  }
+  Mrg k2[3];
+  const Blk B = tree_up_full<2, 1>(b, g >> 1, k2);
+  keep[1] = k2[0];
+  keep[2] = k2[1];
+  return B;
+}
+
+TDMA_DEV void named_arrive(int id) { asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(kPackThreads) : "memory"); }
+TDMA_DEV void named_sync(int id) { asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(kPackThreads) : "memory"); }
+
+struct WarpEdge { float u, v, xs, xe; };
+
+TDMA_DEV WarpEdge packed_compute_b(const Blk& blk, float* wsl, const float4* dsl, int w, int lane, float& u,
+                                   float& v) {
+  Aff kl[5];
+  const Blk W = tree_up<5, 0, 5>(blk, lane, kl);
+  if (lane == 0) {
+    float4* s = reinterpret_cast<float4*>(wsl + w * 8);
+    s[0] = make_float4(W.p1, W.q1, W.r1, W.p2);
+    s[1] = make_float4(W.q2, W.r2, 0.f, 0.f);
+  }
+  named_arrive(1);
+  named_sync(2);
+  const float4 e = dsl[w];
+  u = e.x;
+  v = e.y;
+  tree_down<5, 5>(u, v, lane, kl);
+  return WarpEdge{e.x, e.y, e.z, e.w};
+}
+
+template <int C>
+TDMA_DEV void packed_coord_b(const float* wsl, float4* dsl, float* csl, uint64_t* bar, uint32_t phase, int rank,
+                             int lane, bool& alive, DevStatus* st) {
+  constexpr int LC = C == 8 ? 3 : (C == 4 ? 2 : 1);
+  named_sync(1);
+  const float4* sw = reinterpret_cast<const float4*>(wsl + (lane & 7) * 8);
+  const float4 w0 = sw[0], w1 = sw[1];
+  Mrg kw[3];
+  const Blk B = tree_up_full_ident7(Blk{w0.x, w0.y, w0.z, w0.w, w1.x, w1.y}, lane & 7, kw);
+  if (lane == 0) mbar_arrive_expect_tx(bar, (uint32_t)C * 32u);
+  if (lane < C) {  // the CTA block to every CTA of the cluster (slot `rank` there)
+    const uint32_t dst = map_rank(csl + rank * 8, lane), rb = map_rank(bar, lane);
+    st_async4(dst, B.p1, B.q1, B.r1, B.p2, rb);
+    st_async4(dst + 16, B.q2, B.r2, 0.f, 0.f, rb);
+  }
+  if (alive && !mbar_wait_bounded(bar, phase, kPackWaitPolls)) {
+    alive = false;
+    report_error(st, 6);
+  }
+  const float4* sc = reinterpret_cast<const float4*>(csl + (lane & (C - 1)) * 8);
+  const float4 c0 = sc[0], c1 = sc[1];
+  float uq = 0.f, vq = 0.f, xsq = 0.f, xeq = 0.f;
+  {
+    Mrg kc[3];
+    tree_up_full<LC, 0>(Blk{c0.x, c0.y, c0.z, c0.w, c1.x, c1.y}, lane & (C - 1), kc);
+    tree_down_full<LC>(uq, vq, xsq, xeq, lane & (C - 1), kc);  // the chunk ends have u = v = 0
+  }
+  float uc = __shfl_sync(~0u, uq, rank), vc = __shfl_sync(~0u, vq, rank);
+  float xsc = __shfl_sync(~0u, xsq, rank), xec = __shfl_sync(~0u, xeq, rank);
+  // down the warp tree; the pair (6, 7) is block 6 alone, so level 0 leaves its values as they
+  // are, and warp 6 keeps the CTA's last unknown exactly as the cluster tree gave it
+  const int g = lane & 7;
+#pragma unroll
+  for (int l = 2; l >= 0; --l) {
+    if (l == 0 && (g >> 1) == 3) break;
+    const float y = fmaf(kw[l].y.q, uc, fmaf(kw[l].y.r, vc, kw[l].y.p));
+    const float z = fmaf(kw[l].z.q, uc, fmaf(kw[l].z.r, vc, kw[l].z.p));
+    if ((g >> l) & 1) { uc = y; xsc = z; } else { vc = z; xec = y; }
+  }
+  if (lane < kPackW) dsl[lane] = make_float4(uc, vc, xsc, xec);
+  named_arrive(2);
+}
+
+// Segmented maxima of one partition's rows into the per-line table, fed from the last row down:
+// rows of one line form a piece, flushed by an atomic pair when the walk passes the row that
+// starts its line; a warp whose rows all belong to one line reduces first and makes one pair.
+struct LineMax {
+  unsigned pdx, px;
+  int cur;  // line of the rows being accumulated
+  TDMA_DEV void init(uint32_t mask, int m, int line) {
+    pdx = px = 0u;
+    cur = line + __popc(mask & ~1u & ((1u << m) - 1u));
+  }
+  TDMA_DEV void add(int t, uint32_t mask, float dxv, float xv, uint32_t* norms) {
+    pdx = max(pdx, abs_bits(dxv));
+    px = max(px, abs_bits(xv));
+    if (t > 0 && ((mask >> t) & 1u)) {  // row t starts line `cur`: its piece is complete
+      atomicMax(&norms[3 * cur], pdx);
+      atomicMax(&norms[3 * cur + 1], px);
+      pdx = px = 0u;
+      --cur;
+    }
+  }
+  // the piece of row 0 (line `cur`), warp-reduced when the whole warp lies in one line
+  TDMA_DEV void finish(uint32_t mask, int m, int lane, uint32_t* norms) {
+    const bool one_line = __all_sync(~0u, (mask & ~1u) == 0u && (lane == 0 || (mask & 1u) == 0u));
+    if (one_line) {
+#pragma unroll
+      for (int o = 16; o >= 1; o >>= 1) {
+        pdx = max(pdx, __shfl_xor_sync(~0u, pdx, o));
+        px = max(px, __shfl_xor_sync(~0u, px, o));
+      }
+      const int l0 = __shfl_sync(~0u, cur, 0);
+      if (lane == 0) {
+        atomicMax(&norms[3 * l0], pdx);
+        atomicMax(&norms[3 * l0 + 1], px);
+      }
+    } else if (m > 0) {
+      atomicMax(&norms[3 * cur], pdx);
+      atomicMax(&norms[3 * cur + 1], px);
+    }
+  }
+};
+
+// Stop rule for the lines whose first row lies in this partition (after the cluster barrier
+// that completes the atomics): estimated error rho |dx| <= tol |x| with rho = |dx| / |dx_prev|
+// (|dx_prev| = |x_0| after the first correction). Resets the line's maxima for the next pass.
+// Returns true when one of these lines needs another correction.
+TDMA_DEV bool packed_lines_verdict(uint32_t mask, int m, int line, uint32_t* norms, bool first_pass, float tol,
+                                   bool last_pass, DevStatus* st) {
+  bool more = false;
+  uint32_t own = m > 0 ? (mask & ((m >= 32 ? 0u : (1u << m)) - 1u)) : 0u;
+  while (own) {
+    const int t = __ffs(own) - 1;
+    own &= own - 1u;
+    const int L = line + __popc(mask & ~1u & ((2u << t) - 1u));
+    uint32_t* nl = norms + 3 * L;
+    const uint32_t gdx = ld_relaxed_u32(nl), gx = ld_relaxed_u32(nl + 1);
+    const uint32_t prev = first_pass ? gx : ld_relaxed_u32(nl + 2);
+    nl[0] = 0u;
+    nl[1] = 0u;
+    nl[2] = gdx;
+    if (!(bits_finite(gdx) && bits_finite(gx))) {
+      report_error(st, 5);
+      continue;
+    }
+    const float dxn = __uint_as_float(gdx), xn = __uint_as_float(gx), pv = __uint_as_float(prev);
+    const float ratio = pv > 0.f ? dxn / pv : 0.f;
+    const bool done = ratio * dxn <= tol * xn || dxn == 0.f;
+    if (!done) {
+      if (last_pass) report_error(st, 7);
+      else more = true;
+    }
+  }
+  return more;
+}
+
+// One further correction of a partition (rare): x of this partition and its neighbours read back
+// from global memory, residual in float pairs, Stage A/B/C, x += dx written back. Kept out of
+// line so that its registers do not weigh on the two main passes.
+__device__ __noinline__ void packed_later_pass(const PackedTables& PT, const float* ra, const float* rb,
+                                               const float* rc, const float2* rd2, float* wslq, const float4* dslq,
+                                               double* gx, int64_t prow, int w, int lane, int kp, int m,
+                                               uint32_t mask, uint32_t endmask, int line, int row0, int rows) {
+  {
+    SweepR<kPackM> S;
+    ff xm{0.f, 0.f}, xc{0.f, 0.f};
+    if (m > 0) {
+      if (kp > 0) xm = split_f64(__ldcg(gx + prow - 1));
+      xc = split_f64(__ldcg(gx + prow));
+    }
+#pragma unroll
+    for (int t = 0; t < kPackM; ++t) {
+      if (t < m) {
+        float a = ra[t * kPackPitch], b = rb[t * kPackPitch], c = rc[t * kPackPitch];
+        if ((mask >> t) & 1u) a = 0.f;
+        if ((endmask >> t) & 1u) c = 0.f;
+        const float2 dd = rd2[t * kPackPitch];
+        const bool has_next = t + 1 < m || row0 + t + 1 < rows;
+        const ff xn = has_next ? split_f64(__ldcg(gx + prow + t + 1)) : ff{0.f, 0.f};
+        S.row(t, m, a, b, c, residual_ff(a, b, c, ff{dd.x, dd.y}, xm, xc, xn));
+        xm = xc;
+        xc = xn;
+      }
+    }
+    const Blk blk = S.block(m);
+    float u, v;
+    packed_compute_b(blk, wslq, dslq, w, lane, u, v);
+    // Every read of x above happened before its warp arrived on named barrier 1; another
+    // warp writes only after barrier 2, and another CTA only after receiving this CTA's
+    // block, which left after barrier 1.
+    LineMax nm;
+    nm.init(mask, m, line);
+    S.solve_visit(m, SweepR<kPackM>::first(blk, u, v), SweepR<kPackM>::last(blk, u, v), [&](int t, float dxv) {
+      const double xv = __ldcg(gx + prow + t) + f2d(dxv);
+      gx[prow + t] = xv;
+      nm.add(t, mask, dxv, __double2float_rn(xv), PT.norms);
+    });
+    nm.finish(mask, m, lane, PT.norms);
+  }
+}
+
+// Persistent: the grid holds the clusters that fit on the GPU at once; cluster q takes chunks
+// q, q + Q, q + 2Q, ... (Q clusters, chunks sorted longest first at plan time). Warps 0..6 of a
+// CTA compute (one partition per thread), warp 7 coordinates Stage B.
+template <int C>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
+    packed_refine_kernel(const Args A, const PackedTables PT) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t xbar[2];      // exchange mbarriers, by pass parity
+  __shared__ __align__(16) float wsl[2][8 * 8];  // warp blocks (slot 7 unused), by pass parity
+  __shared__ __align__(16) float4 dsl[2][8];     // per warp: u, v, first and last unknowns
+  __shared__ __align__(16) float csl[2][C * 8];  // CTA blocks of the cluster, by pass parity
+  __shared__ uint32_t s_more;                    // epoch stamp: some line of the chunk needs more
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const bool coord = w == kPackW;
+  const int rank = (int)cluster_rank();
+  const int kp = rank * kPackT + tid;  // partition index within the chunk (compute threads)
+  float* ta = reinterpret_cast<float*>(smem_raw);
+  float* tb = ta + kPackM * kPackPitch;
+  float* tc = tb + kPackM * kPackPitch;
+  double* td = reinterpret_cast<double*>(tc + kPackM * kPackPitch);
+  float2* td2 = reinterpret_cast<float2*>(td);
+  double* tx = reinterpret_cast<double*>(ta);  // x leaves through the a and b space
+  const float* fa = (const float*)A.a;
+  const float* fb = (const float*)A.b;
+  const float* fc = (const float*)A.c;
+  const double* gd = (const double*)A.d;
+  double* gx = (double*)A.x;
+
+  if (tid == 0) {
+    mbar_init(&xbar[0], 1);
+    mbar_init(&xbar[1], 1);
+    s_more = 0u;
+    for (int i = 0; i < 8; ++i) wsl[i / 4][7 * 8 + (i & 3)] = 0.f;  // the empty slot 7
+    mbar_fence_init();
+  }
+  __syncthreads();
+  cluster_arrive();  // barriers initialised; the matching wait precedes the first remote store
+  bool started = false, alive = true;
+  uint32_t xph[2] = {0u, 0u};
+  uint32_t epoch = 0u;
+  const int n_clusters = (int)(gridDim.x / C);
+
+  for (int g = (int)(blockIdx.x / C); g < PT.n_chunks; g += n_clusters) {
+    const PackedChunk ch = PT.chunks[g];
+    const int M = ch.M;
+    const uint32_t inv = ((1u << 20) + (uint32_t)M - 1u) / (uint32_t)M;
+    const int seg0 = rank * kPackT * M;
+    const int segn = max(0, min(ch.rows - seg0, kPackT * M));
+    const int m = coord ? 0 : max(0, min(M, segn - tid * M));
+    const uint2 meta = coord ? make_uint2(0u, 0u) : PT.meta[(int64_t)g * (C * kPackT) + kp];
+    const uint32_t mask = meta.x & 0xFFFFFu;
+    const int line = ch.line0 + (int)meta.y;
+    // c = 0 on rows that end a line: row t ends one when row t + 1 starts one
+    const uint32_t endmask = m > 0 ? ((mask >> 1) | (((meta.x >> 20) & 1u) << (m - 1))) : 0u;
+    const int64_t gbase = ch.base + seg0;
+
+    // ---------------- segment into shared memory (transposed), next chunk into L2
+    if (!coord) {
+      for (int i = tid; i < segn; i += kPackT) {
+        int k, t;
+        seg_row(i, M, inv, k, t);
+        const int pos = t * kPackPitch + k;
+        cp_async4(ta + pos, fa + gbase + i);
+        cp_async4(tb + pos, fb + gbase + i);
+        cp_async4(tc + pos, fc + gbase + i);
+        cp_async8(td + pos, gd + gbase + i);
+      }
+    } else if (lane == 0 && g + n_clusters < PT.n_chunks) {
+      const PackedChunk nx = PT.chunks[g + n_clusters];
+      const int s1 = rank * kPackT * nx.M;
+      const int n1 = max(0, min(nx.rows - s1, kPackT * nx.M));
+      if (n1 > 0) {
+        const int64_t b1 = nx.base + s1;
+        prefetch_l2_range(fa + b1, 4ll * n1);
+        prefetch_l2_range(fb + b1, 4ll * n1);
+        prefetch_l2_range(fc + b1, 4ll * n1);
+        prefetch_l2_range(gd + b1, 8ll * n1);
+      }
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    if (!started) {
+      cluster_wait();  // every CTA of the cluster has started: remote stores may begin
+      started = true;
+    }
+    const float* ra = ta + tid;
+    const float* rb = tb + tid;
+    const float* rc = tc + tid;
+    const double* rd = td + tid;
+    float2* rd2 = td2 + tid;
+    const bool edge_s = lane == 0 && kp > 0, edge_e = lane == 31 && kp + 1 < C * kPackT;
+
+    if (coord) {
+      packed_coord_b<C>(wsl[0], dsl[0], csl[0], &xbar[0], xph[0] & 1u, rank, lane, alive, A.st);
+      packed_coord_b<C>(wsl[1], dsl[1], csl[1], &xbar[1], xph[1] & 1u, rank, lane, alive, A.st);
+      ++xph[0];
+      ++xph[1];
+      __syncthreads();  // x staged by the compute warps
+    } else {
+      SweepR<kPackM> S;
+      float x0[kPackM];
+      float u0, v0;
+      // ---------------- pass 0: float solve with the float part of d
+      {
+#pragma unroll
+        for (int t = 0; t < kPackM; ++t) {
+          if (t < m) {
+            float a = ra[t * kPackPitch], b = rb[t * kPackPitch], c = rc[t * kPackPitch];
+            if ((mask >> t) & 1u) a = 0.f;
+            if ((endmask >> t) & 1u) c = 0.f;
+            const ff dd = split_f64(rd[t * kPackPitch]);
+            rd2[t * kPackPitch] = make_float2(dd.h, dd.l);  // same thread, same 8 bytes
+            S.row(t, m, a, b, c, dd.h);
+          }
+        }
+        const Blk blk = S.block(m);
+        float u, v;
+        const WarpEdge e = packed_compute_b(blk, wsl[0], dsl[0], w, lane, u, v);
+        // unknowns at warp and CTA edges exactly as the neighbouring warp computes them
+        const float xs = edge_s ? e.xs : SweepR<kPackM>::first(blk, u, v);
+        const float xe = edge_e ? e.xe : SweepR<kPackM>::last(blk, u, v);
+        S.solve(m, m == 1 && edge_e ? xe : xs, xe, x0);
+        float xl = x0[0];
+#pragma unroll
+        for (int t = 1; t < kPackM; ++t) if (t == m - 1) xl = x0[t];
+        const float from_prev = __shfl_up_sync(~0u, xl, 1), from_next = __shfl_down_sync(~0u, x0[0], 1);
+        u0 = lane == 0 ? e.u : from_prev;
+        v0 = lane == 31 ? e.v : from_next;
+      }
+      // ---------------- pass 1: correction for r = d - A x_0 with the same factors
+      {
+#pragma unroll
+        for (int t = 0; t < kPackM; ++t) {
+          if (t < m) {
+            float a = ra[t * kPackPitch], b = rb[t * kPackPitch], c = rc[t * kPackPitch];
+            if ((mask >> t) & 1u) a = 0.f;
+            if ((endmask >> t) & 1u) c = 0.f;
+            const float2 dd = rd2[t * kPackPitch];
+            const float xm = t == 0 ? u0 : x0[t > 0 ? t - 1 : 0];
+            const float xp = t + 1 < m ? x0[t < kPackM - 1 ? t + 1 : 0] : v0;
+            S.row_rhs(t, m, a, b, residual_f(a, b, c, dd.x, dd.y, xm, x0[t], xp));
+          }
+        }
+        const Blk blk = S.block(m);
+        float u, v;
+        const WarpEdge e = packed_compute_b(blk, wsl[1], dsl[1], w, lane, u, v);
+        const float xs = edge_s ? e.xs : SweepR<kPackM>::first(blk, u, v);
+        const float xe = edge_e ? e.xe : SweepR<kPackM>::last(blk, u, v);
+        // Named barrier 2 of pass 1 completed only after every compute warp arrived on barrier 1,
+        // after its last read of the a and b space: x = x_0 + dx (FP64) goes there.
+        LineMax nm;
+        nm.init(mask, m, line);
+        double* rx = tx + tid;
+        S.solve_visit(m, m == 1 && edge_e ? xe : xs, xe, [&](int t, float dxv) {
+          rx[t * kPackPitch] = f2d(x0[t]) + f2d(dxv);  // exact widenings, one FP64 add
+          nm.add(t, mask, dxv, x0[t], PT.norms);
+        });
+        nm.finish(mask, m, lane, PT.norms);
+      }
+      __syncthreads();
+    }
+    if (!coord) {
+      for (int i = tid; i < segn; i += kPackT) {
+        int k, t;
+        seg_row(i, M, inv, k, t);
+        gx[gbase + i] = tx[t * kPackPitch + k];
+      }
+    }
+    // ---------------- stop rule per line, verdict shared by the cluster
+    ++epoch;
+    cluster_arrive();
+    cluster_wait();  // the atomics of every CTA are complete and visible
+    bool more = !coord && packed_lines_verdict(mask, m, line, PT.norms, true, A.tol, A.max_iters <= 1, A.st);
+    more = __syncthreads_or(more) != 0;
+    if (more && tid < C) st_cluster_u32(map_rank(&s_more, tid), epoch);
+    cluster_arrive();
+    cluster_wait();
+    bool again = s_more == epoch;
+    int it = 1;
+
+    // ---------------- further corrections (rare): x read back from global memory
+    while (again && it < A.max_iters) {
+      ++it;
+      const int q = it & 1;
+      if (!coord) {  // a and b again: x went out through their space
+        for (int i = tid; i < segn; i += kPackT) {
+          int k, t;
+          seg_row(i, M, inv, k, t);
+          const int pos = t * kPackPitch + k;
+          cp_async4(ta + pos, fa + gbase + i);
+          cp_async4(tb + pos, fb + gbase + i);
+        }
+      }
+      cp_async_wait_all();
+      __syncthreads();
+      if (coord) {
+        packed_coord_b<C>(wsl[q], dsl[q], csl[q], &xbar[q], xph[q] & 1u, rank, lane, alive, A.st);
+        ++xph[q];
+        __syncthreads();
+      } else {
+        packed_later_pass(PT, ra, rb, rc, rd2, wsl[q], dsl[q], gx, gbase + (int64_t)tid * M, w, lane, kp, m, mask,
+                          endmask, line, seg0 + tid * M, ch.rows);
+        __syncthreads();
+      }
+      ++epoch;
+      cluster_arrive();
+      cluster_wait();
+      more = !coord && packed_lines_verdict(mask, m, line, PT.norms, false, A.tol, it >= A.max_iters, A.st);
+      more = __syncthreads_or(more) != 0;
+      if (more && tid < C) st_cluster_u32(map_rank(&s_more, tid), epoch);
+      cluster_arrive();
+      cluster_wait();
+      again = s_more == epoch;
+    }
+    if (rank == 0 && tid == 0) report_iters(A.st, it);
+  }
+  if (!started) cluster_wait();  // a cluster without a chunk still completes the start-up barrier
+}
+
+}  // namespace tdma

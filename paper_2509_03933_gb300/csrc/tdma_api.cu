@@ -20,6 +20,7 @@
 #include "kernels_refine_tree.cuh"
 #include "kernels_thomas.cuh"
 #include "kernels_ragged.cuh"
+#include "kernels_packed.cuh"
 #include "kernels_backward.cuh"
 #include "kernels_refine64.cuh"
 
@@ -37,6 +38,9 @@ struct tdma_plan_s {
   size_t r_offset = 0;     // TDMA_F64_REFINE: byte offset of the residual buffer in the workspace
   RaggedTables rt{};       // ragged batches: sorted order, groups, scratch bases, work counter
   void* rt_mem = nullptr;  // one device allocation holding the tables
+  tdma_config_t rcfg{};    // ragged batches: configuration of the group kernels (backward pass)
+  PackedTables pk{};       // ragged F32 + refinement: chunks of packed lines, metadata, line norms
+  void* pk_mem = nullptr;  // one device allocation holding them
 };
 
 namespace {
@@ -481,6 +485,13 @@ cudaError_t launch_forward(const tdma_plan_s* p, const Args& A, cudaStream_t s) 
     }
     case TDMA_VARIANT_THOMAS:
       return launch_thomas(p->desc.precision, p->desc.nrhs, A, c, s);
+    case TDMA_VARIANT_PACKED: {
+      // the per-line maxima start from zero (the kernel also leaves them zero)
+      cudaError_t e = cudaMemsetAsync(p->pk.norms, 0, sizeof(uint32_t) * 3 * (size_t)p->desc.n_lines, s);
+      if (e != cudaSuccess) return e;
+      packed_refine_kernel<kPackC><<<grid, block, sm, s>>>(A, p->pk);
+      break;
+    }
     case TDMA_VARIANT_RAGGED: {
       cudaError_t e = cudaMemsetAsync(p->rt.queue, 0, sizeof(int32_t), s);
       if (e != cudaSuccess) return e;
@@ -544,6 +555,8 @@ cudaError_t prepare_kernel(const tdma_plan_s* p) {
       return prepare_thomas(p->desc.precision, p->desc.nrhs, sm);
     case TDMA_VARIANT_RAGGED:
       return cudaSuccess;
+    case TDMA_VARIANT_PACKED:
+      return set_smem(packed_refine_kernel<kPackC>, sm);
   }
   return cudaSuccess;
 }
@@ -578,7 +591,7 @@ cudaError_t backward_impl(const tdma_plan_s* p, const void* a, const void* b, co
   (void)cudaGetLastError();  // drop a stale non-sticky error left by another runtime call
   cudaError_t e;
   if (d.n == 0) {  // ragged: the same persistent launch on the transposed rows
-    const tdma_config_t& rc = p->cfg;
+    const tdma_config_t& rc = p->rcfg;
     e = cudaMemsetAsync(p->rt.queue, 0, sizeof(int32_t), s);
     if (e != cudaSuccess) return e;
     const size_t sm = (size_t)rc.smem_bytes;
@@ -702,9 +715,114 @@ tdma_status_t build_ragged(tdma_plan_s* p) {
   c.rows_per_thread = kRaggedRowsPerPart;
   c.lines_per_block = groups.empty() ? 1 : groups.front().count;
   p->cfg = c;
+  p->rcfg = c;
   const size_t arrays = d.precision == TDMA_F32_REFINE ? 5 : 3;
   p->workspace = arrays * (size_t)scratch * (d.precision == TDMA_F64 ? 8 : 4);
   return TDMA_OK;
+}
+
+// Ragged F32 + refinement with the chunk kernel: lines in memory order cut into chunks of whole,
+// contiguous lines of at most kPackChunk rows (a gap or a longer line ends a chunk), each chunk
+// with kPackC x kPackT partitions of M = ceil(rows / (kPackC kPackT)) rows and one metadata pair
+// per partition (line starts, line end after the partition, line of its first row). Chunks are
+// ordered longest first. Leaves the plan unchanged (returns false) when the batch does not
+// qualify: other precisions, a line longer than a chunk, overlapping lines, or
+// TDMA_DISABLE_PACKED=1.
+bool build_packed(tdma_plan_s* p) {
+  const tdma_desc_t& d = p->desc;
+  if (const char* e = std::getenv("TDMA_DISABLE_PACKED")) if (e[0] == '1') return false;
+  if (d.precision != TDMA_F32_REFINE || d.nrhs != 1 || d.n_lines < 1 || d.ragged_max_n > kPackChunk) return false;
+  const int64_t L = d.n_lines;
+  if (L >= (1ll << 31)) return false;
+  std::vector<int32_t> len((size_t)L);
+  std::vector<int64_t> off((size_t)L);
+  if (cudaMemcpy(len.data(), d.ragged_lengths, sizeof(int32_t) * L, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(off.data(), d.ragged_offsets, sizeof(int64_t) * L, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return false;
+  std::vector<int32_t> order((size_t)L);
+  for (int64_t i = 0; i < L; ++i) order[i] = (int32_t)i;
+  std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return off[x] < off[y]; });
+  struct Span { int64_t first, count, rows; };
+  std::vector<Span> spans;
+  for (int64_t i = 0; i < L;) {
+    const int64_t n0 = len[order[i]];
+    if (n0 < 1 || n0 > kPackChunk || off[order[i]] < 0) return false;
+    Span sp{i, 1, n0};
+    while (i + sp.count < L) {
+      const int32_t prev = order[i + sp.count - 1], next = order[i + sp.count];
+      if (off[next] < off[prev] + len[prev]) return false;  // overlapping lines
+      if (off[next] != off[prev] + len[prev] || sp.rows + len[next] > kPackChunk) break;
+      sp.rows += len[next];
+      ++sp.count;
+    }
+    spans.push_back(sp);
+    i += sp.count;
+  }
+  std::stable_sort(spans.begin(), spans.end(), [](const Span& x, const Span& y) { return x.rows > y.rows; });
+  constexpr int PPC = kPackC * kPackT;  // partitions per chunk
+  std::vector<PackedChunk> chunks(spans.size());
+  std::vector<uint2> meta(spans.size() * (size_t)PPC);
+  std::vector<int32_t> starts;
+  for (size_t g = 0; g < spans.size(); ++g) {
+    const Span& sp = spans[g];
+    const int rows = (int)sp.rows, M = (rows + PPC - 1) / PPC;
+    chunks[g] = PackedChunk{off[order[sp.first]], rows, M, (int32_t)sp.first, 0};
+    starts.assign(1, 0);  // first row of every line of the chunk, relative to the chunk
+    for (int64_t j = 1; j < sp.count; ++j) starts.push_back(starts.back() + len[order[sp.first + j - 1]]);
+    size_t li = 0;  // line of the current row
+    for (int k = 0; k < PPC; ++k) {
+      const int r0 = k * M, r1 = std::min(rows, r0 + M);
+      uint32_t w = 0;
+      if (r0 < rows) {
+        while (li + 1 < starts.size() && starts[li + 1] <= r0) ++li;
+        for (size_t q = li; q < starts.size() && starts[q] < r1; ++q)
+          if (starts[q] >= r0) w |= 1u << (starts[q] - r0);
+        const bool ends = r1 >= rows || std::binary_search(starts.begin(), starts.end(), r1);
+        if (ends) w |= 1u << 20;
+      } else {
+        li = starts.size() - 1;
+      }
+      meta[g * PPC + k] = make_uint2(w, (uint32_t)li);
+    }
+  }
+  const size_t b_chunks = sizeof(PackedChunk) * chunks.size();
+  const size_t off_meta = (b_chunks + 255) / 256 * 256;
+  const size_t off_norms = off_meta + (sizeof(uint2) * meta.size() + 255) / 256 * 256;
+  const size_t total = off_norms + sizeof(uint32_t) * 3 * (size_t)L;
+  void* mem = nullptr;
+  if (cudaMalloc(&mem, total) != cudaSuccess) { (void)cudaGetLastError(); return false; }
+  unsigned char* m = (unsigned char*)mem;
+  if (cudaMemcpy(m, chunks.data(), b_chunks, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(m + off_meta, meta.data(), sizeof(uint2) * meta.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(m + off_norms, 0, sizeof(uint32_t) * 3 * (size_t)L) != cudaSuccess) {
+    cudaFree(mem);
+    return false;
+  }
+  const size_t sm = (size_t)kPackM * kPackPitch * (3 * sizeof(float) + sizeof(double));
+  if (set_smem(packed_refine_kernel<kPackC>, sm) != cudaSuccess) { cudaFree(mem); return false; }
+  cudaLaunchConfig_t lc{};
+  lc.gridDim = dim3(kPackC);
+  lc.blockDim = dim3(kPackThreads);
+  lc.dynamicSmemBytes = sm;
+  int resident = 0;
+  if (cudaOccupancyMaxActiveClusters(&resident, packed_refine_kernel<kPackC>, &lc) != cudaSuccess) resident = 0;
+  (void)cudaGetLastError();
+  p->pk_mem = mem;
+  p->pk.chunks = (const PackedChunk*)m;
+  p->pk.meta = (const uint2*)(m + off_meta);
+  p->pk.norms = (uint32_t*)(m + off_norms);
+  p->pk.n_chunks = (int32_t)chunks.size();
+  tdma_config_t c{};
+  c.variant = TDMA_VARIANT_PACKED;
+  c.partitions = PPC;
+  c.rows_per_thread = chunks.empty() ? 1 : chunks.front().M;
+  c.lines_per_block = spans.empty() ? 0 : (int32_t)spans.front().count;  // lines of the first chunk
+  c.threads_per_block = kPackThreads;
+  c.smem_bytes = (int64_t)sm;
+  const int64_t nc = (int64_t)chunks.size();
+  c.blocks = (int32_t)(kPackC * (resident > 0 ? std::min<int64_t>(nc, resident) : nc));
+  p->cfg = c;
+  return true;
 }
 
 // ---- autotuning -----------------------------------------------------------------------
@@ -945,6 +1063,7 @@ tdma_status_t tdma_plan_create(tdma_plan_t* plan, const tdma_desc_t* desc, size_
       delete p;
       return r;
     }
+    build_packed(p);  // the chunk kernel for the forward pass where it applies
   }
   if (p->refine64) {  // residual / correction buffer after the solver's own workspace
     p->r_offset = (p->workspace + 255) / 256 * 256;
@@ -963,6 +1082,7 @@ tdma_status_t tdma_plan_destroy(tdma_plan_t p) {
   cudaError_t e = cudaSuccess;
   if (p->status) e = cudaFree(p->status);
   if (p->rt_mem && cudaFree(p->rt_mem) != cudaSuccess) e = cudaErrorUnknown;
+  if (p->pk_mem && cudaFree(p->pk_mem) != cudaSuccess) e = cudaErrorUnknown;
   delete p;
   return e == cudaSuccess ? TDMA_OK : TDMA_ERR_CUDA;
 }

@@ -1,0 +1,172 @@
+"""Ragged batches in FP32 storage + refinement on the chunk kernel (packed unit-stride lines, one
+chunk of whole lines per CTA cluster) against the oracle, including the layouts that change how
+chunks are cut: lines out of memory order, gaps between lines, the longest line a chunk holds,
+thousands of one-row lines, lines that need a second correction, and x written over d."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+import synth
+import paper_2509_03933_gb300 as tdma
+
+pytestmark = pytest.mark.gpu
+
+PACKED = 9        # TDMA_VARIANT_PACKED
+RAGGED = 3        # TDMA_VARIANT_RAGGED
+CHUNK_ROWS = 17920  # longest line the chunk kernel takes (4 CTAs x 224 partitions x 20 rows)
+
+
+def _oracle(a, b, c, d, offs, lens, lines=None, dtype=np.float64):
+    h = lambda t: t.double().cpu().numpy()
+    return O.thomas_ragged(h(a), h(b), h(c), h(d), offs, lens, lines=lines, dtype=dtype)
+
+
+def _err(x, ref, offs, lens):
+    xs = x.double().cpu().numpy()
+    got = np.concatenate([xs[offs[l]:offs[l] + lens[l]] for l in sorted(ref)])
+    want = np.concatenate([ref[l] for l in sorted(ref)])
+    return O.rel_l2(got, want)
+
+
+def _problem(lengths, seed):
+    r = synth.ragged_general(np.asarray(lengths, np.int32), seed, device="cuda", fp32_coefficients=True)
+    return r["a32"], r["b32"], r["c32"], r["d"], r["offsets"], r["lengths"]
+
+
+def _solve(a, b, c, d, offs, lens, out=None, check=True, **kw):
+    x, plan = tdma.solve_ragged(a, b, c, d, offs, lens, precision="f32r", out=out, check=check, **kw)
+    return x, plan
+
+
+@pytest.mark.parametrize("lengths", [
+    [1, 2, 3, 4, 5, 7, 16, 17, 31, 33, 100, 257, 1000, 4097, 2, 64, 65, 1, 12, 300],
+    [CHUNK_ROWS],
+    [CHUNK_ROWS, CHUNK_ROWS, 1, CHUNK_ROWS - 1],
+    [5],
+    [895, 896, 897, 1792, 1793, 3583, 8961],
+    [20] * 900,
+])
+def test_packed_matches_oracle(lengths):
+    a, b, c, d, offs, lens = _problem(lengths, 11)
+    x, plan = _solve(a, b, c, d, offs, lens)
+    assert plan.config["variant"] == PACKED
+    err = _err(x, _oracle(a, b, c, d, offs.cpu().numpy(), lens.cpu().numpy()), offs.cpu().numpy(),
+               lens.cpu().numpy())
+    assert err <= 1e-12
+
+
+def test_packed_many_one_row_lines():
+    lengths = np.ones(5000, np.int32)
+    lengths[::7] = 3
+    a, b, c, d, offs, lens = _problem(lengths, 12)
+    x, plan = _solve(a, b, c, d, offs, lens)
+    assert plan.config["variant"] == PACKED
+    o, n = offs.cpu().numpy(), lens.cpu().numpy()
+    assert _err(x, _oracle(a, b, c, d, o, n), o, n) <= 1e-12
+
+
+def test_packed_log_uniform_batch_sampled():
+    lengths = synth.ragged_lengths(3000, 16, 16384, seed=4)
+    a, b, c, d, offs, lens = _problem(lengths, 4)
+    x, plan = _solve(a, b, c, d, offs, lens, check=False)
+    assert plan.config["variant"] == PACKED
+    o, n = offs.cpu().numpy(), lens.cpu().numpy()
+    rng = np.random.default_rng(0)
+    lines = np.unique(np.concatenate([np.argsort(-lengths)[:20], rng.choice(len(lengths), 180, replace=False)]))
+    assert _err(x, _oracle(a, b, c, d, o, n, lines=lines), o, n) <= 1e-12
+    st, iters = plan.last_error()
+    assert st == 0 and iters >= 1
+
+
+def test_packed_lines_out_of_memory_order_and_gaps():
+    # the same lines described in a shuffled order, then with gaps between them in memory
+    lengths = np.array([40, 3000, 7, 17000, 1, 900, 2, 5000, 64], np.int32)
+    a, b, c, d, offs, lens = _problem(lengths, 13)
+    perm = np.random.default_rng(1).permutation(len(lengths))
+    offs_p, lens_p = offs[torch.from_numpy(perm).cuda()], lens[torch.from_numpy(perm).cuda()]
+    x, plan = _solve(a, b, c, d, offs_p, lens_p)
+    assert plan.config["variant"] == PACKED
+    o, n = offs.cpu().numpy(), lens.cpu().numpy()
+    ref = _oracle(a, b, c, d, o, n)
+    assert _err(x, ref, o, n) <= 1e-12
+    # gaps: every line shifted by 3 elements per preceding line; the gap elements stay untouched
+    gap = 3
+    o2 = o + gap * np.arange(len(o))
+    total = int(o2[-1] + n[-1])
+    sp = lambda t, fill: torch.full((total,), fill, dtype=t.dtype, device="cuda")
+    a2, b2, c2, d2 = sp(a, 0.0), sp(b, 1.0), sp(c, 0.0), sp(d, 0.0)
+    for l in range(len(o)):
+        for src, dst in ((a, a2), (b, b2), (c, c2), (d, d2)):
+            dst[o2[l]:o2[l] + n[l]] = src[o[l]:o[l] + n[l]]
+    x2 = torch.full_like(d2, 7.0)
+    offs2 = torch.from_numpy(o2).cuda()
+    x2, plan2 = _solve(a2, b2, c2, d2, offs2, lens, out=x2)
+    assert plan2.config["variant"] == PACKED
+    assert _err(x2, ref, o2, n) <= 1e-12
+    mask = torch.ones(total, dtype=torch.bool, device="cuda")
+    for l in range(len(o)):
+        mask[o2[l]:o2[l] + n[l]] = False
+    assert bool((x2[mask] == 7.0).all())  # nothing outside the lines is written
+
+
+def test_packed_in_place_and_repeated_solves():
+    lengths = synth.ragged_lengths(400, 16, 16384, seed=5)
+    a, b, c, d, offs, lens = _problem(lengths, 14)
+    o, n = offs.cpu().numpy(), lens.cpu().numpy()
+    ref = _oracle(a, b, c, d, o, n)
+    x1, plan = _solve(a, b, c, d, offs, lens)
+    x2, _ = _solve(a, b, c, d, offs, lens, plan=plan)
+    assert torch.equal(x1, x2)  # the per-line maxima are back at zero after every launch
+    dd = d.clone()
+    _solve(a, b, c, dd, offs, lens, out=dd, plan=plan)  # x over d
+    assert _err(dd, ref, o, n) <= 1e-12
+
+
+def test_packed_second_correction_for_weakly_dominant_lines():
+    # tridiag(-1, 2.001, -1) has condition number about 4000: the float solve is good to about
+    # 2e-4, one correction leaves about 6e-8 and the stop rule asks for more (the rare path that
+    # reads x back); the reference is the extended-precision oracle
+    lengths = np.array([3000, 50, 17000, 700], np.int32)
+    a, b, c, d, offs, lens = _problem(lengths, 15)
+    o, n = offs.cpu().numpy(), lens.cpu().numpy()
+    a.fill_(-1.0)
+    c.fill_(-1.0)
+    b.fill_(2.001)
+    A, B, C = a.double(), b.double(), c.double()
+    xt = torch.sin(torch.arange(a.numel(), device="cuda", dtype=torch.float64) * 0.37)
+    dn = B * xt
+    for l in range(len(o)):
+        s, e = o[l], o[l] + n[l]
+        dn[s + 1:e] += A[s + 1:e] * xt[s:e - 1]
+        dn[s:e - 1] += C[s:e - 1] * xt[s + 1:e]
+    x, plan = _solve(a, b, c, dn, offs, lens, check=False)
+    assert plan.config["variant"] == PACKED
+    st, iters = plan.last_error()
+    assert st == 0
+    assert iters >= 2
+    assert _err(x, _oracle(a, b, c, dn, o, n, dtype=np.longdouble), o, n) <= 1e-12
+
+
+def test_packed_agrees_with_group_kernel():
+    lengths = synth.ragged_lengths(500, 16, 16384, seed=6)
+    a, b, c, d, offs, lens = _problem(lengths, 16)
+    x1, p1 = _solve(a, b, c, d, offs, lens)
+    os.environ["TDMA_DISABLE_PACKED"] = "1"
+    try:
+        x2, p2 = _solve(a, b, c, d, offs, lens)
+    finally:
+        del os.environ["TDMA_DISABLE_PACKED"]
+    assert (p1.config["variant"], p2.config["variant"]) == (PACKED, RAGGED)
+    assert O.rel_l2(x1.cpu().numpy(), x2.cpu().numpy()) <= 2e-12
+
+
+def test_line_longer_than_a_chunk_uses_group_kernel():
+    lengths = np.array([CHUNK_ROWS + 1, 10], np.int32)
+    a, b, c, d, offs, lens = _problem(lengths, 17)
+    x, plan = _solve(a, b, c, d, offs, lens)
+    assert plan.config["variant"] == RAGGED
+    o, n = offs.cpu().numpy(), lens.cpu().numpy()
+    assert _err(x, _oracle(a, b, c, d, o, n), o, n) <= 1e-12
