@@ -334,17 +334,17 @@ def suite_poisson(stream, hbm_peak):
     return out
 
 
-def suite_ragged(stream, hbm_peak):
+def suite_ragged(stream, hbm_peak, n_lines=20000):
     """20000 lines, n log-uniform in [16, 16384], packed; FP32+refinement and FP64 in one
     persistent launch each; backward for loss = sum(w * x), w ~ N(0, 1)."""
     import oracle
     import synth
     import paper_2509_03933_gb300 as tdma
-    lengths = synth.ragged_lengths(20000, 16, 16384, seed=4)
+    lengths = synth.ragged_lengths(n_lines, 16, 16384, seed=4)
     r = synth.ragged_general(lengths, 4, device="cuda", fp32_coefficients=True)
     U = r["total"]
     rng = np.random.default_rng(4)
-    lines = np.unique(np.concatenate([np.argsort(-lengths)[:10], rng.choice(20000, 300, replace=False)]))
+    lines = np.unique(np.concatenate([np.argsort(-lengths)[:10], rng.choice(n_lines, min(300, n_lines), replace=False)]))
     offs, lens = r["offsets"].cpu().numpy(), r["lengths"].cpu().numpy()
     ha, hb, hc, hd = (r[k].cpu().numpy() for k in ("a", "b", "c", "d"))
     # CPU-baseline leg: the oracle on the sampled lines (timed), its output also the reference
@@ -353,7 +353,7 @@ def suite_ragged(stream, hbm_peak):
     dt = time.perf_counter() - t0
     want = np.concatenate([ref[l] for l in sorted(ref)])
     w = synth.normal(4, synth.AID["w"], torch.arange(U, device="cuda"))
-    out = {"lines": 20000, "unknowns": int(U),
+    out = {"lines": n_lines, "unknowns": int(U),
            "cpu_baseline": {"value": int(want.size) / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
                             "sample": f"{len(ref)} lines ({int(want.size)} unknowns), longest 10 + random"}}
     for prec, keys, fbytes, bbytes in (("f32r", ("a32", "b32", "c32"), BYTES_F32R, 8.0 * 3 + 4 * 3 + 8 * 2),
@@ -426,11 +426,17 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-suite", action="store_true", help="skip the other workloads")
+    ap.add_argument("--only-ragged", type=int, default=0, metavar="LINES",
+                    help="run only the ragged workload with LINES lines (profiling runs) and print it")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_ragged > 0:
+        hbm_peak, _ = peaks()
+        print(json.dumps({"ragged": suite_ragged(torch.cuda.current_stream(), hbm_peak, args.only_ragged)}), flush=True)
+        return 0
 
     ws, rank, local = dist_env()
     if ws > 1:

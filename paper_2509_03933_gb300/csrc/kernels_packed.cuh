@@ -6,9 +6,10 @@
 // solve of that long system is therefore exactly the set of per-line solves: when the merge of
 // two blocks meets a line boundary, the terms that couple them vanish and the merge only copies.
 // At plan time the lines, in memory order, are cut into chunks of whole, contiguous lines of at
-// most kPackChunk rows; chunk g is solved by one cluster of kPackC CTAs with 256 partitions each
-// (M = ceil(rows / 1024) rows per partition, the last partitions partial or empty), so a chunk
-// of any mix of lengths keeps all threads busy. The paper batches lines of one direction into
+// most kPackChunk rows; chunk g is solved by one cluster of kPackC CTAs with 224 partitions each
+// of M rows (M even, the smallest with 896 M >= rows), the rows past the chunk's end being
+// identity rows (a = c = d = 0, b = 1: decoupled unknowns equal to 0), so that every partition is
+// full and the row loops are straight-line code compiled for each M. The paper batches lines of one direction into
 // composite systems (Section 4.2.1); here the batch is a chunk and the composite system is the
 // chunk's rows.
 //
@@ -28,6 +29,8 @@
 #include "tma.cuh"
 #include "kernels_refine.cuh"
 #include "merge_tree.cuh"
+#include "bits.cuh"
+#include "kernels_refine_tree.cuh"
 
 namespace tdma {
 
@@ -406,6 +409,64 @@ __device__ __noinline__ void packed_later_pass(const PackedTables& PT, const flo
   }
 }
 
+// Passes 0 and 1 of one compute thread for chunks of MM rows per partition (every partition
+// full; a and c already zero where lines start and end). Pass 0 solves with the float part of d
+// (split in place into float pairs), pass 1 solves for the extra-precise residual with the same
+// factors, and x = x_0 + dx goes, in FP64, to rx (the a and b space: named barrier 2 of pass 1
+// completes only after every compute warp has arrived on barrier 1, after its last read of a and
+// b), with the per-line maxima of |dx| and |x_0| to the line table.
+template <int MM>
+TDMA_DEV void packed_passes(const float* ra, const float* rb, const float* rc, const double* rd, float2* rd2,
+                            double* rx, float* wsl0, const float4* dsl0, float* wsl1, const float4* dsl1, int w,
+                            int lane, bool edge_s, bool edge_e, uint32_t mask, int line, uint32_t* norms) {
+  Sweep<MM> S;
+  float x0[MM];
+  float u0, v0;
+  {
+#pragma unroll
+    for (int t = 0; t < MM; ++t) {
+      const ff dd = split_f64_fast(rd[t * kPackPitch]);
+      rd2[t * kPackPitch] = make_float2(dd.h, dd.l);  // same thread, same 8 bytes
+      S.row(t, ra[t * kPackPitch], rb[t * kPackPitch], rc[t * kPackPitch], dd.h);
+    }
+    const Blk blk = S.block();
+    float u, v;
+    const WarpEdge e = packed_compute_b(blk, wsl0, dsl0, w, lane, u, v);
+    // unknowns at warp and CTA edges exactly as the neighbouring warp computes them
+    const float xs = edge_s ? e.xs : Sweep<MM>::first(blk, u, v);
+    const float xe = edge_e ? e.xe : Sweep<MM>::last(blk, u, v);
+    S.solve(xs, xe, x0);
+    const float from_prev = __shfl_up_sync(~0u, x0[MM - 1], 1), from_next = __shfl_down_sync(~0u, x0[0], 1);
+    u0 = lane == 0 ? e.u : from_prev;
+    v0 = lane == 31 ? e.v : from_next;
+  }
+  {
+#pragma unroll
+    for (int t = 0; t < MM; ++t) {
+      const float a = ra[t * kPackPitch], b = rb[t * kPackPitch], c = rc[t * kPackPitch];
+      const float2 dd = rd2[t * kPackPitch];
+      const float xm = t == 0 ? u0 : x0[t > 0 ? t - 1 : 0];
+      const float xp = t == MM - 1 ? v0 : x0[t < MM - 1 ? t + 1 : 0];
+      S.row_rhs(t, a, b, residual_f(a, b, c, dd.x, dd.y, xm, x0[t], xp));
+    }
+    const Blk blk = S.block();
+    float u, v;
+    const WarpEdge e = packed_compute_b(blk, wsl1, dsl1, w, lane, u, v);
+    const float xs = edge_s ? e.xs : Sweep<MM>::first(blk, u, v);
+    const float xe = edge_e ? e.xe : Sweep<MM>::last(blk, u, v);
+    LineMax nm;
+    nm.init(mask, MM, line);
+    S.solve_visit(xs, xe, [&](int t, float dxv) {
+      rx[t * kPackPitch] = f2d_fast(x0[t]) + f2d_fast(dxv);  // exact widenings, one FP64 add
+      nm.add(t, mask, dxv, x0[t], norms);
+    });
+    nm.finish(mask, MM, lane, norms);
+  }
+}
+
+// compiled rows per partition (the plan rounds M up to one of these)
+#define TDMA_PACKED_M(X) X(2) X(4) X(6) X(8) X(10) X(12) X(14) X(16) X(18) X(20)
+
 // Persistent: the grid holds the clusters that fit on the GPU at once; cluster q takes chunks
 // q, q + Q, q + 2Q, ... (Q clusters, chunks sorted longest first at plan time). Warps 0..6 of a
 // CTA compute (one partition per thread), warp 7 coordinates Stage B.
@@ -464,14 +525,21 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
 
     // ---------------- segment into shared memory (transposed), next chunk into L2
     if (!coord) {
-      for (int i = tid; i < segn; i += kPackT) {
+      for (int i = tid; i < kPackT * M; i += kPackT) {
         int k, t;
         seg_row(i, M, inv, k, t);
         const int pos = t * kPackPitch + k;
-        cp_async4(ta + pos, fa + gbase + i);
-        cp_async4(tb + pos, fb + gbase + i);
-        cp_async4(tc + pos, fc + gbase + i);
-        cp_async8(td + pos, gd + gbase + i);
+        if (i < segn) {
+          cp_async4(ta + pos, fa + gbase + i);
+          cp_async4(tb + pos, fb + gbase + i);
+          cp_async4(tc + pos, fc + gbase + i);
+          cp_async8(td + pos, gd + gbase + i);
+        } else {  // identity row past the chunk's end
+          ta[pos] = 0.f;
+          tb[pos] = 1.f;
+          tc[pos] = 0.f;
+          td[pos] = 0.0;
+        }
       }
     } else if (lane == 0 && g + n_clusters < PT.n_chunks) {
       const PackedChunk nx = PT.chunks[g + n_clusters];
@@ -491,6 +559,9 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
       cluster_wait();  // every CTA of the cluster has started: remote stores may begin
       started = true;
     }
+    // a = 0 where a line starts, c = 0 where one ends (each thread its own rows)
+    for (uint32_t bm = mask; bm; bm &= bm - 1u) ta[(__ffs(bm) - 1) * kPackPitch + tid] = 0.f;
+    for (uint32_t bm = endmask; bm; bm &= bm - 1u) tc[(__ffs(bm) - 1) * kPackPitch + tid] = 0.f;
     const float* ra = ta + tid;
     const float* rb = tb + tid;
     const float* rc = tc + tid;
@@ -505,65 +576,20 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
       ++xph[1];
       __syncthreads();  // x staged by the compute warps
     } else {
-      SweepR<kPackM> S;
-      float x0[kPackM];
-      float u0, v0;
-      // ---------------- pass 0: float solve with the float part of d
-      {
-#pragma unroll
-        for (int t = 0; t < kPackM; ++t) {
-          if (t < m) {
-            float a = ra[t * kPackPitch], b = rb[t * kPackPitch], c = rc[t * kPackPitch];
-            if ((mask >> t) & 1u) a = 0.f;
-            if ((endmask >> t) & 1u) c = 0.f;
-            const ff dd = split_f64(rd[t * kPackPitch]);
-            rd2[t * kPackPitch] = make_float2(dd.h, dd.l);  // same thread, same 8 bytes
-            S.row(t, m, a, b, c, dd.h);
-          }
+      switch (M) {
+#define TDMA_PASSES(MM)                                                                             \
+  case MM:                                                                                           \
+    packed_passes<MM>(ra, rb, rc, rd, rd2, tx + tid, wsl[0], dsl[0], wsl[1], dsl[1], w, lane, edge_s, edge_e, \
+                      mask, line, PT.norms);                                                         \
+    break;
+        TDMA_PACKED_M(TDMA_PASSES)
+#undef TDMA_PASSES
+        default: {  // not a compiled M (the plan never makes one): report; the barriers still run
+          if (tid == 0) report_error(A.st, 2);
+          float du, dv;
+          packed_compute_b(Blk{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, wsl[0], dsl[0], w, lane, du, dv);
+          packed_compute_b(Blk{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, wsl[1], dsl[1], w, lane, du, dv);
         }
-        const Blk blk = S.block(m);
-        float u, v;
-        const WarpEdge e = packed_compute_b(blk, wsl[0], dsl[0], w, lane, u, v);
-        // unknowns at warp and CTA edges exactly as the neighbouring warp computes them
-        const float xs = edge_s ? e.xs : SweepR<kPackM>::first(blk, u, v);
-        const float xe = edge_e ? e.xe : SweepR<kPackM>::last(blk, u, v);
-        S.solve(m, m == 1 && edge_e ? xe : xs, xe, x0);
-        float xl = x0[0];
-#pragma unroll
-        for (int t = 1; t < kPackM; ++t) if (t == m - 1) xl = x0[t];
-        const float from_prev = __shfl_up_sync(~0u, xl, 1), from_next = __shfl_down_sync(~0u, x0[0], 1);
-        u0 = lane == 0 ? e.u : from_prev;
-        v0 = lane == 31 ? e.v : from_next;
-      }
-      // ---------------- pass 1: correction for r = d - A x_0 with the same factors
-      {
-#pragma unroll
-        for (int t = 0; t < kPackM; ++t) {
-          if (t < m) {
-            float a = ra[t * kPackPitch], b = rb[t * kPackPitch], c = rc[t * kPackPitch];
-            if ((mask >> t) & 1u) a = 0.f;
-            if ((endmask >> t) & 1u) c = 0.f;
-            const float2 dd = rd2[t * kPackPitch];
-            const float xm = t == 0 ? u0 : x0[t > 0 ? t - 1 : 0];
-            const float xp = t + 1 < m ? x0[t < kPackM - 1 ? t + 1 : 0] : v0;
-            S.row_rhs(t, m, a, b, residual_f(a, b, c, dd.x, dd.y, xm, x0[t], xp));
-          }
-        }
-        const Blk blk = S.block(m);
-        float u, v;
-        const WarpEdge e = packed_compute_b(blk, wsl[1], dsl[1], w, lane, u, v);
-        const float xs = edge_s ? e.xs : SweepR<kPackM>::first(blk, u, v);
-        const float xe = edge_e ? e.xe : SweepR<kPackM>::last(blk, u, v);
-        // Named barrier 2 of pass 1 completed only after every compute warp arrived on barrier 1,
-        // after its last read of the a and b space: x = x_0 + dx (FP64) goes there.
-        LineMax nm;
-        nm.init(mask, m, line);
-        double* rx = tx + tid;
-        S.solve_visit(m, m == 1 && edge_e ? xe : xs, xe, [&](int t, float dxv) {
-          rx[t * kPackPitch] = f2d(x0[t]) + f2d(dxv);  // exact widenings, one FP64 add
-          nm.add(t, mask, dxv, x0[t], PT.norms);
-        });
-        nm.finish(mask, m, lane, PT.norms);
       }
       __syncthreads();
     }

@@ -33,7 +33,9 @@
 #include "layout.cuh"
 #include "tma.cuh"
 #include "kernels_refine.cuh"
+#include "kernels_refine_tma.cuh"  // kTmaWaitPolls
 #include "merge_tree.cuh"
+#include "bits.cuh"
 
 namespace tdma {
 
@@ -150,6 +152,24 @@ struct Sweep {
       Q = -Q * gamma;
     }
   }
+  // Row t of a further solve with the same matrix: alpha and gamma of the interior rows (and of
+  // the last row, in alpha / gamma) and G stay from the first solve; delta, F and Q are redone.
+  TDMA_DEV void row_rhs(int t, float a, float b, float rhs) {
+    if (t == 0) {
+      h0 = rhs;
+      delta = 0.f;
+      F = 0.f;
+      Q = 1.f;
+      return;
+    }
+    const float r = rcp(fmaf(-a, t >= 2 ? ga[t >= 2 ? t - 1 : 1] : 0.f, b));  // pivot of row t
+    delta = fmaf(r, rhs, -(a * r) * delta);
+    if (t <= M - 2) {
+      de[t] = delta;
+      F = fmaf(Q, delta, F);
+      Q = -Q * ga[t];
+    }
+  }
   // row 0 becomes x_s + S u + U x_e = H with x_1 = F - G x_s + Q x_e substituted
   TDMA_DEV Blk block() const {
     const float rho = rcp(fmaf(-c0, G, b0));
@@ -158,6 +178,18 @@ struct Sweep {
   // the partition's first and last unknowns for its outside neighbours (u, v)
   TDMA_DEV static float first(const Blk& b, float u, float v) { return fmaf(b.q1, u, fmaf(b.r1, v, b.p1)); }
   TDMA_DEV static float last(const Blk& b, float u, float v) { return fmaf(b.q2, u, fmaf(b.r2, v, b.p2)); }
+  // Stage C handing each row's value to f(t, x_t), from row M-1 down to row 0
+  template <class Fn>
+  TDMA_DEV void solve_visit(float xs, float xe, Fn&& f) const {
+    f(M - 1, xe);
+    float xn = xe;
+#pragma unroll
+    for (int t = M - 2; t >= 1; --t) {
+      xn = fmaf(-ga[t], xn, fmaf(-al[t], xs, de[t]));
+      f(t, xn);
+    }
+    f(0, xs);
+  }
   // Stage C from the partition's first and last unknowns
   TDMA_DEV void solve(float xs, float xe, float (&x)[M]) const {
     x[0] = xs;
@@ -284,8 +316,8 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
     float x0[M];
     float u0, v0;
     unsigned nx;
+    Sweep<M> S;  // its factors serve pass 1 as well (same matrix)
     {
-      Sweep<M> S;
 #pragma unroll
       for (int t = 0; t < M; ++t) {
         if (t == H) {  // the second half of the rows (the first half is being swept meanwhile)
@@ -298,7 +330,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
         float a = ra[t * 256], b = rb[t * 256], c = rc[t * 256];
         if (t == 0 && first_part) a = 0.f;
         if (t == M - 1 && last_part) c = 0.f;
-        const ff dd = split_f64(rd[t * 128]);
+        const ff dd = split_f64_fast(rd[t * 128]);
         rd2[t * 128] = make_float2(dd.h, dd.l);  // same thread, same 8 bytes: read before write
         S.row(t, a, b, c, dd.h);
       }
@@ -331,7 +363,6 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
       // ---------------- pass 1: correction for r = d - A x_0, x = x_0 + dx
       unsigned prev, gdx, gxm;
       {
-        Sweep<M> S;
 #pragma unroll
         for (int t = 0; t < M; ++t) {
           float a = ra[t * 256], b = rb[t * 256], c = rc[t * 256];
@@ -340,7 +371,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
           const float2 dd = rd2[t * 128];
           const float xm = t == 0 ? u0 : x0[t > 0 ? t - 1 : 0];
           const float xp = t == M - 1 ? v0 : x0[t < M - 1 ? t + 1 : 0];
-          S.row(t, a, b, c, residual_f(a, b, c, dd.x, dd.y, xm, x0[t], xp));
+          S.row_rhs(t, a, b, residual_f(a, b, c, dd.x, dd.y, xm, x0[t], xp));
         }
         const Blk blk = S.block();
         float u, v, xs_c, xe_c;
@@ -356,7 +387,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
         // Every thread of the CTA has sent its block (the exchange wait above needed all of
         // them), so all reads of the a and b tiles in this pass are done: x goes there.
 #pragma unroll
-        for (int t = 0; t < M; ++t) rx[t * 128] = f2d(x0[t]) + f2d(dx[t]);  // exact widenings, one FP64 add
+        for (int t = 0; t < M; ++t) rx[t * 128] = f2d_fast(x0[t]) + f2d_fast(dx[t]);  // exact widenings, one FP64 add
         fence_proxy_async_smem();
         __syncthreads();
         if (tid == 0) {  // out-of-range lines of a partial group are not written
@@ -391,7 +422,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
         tph0 ^= 1u;
         cluster_arrive();  // x of the previous pass, written by every CTA, visible to all
         cluster_wait();
-        Sweep<M> S;
+        Sweep<M> S;  // a fresh solve (the first pass's factors are not kept past pass 1)
         ff xm{0.f, 0.f}, xc{0.f, 0.f}, xe{0.f, 0.f};
         if (active) {
           if (!first_part) xm = split_f64(px[-es]);
