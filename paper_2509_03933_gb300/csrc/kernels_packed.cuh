@@ -42,13 +42,17 @@ constexpr int kPackM = 20;                   // rows per partition at most
 constexpr int kPackPitch = kPackT + 1;       // shared-memory pitch of one row position
 constexpr int kPackChunk = kPackC * kPackT * kPackM;  // rows per chunk at most (17920)
 constexpr uint32_t kPackWaitPolls = 1u << 16;
+// Per-line words of the norm table (float bits of non-negative values): [0] max |dx| and [1] max
+// |x_0| of the first correction (zero at launch, written once); [2] max |dx|, [3] max |x| of a
+// further correction and [4] the previous max |dx| (reset by the line's owner after each use).
+constexpr int kPackNormWords = 5;
 
 struct PackedChunk {
   int64_t base;   // element index of the chunk's first row
   int32_t rows;   // rows in the chunk (1..kPackChunk)
   int32_t M;      // rows per partition: partition k holds rows [k M, min((k + 1) M, rows))
   int32_t line0;  // position, in memory order, of the chunk's first line (its norm slot)
-  int32_t pad;
+  int32_t nlines; // lines in the chunk
 };
 
 // Partition metadata (one pair of words per partition of every chunk):
@@ -58,7 +62,7 @@ struct PackedChunk {
 struct PackedTables {
   const PackedChunk* chunks;
   const uint2* meta;      // kPackC * kPackT pairs per chunk
-  uint32_t* norms;        // per line in memory order: max |dx|, max |x| (float bits), previous max |dx|
+  uint32_t* norms;        // kPackNormWords per line in memory order (see packed_first_verdict)
   int32_t n_chunks;
 };
 
@@ -117,27 +121,6 @@ struct SweepR {
       Q = -Q * gamma;
     }
   }
-  // Row t of a further solve with the same matrix: the factors alpha, gamma of the interior rows
-  // (and of the last row, in alpha / gamma) are those of the first solve and stay; only delta and
-  // F are recomputed, with Q regenerated from the kept gammas.
-  TDMA_DEV void row_rhs(int t, int m, float a, float b, float rhs) {
-    if (t == 0) {
-      h0 = rhs;
-      delta = 0.f;
-      F = 0.f;
-      Q = 1.f;
-      return;
-    }
-    if (t >= m) return;
-    const float gp = t >= 2 ? ga[t >= 2 ? t - 1 : 1] : 0.f;  // gamma of row t - 1 (0 before row 1)
-    const float r = rcp(fmaf(-a, gp, b));
-    delta = fmaf(r, rhs, -(a * r) * delta);
-    if (t <= m - 2) {
-      de[t] = delta;
-      F = fmaf(Q, delta, F);
-      Q = -Q * ga[t];
-    }
-  }
   // Block form of the partition (all zero for an empty one: a decoupled unknown x = 0, which
   // merges with its neighbours without changing them).
   TDMA_DEV Blk block(int m) const {
@@ -165,20 +148,6 @@ struct SweepR {
         else v = fmaf(-ga[t > 0 ? t : 1], xn, fmaf(-al[t > 0 ? t : 1], xs, de[t > 0 ? t : 1]));
         xn = v;
         f(t, v);
-      }
-    }
-  }
-  // Stage C from the partition's first and last unknowns (x[0] = xs; x[m-1] = xe for m >= 2)
-  TDMA_DEV void solve(int m, float xs, float xe, float (&x)[MM]) const {
-    x[0] = xs;
-    float xn = xe;
-#pragma unroll
-    for (int t = MM - 1; t >= 1; --t) {
-      if (t == m - 1) {
-        x[t] = xe;
-      } else if (t < m - 1) {
-        xn = fmaf(-ga[t], xn, fmaf(-al[t], xs, de[t]));
-        x[t] = xn;
       }
     }
   }
@@ -295,17 +264,19 @@ TDMA_DEV void packed_coord_b(const float* wsl, float4* dsl, float* csl, uint64_t
 // starts its line; a warp whose rows all belong to one line reduces first and makes one pair.
 struct LineMax {
   unsigned pdx, px;
-  int cur;  // line of the rows being accumulated
-  TDMA_DEV void init(uint32_t mask, int m, int line) {
+  int cur;   // line of the rows being accumulated
+  int slot;  // first of the two words written (0: first correction, 2: further ones)
+  TDMA_DEV void init(uint32_t mask, int m, int line, int slot_) {
     pdx = px = 0u;
+    slot = slot_;
     cur = line + __popc(mask & ~1u & ((1u << m) - 1u));
   }
   TDMA_DEV void add(int t, uint32_t mask, float dxv, float xv, uint32_t* norms) {
     pdx = max(pdx, abs_bits(dxv));
     px = max(px, abs_bits(xv));
     if (t > 0 && ((mask >> t) & 1u)) {  // row t starts line `cur`: its piece is complete
-      atomicMax(&norms[3 * cur], pdx);
-      atomicMax(&norms[3 * cur + 1], px);
+      atomicMax(&norms[kPackNormWords * cur + slot], pdx);
+      atomicMax(&norms[kPackNormWords * cur + slot + 1], px);
       pdx = px = 0u;
       --cur;
     }
@@ -321,21 +292,51 @@ struct LineMax {
       }
       const int l0 = __shfl_sync(~0u, cur, 0);
       if (lane == 0) {
-        atomicMax(&norms[3 * l0], pdx);
-        atomicMax(&norms[3 * l0 + 1], px);
+        atomicMax(&norms[kPackNormWords * l0 + slot], pdx);
+        atomicMax(&norms[kPackNormWords * l0 + slot + 1], px);
       }
     } else if (m > 0) {
-      atomicMax(&norms[3 * cur], pdx);
-      atomicMax(&norms[3 * cur + 1], px);
+      atomicMax(&norms[kPackNormWords * cur + slot], pdx);
+      atomicMax(&norms[kPackNormWords * cur + slot + 1], px);
     }
   }
 };
 
-// Stop rule for the lines whose first row lies in this partition (after the cluster barrier
-// that completes the atomics): estimated error rho |dx| <= tol |x| with rho = |dx| / |dx_prev|
-// (|dx_prev| = |x_0| after the first correction). Resets the line's maxima for the next pass.
-// Returns true when one of these lines needs another correction.
-TDMA_DEV bool packed_lines_verdict(uint32_t mask, int m, int line, uint32_t* norms, bool first_pass, float tol,
+// Stop rule of the refinement, as in the other refinement kernels: a line is done when its
+// estimated error rho |dx| <= tol |x| with rho = |dx| / |dx_prev| (|dx_prev| = |x_0| after the first
+// correction). A non-finite norm ends the line with status 5.
+TDMA_DEV bool line_rule(uint32_t gdx, uint32_t gx, uint32_t prev, float tol, bool& bad) {
+  bad = !(bits_finite(gdx) && bits_finite(gx));
+  if (bad) return true;
+  const float dxn = __uint_as_float(gdx), xn = __uint_as_float(gx), pv = __uint_as_float(prev);
+  const float ratio = pv > 0.f ? dxn / pv : 0.f;
+  return ratio * dxn <= tol * xn || dxn == 0.f;
+}
+
+// After the first correction: every CTA of the cluster reads the norms of all lines of the chunk
+// (complete after the cluster barrier, written by no one afterwards) and so reaches the same
+// verdict without another exchange. Returns true when some line needs a further correction; with
+// `last_pass` such a line reports status 7 instead. Statuses are reported by CTA rank 0.
+TDMA_DEV bool packed_first_verdict(const PackedChunk& ch, const uint32_t* norms, float tol, bool last_pass,
+                                   bool reporter, DevStatus* st) {
+  bool more = false;
+  for (int l = threadIdx.x; l < ch.nlines; l += blockDim.x) {
+    const uint32_t* nl = norms + (int64_t)kPackNormWords * (ch.line0 + l);
+    const uint32_t gdx = ld_relaxed_u32(nl), gx = ld_relaxed_u32(nl + 1);
+    bool bad;
+    const bool done = line_rule(gdx, gx, gx, tol, bad);
+    if (bad && reporter) report_error(st, 5);
+    if (!done) {
+      if (last_pass) { if (reporter) report_error(st, 7); }
+      else more = true;
+    }
+  }
+  return more;
+}
+
+// After a further correction: the thread holding each line's first row applies the rule to words
+// 2 and 3 (previous |dx| in word 4, or word 0 after the first correction) and resets them.
+TDMA_DEV bool packed_later_verdict(uint32_t mask, int m, int line, uint32_t* norms, bool first_later, float tol,
                                    bool last_pass, DevStatus* st) {
   bool more = false;
   uint32_t own = m > 0 ? (mask & ((m >= 32 ? 0u : (1u << m)) - 1u)) : 0u;
@@ -343,19 +344,15 @@ TDMA_DEV bool packed_lines_verdict(uint32_t mask, int m, int line, uint32_t* nor
     const int t = __ffs(own) - 1;
     own &= own - 1u;
     const int L = line + __popc(mask & ~1u & ((2u << t) - 1u));
-    uint32_t* nl = norms + 3 * L;
-    const uint32_t gdx = ld_relaxed_u32(nl), gx = ld_relaxed_u32(nl + 1);
-    const uint32_t prev = first_pass ? gx : ld_relaxed_u32(nl + 2);
-    nl[0] = 0u;
-    nl[1] = 0u;
-    nl[2] = gdx;
-    if (!(bits_finite(gdx) && bits_finite(gx))) {
-      report_error(st, 5);
-      continue;
-    }
-    const float dxn = __uint_as_float(gdx), xn = __uint_as_float(gx), pv = __uint_as_float(prev);
-    const float ratio = pv > 0.f ? dxn / pv : 0.f;
-    const bool done = ratio * dxn <= tol * xn || dxn == 0.f;
+    uint32_t* nl = norms + (int64_t)kPackNormWords * L;
+    const uint32_t gdx = ld_relaxed_u32(nl + 2), gx = ld_relaxed_u32(nl + 3);
+    const uint32_t prev = ld_relaxed_u32(nl + (first_later ? 0 : 4));
+    nl[2] = 0u;
+    nl[3] = 0u;
+    nl[4] = gdx;
+    bool bad;
+    const bool done = line_rule(gdx, gx, prev, tol, bad);
+    if (bad) report_error(st, 5);
     if (!done) {
       if (last_pass) report_error(st, 7);
       else more = true;
@@ -364,60 +361,69 @@ TDMA_DEV bool packed_lines_verdict(uint32_t mask, int m, int line, uint32_t* nor
   return more;
 }
 
-// One further correction of a partition (rare): x of this partition and its neighbours read back
-// from global memory, residual in float pairs, Stage A/B/C, x += dx written back. Kept out of
-// line so that its registers do not weigh on the two main passes.
-__device__ __noinline__ void packed_later_pass(const PackedTables& PT, const float* ra, const float* rb,
-                                               const float* rc, const float2* rd2, float* wslq, const float4* dslq,
-                                               double* gx, int64_t prow, int w, int lane, int kp, int m,
-                                               uint32_t mask, uint32_t endmask, int line, int row0, int rows) {
-  {
-    SweepR<kPackM> S;
-    ff xm{0.f, 0.f}, xc{0.f, 0.f};
-    if (m > 0) {
-      if (kp > 0) xm = split_f64(__ldcg(gx + prow - 1));
-      xc = split_f64(__ldcg(gx + prow));
-    }
-#pragma unroll
-    for (int t = 0; t < kPackM; ++t) {
-      if (t < m) {
-        float a = ra[t * kPackPitch], b = rb[t * kPackPitch], c = rc[t * kPackPitch];
-        if ((mask >> t) & 1u) a = 0.f;
-        if ((endmask >> t) & 1u) c = 0.f;
-        const float2 dd = rd2[t * kPackPitch];
-        const bool has_next = t + 1 < m || row0 + t + 1 < rows;
-        const ff xn = has_next ? split_f64(__ldcg(gx + prow + t + 1)) : ff{0.f, 0.f};
-        S.row(t, m, a, b, c, residual_ff(a, b, c, ff{dd.x, dd.y}, xm, xc, xn));
-        xm = xc;
-        xc = xn;
-      }
-    }
-    const Blk blk = S.block(m);
-    float u, v;
-    packed_compute_b(blk, wslq, dslq, w, lane, u, v);
-    // Every read of x above happened before its warp arrived on named barrier 1; another
-    // warp writes only after barrier 2, and another CTA only after receiving this CTA's
-    // block, which left after barrier 1.
-    LineMax nm;
-    nm.init(mask, m, line);
-    S.solve_visit(m, SweepR<kPackM>::first(blk, u, v), SweepR<kPackM>::last(blk, u, v), [&](int t, float dxv) {
-      const double xv = __ldcg(gx + prow + t) + f2d(dxv);
-      gx[prow + t] = xv;
-      nm.add(t, mask, dxv, __double2float_rn(xv), PT.norms);
-    });
-    nm.finish(mask, m, lane, PT.norms);
+// One further correction of a partition (rare): the coefficients read from global memory (with
+// TR those of the transposed rows), d from the shared-memory float pairs when they are still there
+// (sd != nullptr) or from global memory, x of the partition and its neighbours read back from
+// global memory; residual in float pairs, Stage A/B/C, x += dx written back. Kept out of line so
+// that its registers do not weigh on the two main passes.
+template <bool TR>
+__device__ __noinline__ void packed_later_pass(const PackedTables& PT, const float* fa, const float* fb,
+                                               const float* fc, const double* gd, const float2* sd, float* wslq,
+                                               const float4* dslq, double* gx, int64_t prow, int w, int lane,
+                                               int kp, int m, uint32_t mask, uint32_t endmask, int line, int row0,
+                                               int rows) {
+  SweepR<kPackM> S;
+  ff xm{0.f, 0.f}, xc{0.f, 0.f};
+  if (m > 0) {
+    if (kp > 0) xm = split_f64(__ldcg(gx + prow - 1));
+    xc = split_f64(__ldcg(gx + prow));
   }
+#pragma unroll
+  for (int t = 0; t < kPackM; ++t) {
+    if (t < m) {
+      const int64_t gi = prow + t;
+      const float a = ((mask >> t) & 1u) ? 0.f : (TR ? fc[gi - 1] : fa[gi]);
+      const float c = ((endmask >> t) & 1u) ? 0.f : (TR ? fa[gi + 1] : fc[gi]);
+      const float b = fb[gi];
+      ff dd;
+      if (sd) {
+        const float2 v = sd[t * kPackPitch];
+        dd = ff{v.x, v.y};
+      } else {
+        dd = split_f64(gd[gi]);
+      }
+      const bool has_next = t + 1 < m || row0 + t + 1 < rows;
+      const ff xn = has_next ? split_f64(__ldcg(gx + gi + 1)) : ff{0.f, 0.f};
+      S.row(t, m, a, b, c, residual_ff(a, b, c, dd, xm, xc, xn));
+      xm = xc;
+      xc = xn;
+    }
+  }
+  const Blk blk = S.block(m);
+  float u, v;
+  packed_compute_b(blk, wslq, dslq, w, lane, u, v);
+  // Every read of x above happened before its warp arrived on named barrier 1; another warp
+  // writes only after barrier 2, and another CTA only after receiving this CTA's block, which
+  // left after barrier 1.
+  LineMax nm;
+  nm.init(mask, m, line, 2);
+  S.solve_visit(m, SweepR<kPackM>::first(blk, u, v), SweepR<kPackM>::last(blk, u, v), [&](int t, float dxv) {
+    const double xv = __ldcg(gx + prow + t) + f2d(dxv);
+    gx[prow + t] = xv;
+    nm.add(t, mask, dxv, __double2float_rn(xv), PT.norms);
+  });
+  nm.finish(mask, m, lane, PT.norms);
 }
 
 // Passes 0 and 1 of one compute thread for chunks of MM rows per partition (every partition
 // full; a and c already zero where lines start and end). Pass 0 solves with the float part of d
 // (split in place into float pairs), pass 1 solves for the extra-precise residual with the same
-// factors, and x = x_0 + dx goes, in FP64, to rx (the a and b space: named barrier 2 of pass 1
+// factors, and the pair (x_0, dx) goes to rx (the a and b space: named barrier 2 of pass 1
 // completes only after every compute warp has arrived on barrier 1, after its last read of a and
-// b), with the per-line maxima of |dx| and |x_0| to the line table.
+// b), with the per-line maxima of |dx| and |x_0| to the line table. The copy-out forms x in FP64.
 template <int MM>
 TDMA_DEV void packed_passes(const float* ra, const float* rb, const float* rc, const double* rd, float2* rd2,
-                            double* rx, float* wsl0, const float4* dsl0, float* wsl1, const float4* dsl1, int w,
+                            float2* rx, float* wsl0, const float4* dsl0, float* wsl1, const float4* dsl1, int w,
                             int lane, bool edge_s, bool edge_e, uint32_t mask, int line, uint32_t* norms) {
   Sweep<MM> S;
   float x0[MM];
@@ -455,9 +461,9 @@ TDMA_DEV void packed_passes(const float* ra, const float* rb, const float* rc, c
     const float xs = edge_s ? e.xs : Sweep<MM>::first(blk, u, v);
     const float xe = edge_e ? e.xe : Sweep<MM>::last(blk, u, v);
     LineMax nm;
-    nm.init(mask, MM, line);
+    nm.init(mask, MM, line, 0);
     S.solve_visit(xs, xe, [&](int t, float dxv) {
-      rx[t * kPackPitch] = f2d_fast(x0[t]) + f2d_fast(dxv);  // exact widenings, one FP64 add
+      rx[t * kPackPitch] = make_float2(x0[t], dxv);
       nm.add(t, mask, dxv, x0[t], norms);
     });
     nm.finish(mask, MM, lane, norms);
@@ -470,7 +476,79 @@ TDMA_DEV void packed_passes(const float* ra, const float* rb, const float* rc, c
 // Persistent: the grid holds the clusters that fit on the GPU at once; cluster q takes chunks
 // q, q + Q, q + 2Q, ... (Q clusters, chunks sorted longest first at plan time). Warps 0..6 of a
 // CTA compute (one partition per thread), warp 7 coordinates Stage B.
-template <int C>
+// Coefficients of row i of the chunk, copied into shared memory: (a_i, c_i), or with TR the
+// transposed system's (c_{i-1}, a_{i+1}) (the adjoint solve of the backward pass). Entries that
+// would come from outside the chunk lie on a line boundary, where they are zero.
+template <bool TR>
+TDMA_DEV void load_ac(float* sa, float* sc, const float* fa, const float* fc, int64_t gi, int ci, int rows) {
+  if (!TR) {
+    cp_async4(sa, fa + gi);
+    cp_async4(sc, fc + gi);
+  } else {
+    if (ci > 0) cp_async4(sa, fc + gi - 1); else *sa = 0.f;
+    if (ci + 1 < rows) cp_async4(sc, fa + gi + 1); else *sc = 0.f;
+  }
+}
+
+// Copies of chunk g's segment for this CTA into shared memory, transposed; rows past the chunk's
+// end become identity rows. Compute threads only.
+template <int C, bool TR>
+TDMA_DEV void packed_issue_loads(const PackedTables& PT, const Args& A, int g, int rank, int tid, float* ta, float* tb,
+                                 float* tc, double* td) {
+  const PackedChunk ch = PT.chunks[g];
+  const int M = ch.M;
+  const uint32_t inv = ((1u << 20) + (uint32_t)M - 1u) / (uint32_t)M;
+  const int seg0 = rank * kPackT * M;
+  const int segn = max(0, min(ch.rows - seg0, kPackT * M));
+  const int64_t gbase = ch.base + seg0;
+  const float* fa = (const float*)A.a;
+  const float* fb = (const float*)A.b;
+  const float* fc = (const float*)A.c;
+  const double* gd = (const double*)A.d;
+  // row i = tid + kPackT j of the segment is row t of partition k; both advance by fixed steps
+  int k, t;
+  seg_row(tid, M, inv, k, t);
+  const int dk = kPackT / M, dt = kPackT - dk * M;
+  for (int i = tid; i < kPackT * M; i += kPackT) {
+    const int pos = t * kPackPitch + k;
+    if (i < segn) {
+      load_ac<TR>(ta + pos, tc + pos, fa, fc, gbase + i, seg0 + i, ch.rows);
+      cp_async4(tb + pos, fb + gbase + i);
+      cp_async8(td + pos, gd + gbase + i);
+    } else {  // identity row past the chunk's end
+      ta[pos] = 0.f;
+      tb[pos] = 1.f;
+      tc[pos] = 0.f;
+      td[pos] = 0.0;
+    }
+    k += dk;
+    t += dt;
+    if (t >= M) {
+      t -= M;
+      ++k;
+    }
+  }
+}
+// L2 prefetch of chunk g's segment for this CTA (one thread)
+TDMA_DEV void packed_prefetch(const PackedTables& PT, const Args& A, int g, int rank) {
+  const PackedChunk nx = PT.chunks[g];
+  const int s1 = rank * kPackT * nx.M;
+  const int n1 = max(0, min(nx.rows - s1, kPackT * nx.M));
+  if (n1 <= 0) return;
+  const int64_t b1 = nx.base + s1;
+  prefetch_l2_range((const float*)A.a + b1 - 1, 4ll * (n1 + 2));
+  prefetch_l2_range((const float*)A.b + b1, 4ll * n1);
+  prefetch_l2_range((const float*)A.c + b1 - 1, 4ll * (n1 + 2));
+  prefetch_l2_range((const double*)A.d + b1, 8ll * n1);
+}
+
+// Persistent: the grid holds the clusters that fit on the GPU at once; cluster q takes chunks
+// q, q + Q, q + 2Q, ... (Q clusters, chunks sorted longest first at plan time). Warps 0..6 of a
+// CTA compute (one partition per thread), warp 7 coordinates Stage B. Unless x is written over d,
+// the next chunk's copies go out as soon as x has left shared memory, so that they overlap the
+// per-line stop rule and its two cluster barriers; the rare further corrections then read the
+// coefficients and d from global memory.
+template <int C, bool TR>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
     packed_refine_kernel(const Args A, const PackedTables PT) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -488,12 +566,13 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
   float* tc = tb + kPackM * kPackPitch;
   double* td = reinterpret_cast<double*>(tc + kPackM * kPackPitch);
   float2* td2 = reinterpret_cast<float2*>(td);
-  double* tx = reinterpret_cast<double*>(ta);  // x leaves through the a and b space
+  float2* tx = reinterpret_cast<float2*>(ta);  // (x_0, dx) pairs leave through the a and b space
   const float* fa = (const float*)A.a;
   const float* fb = (const float*)A.b;
   const float* fc = (const float*)A.c;
   const double* gd = (const double*)A.d;
   double* gx = (double*)A.x;
+  const bool overlap = A.x != A.d;  // with x over d, d must stay in shared memory until done
 
   if (tid == 0) {
     mbar_init(&xbar[0], 1);
@@ -508,8 +587,13 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
   uint32_t xph[2] = {0u, 0u};
   uint32_t epoch = 0u;
   const int n_clusters = (int)(gridDim.x / C);
+  const int g0 = (int)(blockIdx.x / C);
+  if (g0 < PT.n_chunks) {
+    if (!coord) packed_issue_loads<C, TR>(PT, A, g0, rank, tid, ta, tb, tc, td);
+    else if (lane == 0 && g0 + n_clusters < PT.n_chunks) packed_prefetch(PT, A, g0 + n_clusters, rank);
+  }
 
-  for (int g = (int)(blockIdx.x / C); g < PT.n_chunks; g += n_clusters) {
+  for (int g = g0; g < PT.n_chunks; g += n_clusters) {
     const PackedChunk ch = PT.chunks[g];
     const int M = ch.M;
     const uint32_t inv = ((1u << 20) + (uint32_t)M - 1u) / (uint32_t)M;
@@ -522,38 +606,9 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
     // c = 0 on rows that end a line: row t ends one when row t + 1 starts one
     const uint32_t endmask = m > 0 ? ((mask >> 1) | (((meta.x >> 20) & 1u) << (m - 1))) : 0u;
     const int64_t gbase = ch.base + seg0;
+    const bool has_next = g + n_clusters < PT.n_chunks;
 
-    // ---------------- segment into shared memory (transposed), next chunk into L2
-    if (!coord) {
-      for (int i = tid; i < kPackT * M; i += kPackT) {
-        int k, t;
-        seg_row(i, M, inv, k, t);
-        const int pos = t * kPackPitch + k;
-        if (i < segn) {
-          cp_async4(ta + pos, fa + gbase + i);
-          cp_async4(tb + pos, fb + gbase + i);
-          cp_async4(tc + pos, fc + gbase + i);
-          cp_async8(td + pos, gd + gbase + i);
-        } else {  // identity row past the chunk's end
-          ta[pos] = 0.f;
-          tb[pos] = 1.f;
-          tc[pos] = 0.f;
-          td[pos] = 0.0;
-        }
-      }
-    } else if (lane == 0 && g + n_clusters < PT.n_chunks) {
-      const PackedChunk nx = PT.chunks[g + n_clusters];
-      const int s1 = rank * kPackT * nx.M;
-      const int n1 = max(0, min(nx.rows - s1, kPackT * nx.M));
-      if (n1 > 0) {
-        const int64_t b1 = nx.base + s1;
-        prefetch_l2_range(fa + b1, 4ll * n1);
-        prefetch_l2_range(fb + b1, 4ll * n1);
-        prefetch_l2_range(fc + b1, 4ll * n1);
-        prefetch_l2_range(gd + b1, 8ll * n1);
-      }
-    }
-    cp_async_wait_all();
+    cp_async_wait_all();  // this chunk's copies (issued during the previous chunk or before the loop)
     __syncthreads();
     if (!started) {
       cluster_wait();  // every CTA of the cluster has started: remote stores may begin
@@ -562,11 +617,6 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
     // a = 0 where a line starts, c = 0 where one ends (each thread its own rows)
     for (uint32_t bm = mask; bm; bm &= bm - 1u) ta[(__ffs(bm) - 1) * kPackPitch + tid] = 0.f;
     for (uint32_t bm = endmask; bm; bm &= bm - 1u) tc[(__ffs(bm) - 1) * kPackPitch + tid] = 0.f;
-    const float* ra = ta + tid;
-    const float* rb = tb + tid;
-    const float* rc = tc + tid;
-    const double* rd = td + tid;
-    float2* rd2 = td2 + tid;
     const bool edge_s = lane == 0 && kp > 0, edge_e = lane == 31 && kp + 1 < C * kPackT;
 
     if (coord) {
@@ -576,6 +626,11 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
       ++xph[1];
       __syncthreads();  // x staged by the compute warps
     } else {
+      const float* ra = ta + tid;
+      const float* rb = tb + tid;
+      const float* rc = tc + tid;
+      const double* rd = td + tid;
+      float2* rd2 = td2 + tid;
       switch (M) {
 #define TDMA_PASSES(MM)                                                                             \
   case MM:                                                                                           \
@@ -593,53 +648,53 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
       }
       __syncthreads();
     }
+    // The line maxima of every CTA are in: arrive on the cluster barrier now and wait only after
+    // x has gone out and the next chunk's copies are on their way.
+    ++epoch;
+    cluster_arrive();
+    // x = x_0 + dx in FP64 (exact widenings, one FP64 add), coalesced out of shared memory
     if (!coord) {
       for (int i = tid; i < segn; i += kPackT) {
         int k, t;
         seg_row(i, M, inv, k, t);
-        gx[gbase + i] = tx[t * kPackPitch + k];
+        const float2 v = tx[t * kPackPitch + k];
+        gx[gbase + i] = f2d_fast(v.x) + f2d_fast(v.y);
       }
     }
-    // ---------------- stop rule per line, verdict shared by the cluster
-    ++epoch;
-    cluster_arrive();
+    if (overlap) {
+      __syncthreads();  // the pairs have left shared memory: the next chunk may come in
+      if (has_next) {
+        if (!coord) packed_issue_loads<C, TR>(PT, A, g + n_clusters, rank, tid, ta, tb, tc, td);
+        else if (lane == 0 && g + 2 * n_clusters < PT.n_chunks) packed_prefetch(PT, A, g + 2 * n_clusters, rank);
+      }
+    }
     cluster_wait();  // the atomics of every CTA are complete and visible
-    bool more = !coord && packed_lines_verdict(mask, m, line, PT.norms, true, A.tol, A.max_iters <= 1, A.st);
-    more = __syncthreads_or(more) != 0;
-    if (more && tid < C) st_cluster_u32(map_rank(&s_more, tid), epoch);
-    cluster_arrive();
-    cluster_wait();
-    bool again = s_more == epoch;
+    // ---------------- stop rule per line: every CTA evaluates all lines of the chunk
+    bool again = __syncthreads_or(packed_first_verdict(ch, PT.norms, A.tol, A.max_iters <= 1, rank == 0, A.st)) != 0;
     int it = 1;
 
-    // ---------------- further corrections (rare): x read back from global memory
+    // ---------------- further corrections (rare): coefficients and x from global memory
+    if (again && it < A.max_iters) {  // x of every CTA went out after its first arrival: wait for it
+      cluster_arrive();
+      cluster_wait();
+    }
     while (again && it < A.max_iters) {
       ++it;
       const int q = it & 1;
-      if (!coord) {  // a and b again: x went out through their space
-        for (int i = tid; i < segn; i += kPackT) {
-          int k, t;
-          seg_row(i, M, inv, k, t);
-          const int pos = t * kPackPitch + k;
-          cp_async4(ta + pos, fa + gbase + i);
-          cp_async4(tb + pos, fb + gbase + i);
-        }
-      }
-      cp_async_wait_all();
-      __syncthreads();
       if (coord) {
         packed_coord_b<C>(wsl[q], dsl[q], csl[q], &xbar[q], xph[q] & 1u, rank, lane, alive, A.st);
         ++xph[q];
         __syncthreads();
       } else {
-        packed_later_pass(PT, ra, rb, rc, rd2, wsl[q], dsl[q], gx, gbase + (int64_t)tid * M, w, lane, kp, m, mask,
-                          endmask, line, seg0 + tid * M, ch.rows);
+        packed_later_pass<TR>(PT, fa, fb, fc, gd, overlap ? nullptr : td2 + tid, wsl[q], dsl[q], gx,
+                              gbase + (int64_t)tid * M, w, lane, kp, m, mask, endmask, line, seg0 + tid * M,
+                              ch.rows);
         __syncthreads();
       }
       ++epoch;
       cluster_arrive();
       cluster_wait();
-      more = !coord && packed_lines_verdict(mask, m, line, PT.norms, false, A.tol, it >= A.max_iters, A.st);
+      bool more = !coord && packed_later_verdict(mask, m, line, PT.norms, it == 2, A.tol, it >= A.max_iters, A.st);
       more = __syncthreads_or(more) != 0;
       if (more && tid < C) st_cluster_u32(map_rank(&s_more, tid), epoch);
       cluster_arrive();
@@ -647,6 +702,10 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
       again = s_more == epoch;
     }
     if (rank == 0 && tid == 0) report_iters(A.st, it);
+    if (!overlap && has_next) {  // every use of this chunk's shared memory is over (cluster barriers)
+      if (!coord) packed_issue_loads<C, TR>(PT, A, g + n_clusters, rank, tid, ta, tb, tc, td);
+      else if (lane == 0 && g + 2 * n_clusters < PT.n_chunks) packed_prefetch(PT, A, g + 2 * n_clusters, rank);
+    }
   }
   if (!started) cluster_wait();  // a cluster without a chunk still completes the start-up barrier
 }

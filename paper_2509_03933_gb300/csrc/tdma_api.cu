@@ -487,9 +487,9 @@ cudaError_t launch_forward(const tdma_plan_s* p, const Args& A, cudaStream_t s) 
       return launch_thomas(p->desc.precision, p->desc.nrhs, A, c, s);
     case TDMA_VARIANT_PACKED: {
       // the per-line maxima start from zero (the kernel also leaves them zero)
-      cudaError_t e = cudaMemsetAsync(p->pk.norms, 0, sizeof(uint32_t) * 3 * (size_t)p->desc.n_lines, s);
+      cudaError_t e = cudaMemsetAsync(p->pk.norms, 0, sizeof(uint32_t) * kPackNormWords * (size_t)p->desc.n_lines, s);
       if (e != cudaSuccess) return e;
-      packed_refine_kernel<kPackC><<<grid, block, sm, s>>>(A, p->pk);
+      packed_refine_kernel<kPackC, false><<<grid, block, sm, s>>>(A, p->pk);
       break;
     }
     case TDMA_VARIANT_RAGGED: {
@@ -556,7 +556,7 @@ cudaError_t prepare_kernel(const tdma_plan_s* p) {
     case TDMA_VARIANT_RAGGED:
       return cudaSuccess;
     case TDMA_VARIANT_PACKED:
-      return set_smem(packed_refine_kernel<kPackC>, sm);
+      return set_smem(packed_refine_kernel<kPackC, false>, sm);
   }
   return cudaSuccess;
 }
@@ -597,7 +597,12 @@ cudaError_t backward_impl(const tdma_plan_s* p, const void* a, const void* b, co
     const size_t sm = (size_t)rc.smem_bytes;
     if (d.precision == TDMA_F64) ragged_dc_kernel<double, true><<<rc.blocks, rc.threads_per_block, sm, s>>>(A, p->rt);
     else if (d.precision == TDMA_F32) ragged_dc_kernel<float, true><<<rc.blocks, rc.threads_per_block, sm, s>>>(A, p->rt);
-    else ragged_refine_kernel<true><<<rc.blocks, rc.threads_per_block, sm, s>>>(A, p->rt);
+    else if (p->pk_mem) {  // the chunk kernel on the transposed rows
+      e = cudaMemsetAsync(p->pk.norms, 0, sizeof(uint32_t) * kPackNormWords * (size_t)d.n_lines, s);
+      if (e != cudaSuccess) return e;
+      const tdma_config_t& pc = p->cfg;
+      packed_refine_kernel<kPackC, true><<<pc.blocks, pc.threads_per_block, (size_t)pc.smem_bytes, s>>>(A, p->pk);
+    } else ragged_refine_kernel<true><<<rc.blocks, rc.threads_per_block, sm, s>>>(A, p->rt);
     e = cudaGetLastError();
     if (e != cudaSuccess || (!ga && !gb && !gc)) return e;
     const int64_t blocks = std::min<int64_t>((d.n_lines + 7) / 8, 65535);
@@ -767,7 +772,7 @@ bool build_packed(tdma_plan_s* p) {
     const Span& sp = spans[g];
     // rows per partition: even (a compiled shape), at least 2, partitions full up to 896 M rows
     const int rows = (int)sp.rows, M = std::max(2, ((rows + PPC - 1) / PPC + 1) / 2 * 2);
-    chunks[g] = PackedChunk{off[order[sp.first]], rows, M, (int32_t)sp.first, 0};
+    chunks[g] = PackedChunk{off[order[sp.first]], rows, M, (int32_t)sp.first, (int32_t)sp.count};
     starts.assign(1, 0);  // first row of every line of the chunk, relative to the chunk
     for (int64_t j = 1; j < sp.count; ++j) starts.push_back(starts.back() + len[order[sp.first + j - 1]]);
     size_t li = 0;  // line of the current row
@@ -789,24 +794,28 @@ bool build_packed(tdma_plan_s* p) {
   const size_t b_chunks = sizeof(PackedChunk) * chunks.size();
   const size_t off_meta = (b_chunks + 255) / 256 * 256;
   const size_t off_norms = off_meta + (sizeof(uint2) * meta.size() + 255) / 256 * 256;
-  const size_t total = off_norms + sizeof(uint32_t) * 3 * (size_t)L;
+  const size_t total = off_norms + sizeof(uint32_t) * kPackNormWords * (size_t)L;
   void* mem = nullptr;
   if (cudaMalloc(&mem, total) != cudaSuccess) { (void)cudaGetLastError(); return false; }
   unsigned char* m = (unsigned char*)mem;
   if (cudaMemcpy(m, chunks.data(), b_chunks, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(m + off_meta, meta.data(), sizeof(uint2) * meta.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(m + off_norms, 0, sizeof(uint32_t) * 3 * (size_t)L) != cudaSuccess) {
+      cudaMemset(m + off_norms, 0, sizeof(uint32_t) * kPackNormWords * (size_t)L) != cudaSuccess) {
     cudaFree(mem);
     return false;
   }
   const size_t sm = (size_t)kPackM * kPackPitch * (3 * sizeof(float) + sizeof(double));
-  if (set_smem(packed_refine_kernel<kPackC>, sm) != cudaSuccess) { cudaFree(mem); return false; }
+  if (set_smem(packed_refine_kernel<kPackC, false>, sm) != cudaSuccess ||
+      set_smem(packed_refine_kernel<kPackC, true>, sm) != cudaSuccess) {
+    cudaFree(mem);
+    return false;
+  }
   cudaLaunchConfig_t lc{};
   lc.gridDim = dim3(kPackC);
   lc.blockDim = dim3(kPackThreads);
   lc.dynamicSmemBytes = sm;
   int resident = 0;
-  if (cudaOccupancyMaxActiveClusters(&resident, packed_refine_kernel<kPackC>, &lc) != cudaSuccess) resident = 0;
+  if (cudaOccupancyMaxActiveClusters(&resident, packed_refine_kernel<kPackC, false>, &lc) != cudaSuccess) resident = 0;
   (void)cudaGetLastError();
   p->pk_mem = mem;
   p->pk.chunks = (const PackedChunk*)m;

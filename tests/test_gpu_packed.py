@@ -170,3 +170,58 @@ def test_line_longer_than_a_chunk_uses_group_kernel():
     assert plan.config["variant"] == RAGGED
     o, n = offs.cpu().numpy(), lens.cpu().numpy()
     assert _err(x, _oracle(a, b, c, d, o, n), o, n) <= 1e-12
+
+
+def _grads(a, b, c, x, w, plan):
+    ga, gb, gc, gd = (torch.empty_like(a), torch.empty_like(b), torch.empty_like(c), torch.empty_like(x))
+    plan.backward(a, b, c, x, w, ga, gb, gc, gd)
+    torch.cuda.synchronize()
+    return ga, gb, gc, gd
+
+
+def test_packed_backward_matches_group_kernel_and_oracle():
+    # the adjoint solve A^T lambda = w on the chunk kernel (transposed rows) against the group
+    # kernel and, on sampled lines, against the oracle's adjoint
+    lengths = synth.ragged_lengths(400, 16, 16384, seed=7)
+    a, b, c, d, offs, lens = _problem(lengths, 18)
+    x, p1 = _solve(a, b, c, d, offs, lens)
+    w = synth.normal(18, synth.AID["w"], torch.arange(x.numel(), device="cuda"))
+    g1 = _grads(a, b, c, x, w, p1)
+    assert p1.last_error()[0] == 0
+    os.environ["TDMA_DISABLE_PACKED"] = "1"
+    try:
+        _, p2 = _solve(a, b, c, d, offs, lens)
+    finally:
+        del os.environ["TDMA_DISABLE_PACKED"]
+    g2 = _grads(a, b, c, x, w, p2)
+    assert O.rel_l2(g1[3].cpu().numpy(), g2[3].cpu().numpy()) <= 2e-12
+    o, n = offs.cpu().numpy(), lens.cpu().numpy()
+    h = lambda t: t.double().cpu().numpy()
+    for l in list(np.argsort(-n)[:3]) + [int(np.argmin(n)), 17, 200]:
+        s = slice(o[l], o[l] + n[l])
+        ref = O.adjoint_grads(h(a)[s], h(b)[s], h(c)[s], h(x)[s], h(w)[s])
+        assert O.rel_l2(h(g1[3])[s], ref[3]) <= 1e-12
+        for got, want in zip(g1[:3], ref[:3]):
+            assert O.rel_l2(h(got)[s], want) <= 1e-6  # float gradients of float coefficients
+
+
+def test_packed_backward_second_correction():
+    # tridiag(-1, 2.001, -1) (condition number about 4000, its own transpose): the adjoint solve
+    # on the transposed rows needs more than one correction too; the nonsymmetric case is covered
+    # against the group kernel above
+    lengths = np.array([4000, 9000, 31], np.int32)
+    a, b, c, d, offs, lens = _problem(lengths, 19)
+    a.fill_(-1.0)
+    c.fill_(-1.0)
+    b.fill_(2.001)
+    x, plan = _solve(a, b, c, d, offs, lens)
+    w = torch.cos(torch.arange(x.numel(), device="cuda", dtype=torch.float64) * 0.11)
+    g = _grads(a, b, c, x, w, plan)
+    st, iters = plan.last_error()
+    assert st == 0 and iters >= 2
+    o, n = offs.cpu().numpy(), lens.cpu().numpy()
+    h = lambda t: t.double().cpu().numpy()
+    for l in range(len(o)):
+        s = slice(o[l], o[l] + n[l])
+        at, bt, ct = O.transpose_coefficients(h(a)[s], h(b)[s], h(c)[s])
+        assert O.rel_l2(h(g[3])[s], O.thomas_ext(at, bt, ct, h(w)[s])) <= 1e-12
