@@ -772,8 +772,13 @@ bool build_packed(tdma_plan_s* p) {
   std::vector<int32_t> starts;
   for (size_t g = 0; g < spans.size(); ++g) {
     const Span& sp = spans[g];
-    // rows per partition: even (a compiled shape), at least 2, partitions full up to 896 M rows
-    const int rows = (int)sp.rows, M = std::max(2, ((rows + PPC - 1) / PPC + 1) / 2 * 2);
+    // rows per partition: the smallest compiled M with 896 M >= rows (identity rows fill the rest)
+    const int rows = (int)sp.rows, need = (rows + PPC - 1) / PPC;
+    int M = 0;
+#define TDMA_PICK_M(MM) if (M == 0 && MM >= need) M = MM;
+    TDMA_PACKED_M(TDMA_PICK_M)
+#undef TDMA_PICK_M
+    if (M == 0) return false;
     chunks[g] = PackedChunk{off[order[sp.first]], rows, M, (int32_t)sp.first, (int32_t)sp.count};
     starts.assign(1, 0);  // first row of every line of the chunk, relative to the chunk
     for (int64_t j = 1; j < sp.count; ++j) starts.push_back(starts.back() + len[order[sp.first + j - 1]]);
