@@ -190,6 +190,13 @@ def sample_oracle_lines(g, ys: int):
     return sl(g["a32"]), sl(g["b32"]), sl(g["c32"]), sl(g["d"])
 
 
+def synth_lines_check(hx, ys: int, nl: int, ref) -> float:
+    """Relative L2 error of the first ``nl`` lines of the first ``ys`` y-rows of a host solution."""
+    import oracle
+    import synth
+    return oracle.rel_l2(synth.line_view(hx[:, :ys, :], 0).numpy()[:nl], ref)
+
+
 def time_steps(fn, steps, warmup, stream):
     """Device time of ``steps`` calls after ``warmup`` calls; per-launch events on ``stream``."""
     for _ in range(warmup):
@@ -420,7 +427,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=0, help="solve only the first ny y-rows (profiling runs)")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--e2e-batches", type=int, default=8, help="slices of lines in the pipelined host solve")
     ap.add_argument("--cpu-lines", type=int, default=32768, help="lines in the CPU oracle sample")
     ap.add_argument("--ref-lines", type=int, default=4096, help="lines per reference-arm step")
     ap.add_argument("--no-e2e", action="store_true")
@@ -513,7 +521,9 @@ def main():
     err = {"f32r": oracle.rel_l2(got_r, ref), "f64": oracle.rel_l2(got_d, ref), "lines_checked": int(nl),
            "f32r_status": st, "f64_status": st_d, "f32r_corrections_max": iters}
 
-    # ---------------- end to end: pinned host buffers, copies inside the timed region
+    # ---------------- end to end: pinned host buffers, copies inside the timed region, through the
+    # pipelined host solve (slices of lines in flight on two streams: host-to-device copies,
+    # solves and device-to-host copies of different slices overlap)
     e2e = None
     if not args.no_e2e:
         del g, a, b, c
@@ -523,18 +533,19 @@ def main():
         for k, v in (("a", a32), ("b", b32), ("c", c32), ("d", d)):
             h[k].copy_(v)
         hx = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
-
-        def e2e_step():
-            for k, dv in (("a", a32), ("b", b32), ("c", c32), ("d", d)):
-                dv.copy_(h[k], non_blocking=True)
-            plan_r.solve(a32, b32, c32, d, x)
-            hx.copy_(x, non_blocking=True)
-
-        tot, _ = time_steps(e2e_step, args.e2e_steps, 1, stream)
         bi = sum(v.numel() * v.element_size() for v in (a32, b32, c32, d))
+        bo = x.numel() * x.element_size()
+        shape = tuple(d.shape)
+        a32 = b32 = c32 = d = x = None  # the pipeline stages slices in its own device buffers
+        torch.cuda.empty_cache()
+        pipe = tdma.HostPipeline(shape, axis=0, precision="f32r", batches=args.e2e_batches, slots=2, device=dev)
+        tot, _ = time_steps(lambda: pipe.solve(h["a"], h["b"], h["c"], h["d"], hx), args.e2e_steps, 2, stream)
+        got_e = synth_lines_check(hx, ys, nl, ref)
         e2e = {"value": U / (tot / args.e2e_steps * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi,
-               "d2h_bytes_per_step": x.numel() * x.element_size(), "steps": args.e2e_steps,
-               "ms_per_step": tot / args.e2e_steps}
+               "d2h_bytes_per_step": bo, "steps": args.e2e_steps, "ms_per_step": tot / args.e2e_steps,
+               "api": f"HostPipeline(batches={args.e2e_batches}, slots=2) -> tdma_solve_host",
+               "rel_l2_error": got_e}
+        del pipe, h, hx
 
     cfg_d = plan_d.config
     suite = None

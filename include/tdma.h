@@ -175,6 +175,41 @@ tdma_status_t tdma_last_device_error(tdma_plan_t plan, void* stream, int32_t* in
 /* Static, human-readable name of a status code. */
 const char* tdma_status_string(tdma_status_t status);
 
+/* Layout of a batch of lines in HOST memory for tdma_solve_host: n unknowns per line, n_lines
+ * lines; unknown i of line l is element l * line_stride + i * row_stride of each array. Two forms
+ * are accepted: adjacent lines (line_stride = 1, row_stride >= n_lines; e.g. a C-order grid
+ * solved along its slowest axis) and contiguous lines (row_stride = 1, line_stride >= n). */
+typedef struct {
+  int64_t n;
+  int64_t n_lines;
+  int64_t line_stride;
+  int64_t row_stride;
+} tdma_host_layout_t;
+
+/* Solve lines held in HOST memory (page-locked for full copy speed) as a pipeline of slices
+ * (Section 4.2: batches of systems in flight; on one GPU, slices of lines in flight on CUDA
+ * streams): the host lines are cut into consecutive slices of plan->n_lines lines; slice s goes
+ * to staging slot s mod n_slots, whose stream copies the slice's a, b, c, d to the slot's device
+ * buffers, solves it with `plan` and copies x back, so that the copies of one slice overlap the
+ * solve of another (host-to-device, device-to-host and kernels run concurrently).
+ *   plan          created for ONE slice in the slot buffers' compact layout: n as the host
+ *                 layout, n_lines = slice lines, and either elem_stride = inner_count = slice
+ *                 lines, inner_stride = 1 (adjacent lines) or elem_stride = 1, inner_stride = n,
+ *                 inner_count = slice lines (contiguous lines); nrhs = 1, no broadcast, no shift.
+ *   layout        the host layout (above); layout->n_lines must be a multiple of the slice lines.
+ *   a, b, c, d, x host arrays in the plan's element types; x may not alias d.
+ *   slot_buffers  n_slots x 5 device pointers (a, b, c, d, x of slot k at [5k .. 5k+4]), each
+ *                 holding one slice; slot_workspaces: n_slots device pointers of workspace_bytes
+ *                 each (the plan's workspace; NULL entries allowed when it needs none).
+ *   streams       n_slots cudaStream_t (as void*), one per slot.
+ * Enqueues everything and returns without waiting; allocates nothing. Errors: TDMA_ERR_INVALID_ARG
+ * (layouts that do not match, n_slots < 1, a slice count that does not divide the lines),
+ * TDMA_ERR_UNSUPPORTED (nrhs, broadcast or shift), TDMA_ERR_WORKSPACE, TDMA_ERR_CUDA. */
+tdma_status_t tdma_solve_host(tdma_plan_t plan, const tdma_host_layout_t* layout, const void* a, const void* b,
+                              const void* c, const void* d, void* x, int32_t n_slots,
+                              void* const* slot_buffers, void* const* slot_workspaces,
+                              size_t workspace_bytes, void* const* streams);
+
 /* Solve A x = d with the one-partition Thomas kernel without allocating anything (the paper has
  * no counterpart; this serves callers that must not allocate device memory while they run, e.g.
  * a solver loop that fixed its GPU memory at start-up, or a host program whose own memory pool

@@ -16,7 +16,7 @@ import torch
 from . import _build
 
 __all__ = ["Plan", "solve", "solve_ragged", "solve_backward", "TDMASolve", "line_layout", "TDMAError", "F64", "F32",
-           "F32_REFINE", "load_library", "declared_symbols", "sweep_graph"]
+           "F32_REFINE", "load_library", "declared_symbols", "sweep_graph", "HostPipeline", "HostLayout"]
 
 F64, F32, F32_REFINE, F64_REFINE = 0, 1, 2, 3
 _PREC = {"f64": F64, "f32": F32, "f32r": F32_REFINE, "f64r": F64_REFINE, F64: F64, F32: F32, F32_REFINE: F32_REFINE,
@@ -47,6 +47,11 @@ class Config(ctypes.Structure):
                 ("lines_per_block", ctypes.c_int32), ("threads_per_block", ctypes.c_int32),
                 ("variant", ctypes.c_int32), ("blocks", ctypes.c_int32), ("smem_bytes", ctypes.c_int64),
                 ("workspace_bytes", ctypes.c_int64)]
+
+
+class HostLayout(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("n_lines", ctypes.c_int64), ("line_stride", ctypes.c_int64),
+                ("row_stride", ctypes.c_int64)]
 
 
 _LIB = None
@@ -81,6 +86,9 @@ def load_library(build: bool = True) -> ctypes.CDLL:
     lib.tdma_status_string.restype = ctypes.c_char_p
     lib.tdma_solve_thomas_static.argtypes = [ctypes.POINTER(Desc)] + [_VP] * 6
     lib.tdma_solve_thomas_static.restype = st
+    lib.tdma_solve_host.argtypes = [_VP, ctypes.POINTER(HostLayout)] + [_VP] * 5 + [ctypes.c_int32, _VP, _VP,
+                                                                                     ctypes.c_size_t, _VP]
+    lib.tdma_solve_host.restype = st
     _LIB = lib
     return lib
 
@@ -226,6 +234,69 @@ class Plan:
         info = ctypes.c_int32(0)
         st = self._lib.tdma_last_device_error(self._h, _stream(stream), ctypes.byref(info))
         return st, info.value
+
+
+class HostPipeline:
+    """Solve a grid held in host memory as a pipeline of slices (tdma_solve_host): slices of lines
+    move through ``slots`` device staging buffers, each on its own stream, so that host-to-device
+    copies, solves and device-to-host copies of different slices run at the same time.
+
+    ``shape`` is a C-order grid and ``axis`` the solve axis: 0 (lines adjacent in memory, rows
+    strided) or the last axis (contiguous lines). ``batches`` slices split the lines evenly. The
+    staging buffers, streams and the slice plan are made once; ``solve`` takes host tensors
+    (pinned for full copy speed) of the precision's types and enqueues everything; ``synchronize``
+    waits for it."""
+
+    def __init__(self, shape, axis=0, precision="f64", batches=8, slots=3, device="cuda"):
+        self._lib = load_library()
+        shape = tuple(int(v) for v in shape)
+        axis = axis % len(shape)
+        if axis not in (0, len(shape) - 1):
+            raise ValueError("HostPipeline solves along the first or the last axis")
+        n = shape[axis]
+        lines = 1
+        for k, v in enumerate(shape):
+            if k != axis:
+                lines *= v
+        if lines % batches:
+            raise ValueError("batches must divide the number of lines")
+        L = lines // batches
+        if axis == 0:
+            self.layout = HostLayout(n=n, n_lines=lines, line_stride=1, row_stride=lines)
+            self.plan = Plan(n, L, elem_stride=L, inner_count=L, inner_stride=1, precision=precision)
+        else:
+            self.layout = HostLayout(n=n, n_lines=lines, line_stride=n, row_stride=1)
+            self.plan = Plan(n, L, elem_stride=1, inner_count=L, inner_stride=n, precision=precision)
+        cdt = torch.float64 if precision in ("f64", "f64r") else torch.float32
+        ddt = torch.float32 if precision == "f32" else torch.float64
+        dev = torch.device(device)
+        self.buffers = [[torch.empty(n * L, dtype=t, device=dev) for t in (cdt, cdt, cdt, ddt, ddt)]
+                        for _ in range(slots)]
+        self.workspaces = [self.plan.workspace(dev) if k == 0 else
+                           torch.empty(max(1, self.plan.workspace_bytes), dtype=torch.uint8, device=dev)
+                           for k in range(slots)] if self.plan.workspace_bytes else None
+        self.streams = [torch.cuda.Stream(device=dev) for _ in range(slots)]
+        self._bufs = (_VP * (5 * slots))(*[t.data_ptr() for bl in self.buffers for t in bl])
+        self._ws = (_VP * slots)(*[w.data_ptr() for w in self.workspaces]) if self.workspaces else None
+        self._st = (_VP * slots)(*[s.cuda_stream for s in self.streams])
+        self.slots = slots
+
+    def solve(self, a, b, c, d, x):
+        """Enqueue the pipelined solve of host arrays a, b, c, d into host array x (x must not be d)."""
+        for s in self.streams:
+            s.wait_stream(torch.cuda.current_stream())
+        st = self._lib.tdma_solve_host(self.plan._h, ctypes.byref(self.layout), _ptr(a), _ptr(b), _ptr(c), _ptr(d),
+                                       _ptr(x), self.slots, self._bufs, self._ws,
+                                       ctypes.c_size_t(self.plan.workspace_bytes), self._st)
+        if st != 0:
+            raise TDMAError(st, "tdma_solve_host")
+        for s in self.streams:  # work queued on the caller's stream afterwards follows the pipeline
+            torch.cuda.current_stream().wait_stream(s)
+        return x
+
+    def synchronize(self):
+        for s in self.streams:
+            s.synchronize()
 
 
 def _check_same_layout(ref, *ts):

@@ -1124,6 +1124,65 @@ static tdma_status_t check_ptrs(const tdma_plan_s* p, const void* a, const void*
   return TDMA_OK;
 }
 
+tdma_status_t tdma_solve_host(tdma_plan_t p, const tdma_host_layout_t* hl, const void* a, const void* b,
+                              const void* c, const void* d, void* x, int32_t n_slots, void* const* bufs,
+                              void* const* wss, size_t ws_bytes, void* const* streams) {
+  if (!p || !hl || !bufs || !streams || n_slots < 1 || !a || !b || !c || !d || !x || x == d)
+    return TDMA_ERR_INVALID_ARG;
+  const tdma_desc_t& dsc = p->desc;
+  if (dsc.nrhs != 1 || dsc.coef_broadcast || dsc.diag_shift) return TDMA_ERR_UNSUPPORTED;
+  const int64_t n = hl->n, L = dsc.n_lines;
+  if (dsc.n <= 0 || n != dsc.n || L < 1 || hl->n_lines < 0 || hl->n_lines % L) return TDMA_ERR_INVALID_ARG;
+  // host form and the matching compact slice layout of the plan
+  const bool adjacent = hl->line_stride == 1 && hl->row_stride >= hl->n_lines;
+  const bool contiguous = hl->row_stride == 1 && hl->line_stride >= n;
+  if (!adjacent && !contiguous) return TDMA_ERR_INVALID_ARG;
+  if (adjacent && !(dsc.elem_stride == L && dsc.inner_count >= L && dsc.inner_stride == 1))
+    return TDMA_ERR_INVALID_ARG;
+  if (!adjacent && !(dsc.elem_stride == 1 && dsc.inner_stride == n && dsc.inner_count >= L)) return TDMA_ERR_INVALID_ARG;
+  if (p->workspace > 0 && ws_bytes < p->workspace) return TDMA_ERR_WORKSPACE;
+  for (int k = 0; k < n_slots; ++k) {
+    for (int q = 0; q < 5; ++q)
+      if (!bufs[5 * k + q]) return TDMA_ERR_INVALID_ARG;
+    if (p->workspace > 0 && (!wss || !wss[k])) return TDMA_ERR_WORKSPACE;
+  }
+  const size_t ce = elem_bytes_coef(dsc.precision), de = dsc.precision == TDMA_F32 ? 4 : 8;
+  const void* host_in[4] = {a, b, c, d};
+  const size_t eb[5] = {ce, ce, ce, de, de};
+  (void)cudaGetLastError();
+  const int64_t S = hl->n_lines / L;
+  // one slice's copy between host (full layout) and a slot buffer (compact layout)
+  auto copy = [&](void* dst, const void* src, size_t e, int64_t l0, bool h2d, cudaStream_t st) -> cudaError_t {
+    const cudaMemcpyKind kind = h2d ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost;
+    if (adjacent) {  // n rows of L adjacent elements, rows row_stride apart on the host
+      const size_t hp = (size_t)hl->row_stride * e, dp = (size_t)L * e;
+      unsigned char* hbase = (unsigned char*)(h2d ? src : dst) + (size_t)l0 * e;
+      return h2d ? cudaMemcpy2DAsync(dst, dp, hbase, hp, (size_t)L * e, (size_t)n, kind, st)
+                 : cudaMemcpy2DAsync(hbase, hp, src, dp, (size_t)L * e, (size_t)n, kind, st);
+    }
+    // L lines of n contiguous elements, lines line_stride apart on the host
+    const size_t hp = (size_t)hl->line_stride * e, dp = (size_t)n * e;
+    unsigned char* hbase = (unsigned char*)(h2d ? src : dst) + (size_t)l0 * hl->line_stride * e;
+    if (hp == dp)
+      return h2d ? cudaMemcpyAsync(dst, hbase, (size_t)L * dp, kind, st) : cudaMemcpyAsync(hbase, src, (size_t)L * dp, kind, st);
+    return h2d ? cudaMemcpy2DAsync(dst, dp, hbase, hp, dp, (size_t)L, kind, st)
+               : cudaMemcpy2DAsync(hbase, hp, src, dp, dp, (size_t)L, kind, st);
+  };
+  for (int64_t sidx = 0; sidx < S; ++sidx) {
+    const int k = (int)(sidx % n_slots);
+    cudaStream_t st = (cudaStream_t)streams[k];
+    void* const* sb = bufs + 5 * k;
+    const int64_t l0 = sidx * L;
+    for (int q = 0; q < 4; ++q)
+      if (copy(sb[q], host_in[q], eb[q], l0, true, st) != cudaSuccess) return TDMA_ERR_CUDA;
+    const Args A = make_args(p, sb[0], sb[1], sb[2], sb[3], sb[4], wss ? wss[k] : nullptr);
+    const cudaError_t e = p->refine64 ? solve_refine64(p, A, st) : launch_forward(p, A, st);
+    if (e != cudaSuccess) return TDMA_ERR_CUDA;
+    if (copy(x, sb[4], eb[4], l0, false, st) != cudaSuccess) return TDMA_ERR_CUDA;
+  }
+  return TDMA_OK;
+}
+
 tdma_status_t tdma_solve(tdma_plan_t p, const void* a, const void* b, const void* c, const void* d, void* x,
                          void* ws, size_t ws_bytes, void* stream) {
   if (!p) return TDMA_ERR_INVALID_ARG;
