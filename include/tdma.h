@@ -40,10 +40,14 @@
  *   TDMA_F32_REFINE  a, b, c float; d, x, diag_shift double. Sweeps in float, then
  *                    iterative refinement with an extra-precise residual r = d - A x
  *                    until the estimated error is below refine_tol (relative, per line).
- *   TDMA_F64_REFINE  as TDMA_F64, followed by max_refine_iters (default 1) corrections from a
- *                    double-double residual r = d - A x, for badly conditioned lines where
- *                    plain FP64 elimination stops a few 1e-12 short. x must not alias d; the
- *                    workspace holds one extra right-hand-side buffer.
+ *   TDMA_F64_REFINE  as TDMA_F64, followed by max_refine_iters (default 1) corrections, for
+ *                    badly conditioned lines where plain FP64 elimination stops a few 1e-12
+ *                    short: the residual r = d - A x is formed exactly (integer arithmetic on
+ *                    the 53-bit significands) and the correction A dx = r is solved in FP32.
+ *                    Lines whose residuals fall below the float range (right-hand sides under
+ *                    about 1e-22) keep the plain FP64 accuracy. x must not alias d; the
+ *                    workspace holds the FP32 correction's factors (4 (1 + nrhs) bytes per
+ *                    unknown).
  *
  * Errors
  *   Every call validates its arguments synchronously and returns a status; nothing aborts.

@@ -1,78 +1,98 @@
-// FP64 solve followed by iterative refinement with a double-double residual (TDMA_F64_REFINE).
+// FP64 solve followed by a correction from an exact residual (TDMA_F64_REFINE).
 //
 // For badly conditioned lines (the pinned zero mode of the Poisson wavenumber lines has
 // condition number about 1e9) a plain FP64 elimination is a few 1e-12 away from the exact
-// solution. Mixed-precision refinement with an extra-precise residual (Wilkinson 1963; Demmel
-// et al. 2006) removes that: r = d - A x evaluated in double-double arithmetic (FMA-based
-// TwoProduct and Knuth's TwoSum, accurate as if computed with twice the precision; Ogita, Rump
-// and Oishi 2005), one more FP64 solve for the correction, x += correction. The FP64 solve
-// contracts the error by its own relative error (about 1e-12 here), so one correction leaves
-// only the rounding of x itself.
+// solution. Mixed-precision iterative refinement (Wilkinson 1963; Moler 1967; Carson and Higham
+// 2018) removes that: with the residual r = d - A x evaluated more precisely than the solve and a
+// correction solve whose relative error is well below one, x + dx is accurate to the residual's
+// precision. Here the residual is exact (residual_exact in bits.cuh: 106-bit products and a
+// 128-bit fixed-point sum on the integer pipes) and the correction is solved in FP32 with the
+// coefficients truncated to float: its relative error, about kappa 2^-23, stays near 1e-3 even on
+// the worst Poisson modes, so one correction takes their error from about 2e-12 to the 1e-15
+// range. GB300 runs FP64 arithmetic at 1/64 of the FP32 rate; this correction uses three FP64 adds
+// per unknown (b + shift, and x += dx per right-hand side) where a double-double residual and a
+// second FP64 solve took about 70.
 //
-// The residual and correction live in a workspace buffer R. With broadcast coefficients the
-// correction solve does not depend on the layout of the right-hand side, so R is compact
-// ([row][line]); otherwise R uses the plan's layout.
+// The residual is one thread per unknown (no dependence along the line); the FP32 correction is
+// one thread per line, with its factors c' and the residuals / forward right-hand sides in the
+// workspace ([row][line], coalesced across adjacent lines). Residuals
+// below the float range (right-hand sides under about 1e-22) are flushed to zero: such lines keep
+// the plain FP64 accuracy.
 #pragma once
 #include "layout.cuh"
+#include "bits.cuh"
 
 namespace tdma {
 
-struct dd { double h, l; };
-
-TDMA_DEV dd two_sum_d(double a, double b) {
-  const double s = __dadd_rn(a, b);
-  const double bb = __dsub_rn(s, a);
-  return {s, __dadd_rn(__dsub_rn(a, __dsub_rn(s, bb)), __dsub_rn(b, bb))};
-}
-TDMA_DEV dd two_prod_d(double a, double b) {
-  const double p = __dmul_rn(a, b);
-  return {p, __fma_rn(a, b, -p)};
-}
-
-// r_i = d_i - (a_i x_{i-1} + b_i x_i + c_i x_{i+1}) accumulated in double-double (Dot2-style).
-TDMA_DEV double residual_dd(double a, double b, double c, double d, double xm, double x0, double xp) {
-  const dd p1 = two_prod_d(b, x0), p2 = two_prod_d(a, xm), p3 = two_prod_d(c, xp);
-  const dd s1 = two_sum_d(d, -p1.h);
-  const dd s2 = two_sum_d(s1.h, -p2.h);
-  const dd s3 = two_sum_d(s2.h, -p3.h);
-  const double err = ((s1.l + s2.l) + s3.l) - ((p1.l + p2.l) + p3.l);
-  return __dadd_rn(s3.h, err);
-}
-
-// One thread per (line, row); `lr` is the layout of R (compact or the plan's).
+// r = d - A x exactly for every (line, row), one thread each (adjacent threads on adjacent lines),
+// into R ([row][line], nrhs floats each).
 template <int NR>
-__global__ void __launch_bounds__(256) residual64_kernel(const Args A, const Layout lr, double* __restrict__ R) {
+__global__ void __launch_bounds__(256) residual_exact_kernel(const Args A, float* __restrict__ R) {
   const Layout& L = A.lay;
-  const int64_t total = L.n * L.n_lines;
   const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  const int64_t line = idx % L.n_lines, i = idx / L.n_lines;  // adjacent threads: adjacent lines
-  const int64_t e = L.off(line) + i * L.es, er = lr.off(line) + i * lr.es;
-  const int64_t ci = A.bcast ? i : e;
+  if (idx >= L.n * L.n_lines) return;
+  const int64_t line = idx % L.n_lines, i = idx / L.n_lines;
+  const int64_t e = L.off(line) + i * L.es, ci = A.bcast ? i : e;
   const double shift = A.shift ? ldg((const double*)A.shift + line) : 0.0;
-  const double a = i > 0 ? ldg((const double*)A.a + ci) : 0.0;
-  const double b = ldg((const double*)A.b + ci) + shift;
-  const double c = i < L.n - 1 ? ldg((const double*)A.c + ci) : 0.0;
+  const DecF64 da = dec_f64(i > 0 ? ldg((const double*)A.a + ci) : 0.0);
+  const DecF64 db = dec_f64(ldg((const double*)A.b + ci) + shift);  // the b of the FP64 solve
+  const DecF64 dc = dec_f64(i < L.n - 1 ? ldg((const double*)A.c + ci) : 0.0);
   const double* X = (const double*)A.x;
   const double* D = (const double*)A.d;
 #pragma unroll
   for (int q = 0; q < NR; ++q) {
-    const double xm = i > 0 ? X[(e - L.es) * NR + q] : 0.0;
-    const double xp = i < L.n - 1 ? X[(e + L.es) * NR + q] : 0.0;
-    R[er * NR + q] = residual_dd(a, b, c, D[e * NR + q], xm, X[e * NR + q], xp);
+    const DecF64 dxm = dec_f64(i > 0 ? X[(e - L.es) * NR + q] : 0.0);
+    const DecF64 dxp = dec_f64(i < L.n - 1 ? X[(e + L.es) * NR + q] : 0.0);
+    R[idx * NR + q] = residual_exact_dec(dec_f64(ldg(D + e * NR + q)), da, dxm, db, dec_f64(X[e * NR + q]), dc, dxp);
   }
 }
 
+// The FP32 correction A32 dx = r (A32: coefficients truncated to float) and x += dx, one thread
+// per line: forward elimination over R in place (c' to cw), back substitution into x.
 template <int NR>
-__global__ void __launch_bounds__(256) update64_kernel(const Layout L, const Layout lr, double* __restrict__ X,
-                                                       const double* __restrict__ R) {
-  const int64_t total = L.n * L.n_lines;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  const int64_t line = idx % L.n_lines, i = idx / L.n_lines;
-  const int64_t e = L.off(line) + i * L.es, er = lr.off(line) + i * lr.es;
+__global__ void __launch_bounds__(128) correction32_kernel(const Args A, float* __restrict__ cw, float* __restrict__ R) {
+  const int64_t line = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (line >= A.lay.n_lines) return;
+  const int64_t n = A.lay.n, es = A.lay.es, L = A.lay.n_lines;
+  const int64_t base = A.lay.off(line);
+  const double shift = A.shift ? ldg((const double*)A.shift + line) : 0.0;
+  double* X = (double*)A.x;
+  float cp = 0.f, rp[NR];
 #pragma unroll
-  for (int q = 0; q < NR; ++q) X[e * NR + q] += R[er * NR + q];
+  for (int q = 0; q < NR; ++q) rp[q] = 0.f;
+  for (int64_t i = 0; i < n; ++i) {
+    const int64_t ci = A.bcast ? i : base + i * es;
+    const float a32 = i > 0 ? f64_to_f32_trunc(ldg((const double*)A.a + ci)) : 0.f;
+    const float b32 = f64_to_f32_trunc(ldg((const double*)A.b + ci) + shift);
+    const float c32 = i < n - 1 ? f64_to_f32_trunc(ldg((const double*)A.c + ci)) : 0.f;
+    const float w = rcp(fmaf(-a32, cp, b32));
+    cp = c32 * w;
+    cw[i * L + line] = cp;
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      float* r = R + (i * L + line) * NR + q;
+      rp[q] = fmaf(-a32, rp[q], *r) * w;
+      *r = rp[q];
+    }
+  }
+  float dn[NR];
+  bool ok = true;
+#pragma unroll
+  for (int q = 0; q < NR; ++q) dn[q] = rp[q];
+  for (int64_t i = n - 1; i >= 0; --i) {
+    const int64_t e = base + i * es;
+    if (i < n - 1) {
+      const float cpi = cw[i * L + line];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) dn[q] = fmaf(-cpi, dn[q], R[(i * L + line) * NR + q]);
+    }
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      ok &= isfinite(dn[q]);
+      X[e * NR + q] += f2d_fast(dn[q]);
+    }
+  }
+  if (!ok) report_error(A.st, 5);
 }
 
 }  // namespace tdma

@@ -978,36 +978,25 @@ tdma_status_t autotune_impl(tdma_plan_s* p, const void* a, const void* b, const 
 }
 
 // TDMA_F64_REFINE: layout of the residual buffer R (compact when coefficients are broadcast).
-Layout refine64_layout(const tdma_desc_t& d) {
-  if (d.coef_broadcast) return Layout{d.n, d.n_lines, d.n_lines, std::max<int64_t>(1, d.n_lines), 1, 0};
-  return Layout{d.n, d.n_lines, d.elem_stride, d.inner_count, d.inner_stride, d.outer_stride};
-}
 size_t refine64_buffer_bytes(const tdma_desc_t& d) {
-  if (d.n_lines == 0) return 0;
-  const Layout L = refine64_layout(d);
-  const int64_t last = d.n_lines - 1;
-  const int64_t max_off = (last / L.ic) * L.os + std::min<int64_t>(last, L.ic - 1) * L.is + (L.n - 1) * L.es;
-  return (size_t)(max_off + 1) * d.nrhs * 8;
+  return (size_t)d.n * (size_t)d.n_lines * (1 + (size_t)d.nrhs) * sizeof(float);
 }
 
 cudaError_t solve_refine64(const tdma_plan_s* p, const Args& A, cudaStream_t s) {
   cudaError_t e = launch_forward(p, A, s);
   if (e != cudaSuccess) return e;
-  const Layout lr = refine64_layout(p->desc);
-  double* R = (double*)((unsigned char*)A.ws + p->r_offset);
+  // FP32 factors c' and forward right-hand sides of the corrections, [row][line]
+  float* cw = (float*)((unsigned char*)A.ws + p->r_offset);
+  float* rw = cw + A.lay.n * A.lay.n_lines;
+  const unsigned blocks = (unsigned)((A.lay.n_lines + 127) / 128);
   const int64_t total = A.lay.n * A.lay.n_lines;
-  const unsigned blocks = (unsigned)((total + 255) / 256);
+  const unsigned rblocks = (unsigned)((total + 255) / 256);
   for (int it = 0; it < p->refine64; ++it) {
-    if (p->desc.nrhs == 1) residual64_kernel<1><<<blocks, 256, 0, s>>>(A, lr, R);
-    else residual64_kernel<2><<<blocks, 256, 0, s>>>(A, lr, R);
+    if (p->desc.nrhs == 1) residual_exact_kernel<1><<<rblocks, 256, 0, s>>>(A, rw);
+    else residual_exact_kernel<2><<<rblocks, 256, 0, s>>>(A, rw);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    Args C = A;  // correction: solve A c = r in place in R
-    C.d = R;
-    C.x = R;
-    C.lay = lr;
-    if ((e = launch_forward(p, C, s)) != cudaSuccess) return e;
-    if (p->desc.nrhs == 1) update64_kernel<1><<<blocks, 256, 0, s>>>(A.lay, lr, (double*)A.x, R);
-    else update64_kernel<2><<<blocks, 256, 0, s>>>(A.lay, lr, (double*)A.x, R);
+    if (p->desc.nrhs == 1) correction32_kernel<1><<<blocks, 128, 0, s>>>(A, cw, rw);
+    else correction32_kernel<2><<<blocks, 128, 0, s>>>(A, cw, rw);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -62,7 +62,7 @@ def test_adi_512_cubed_sweeps_match_closed_form():
 def test_poisson_wavenumber_lines_1024_cubed(precision, tol):
     # Against the extended-precision oracle. Plain FP64 elimination is a few 1e-12 off on the
     # lowest modes (so is the FP64 CPU Thomas: 3e-12 on the pinned zero mode), hence its looser
-    # bound; one correction from a double-double residual meets 1e-12.
+    # bound; one correction from an exact residual (solved in FP32) meets 1e-12.
     n = 1024
     p = synth.poisson_lines(n, n, n, seed=2, device="cuda")
     d = p["d"]
