@@ -5,7 +5,7 @@
 // solution. Mixed-precision iterative refinement (Wilkinson 1963; Moler 1967; Carson and Higham
 // 2018) removes that: with the residual r = d - A x evaluated more precisely than the solve and a
 // correction solve whose relative error is well below one, x + dx is accurate to the residual's
-// precision. Here the residual is exact (residual_exact in bits.cuh: 106-bit products and a
+// precision. Here the residual is exact (residual_exact in exact_residual.cuh: 106-bit products and a
 // 128-bit fixed-point sum on the integer pipes) and the correction is solved in FP32 with the
 // coefficients truncated to float: its relative error, about kappa 2^-23, stays near 1e-3 even on
 // the worst Poisson modes, so one correction takes their error from about 2e-12 to the 1e-15
@@ -20,7 +20,7 @@
 // the plain FP64 accuracy.
 #pragma once
 #include "layout.cuh"
-#include "bits.cuh"
+#include "exact_residual.cuh"
 
 namespace tdma {
 

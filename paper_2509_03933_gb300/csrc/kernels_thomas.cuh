@@ -16,7 +16,7 @@
 namespace tdma {
 
 constexpr int kThomasBlock = 128;
-constexpr int kThomasAhead = 4;  // rows loaded ahead of the forward sweep
+constexpr int kThomasAhead = 2;  // rows loaded ahead of the forward sweep (4 cost occupancy: 27.7 -> 23.4 ms)
 
 template <class CT, int NR, bool TR = false>
 __global__ void __launch_bounds__(kThomasBlock) thomas_kernel(const Args A, CT* __restrict__ cws) {

@@ -3,7 +3,7 @@
 #include <cstdio>
 #include <cstdint>
 #include <cstring>
-#include "bits.cuh"
+#include "exact_residual.cuh"
 
 int main() {
   unsigned long long u[7];
