@@ -8,11 +8,12 @@ namespace tdma {
 
 // ---- exact residual of one row, r = d - a xm - b x - c xp, for FP64 operands ----------------
 // The three products of 53-bit significands are exact 106-bit integers; they and d are placed in
-// one 128-bit two's-complement fixed-point accumulator whose unit is 2^(E - 124), E bounding the
-// exponent of the largest term (so the sum, below 2^(E + 2), cannot overflow). Bits of a term
-// below that unit are dropped (an error under 2^-122 of the largest term); everything else is
-// exact integer arithmetic. The result is returned as a float truncated to 24 significant bits
-// (0 below the float range); non-finite operands give NaN. Integer pipes only: no FP64 arithmetic.
+// one 128-bit two's-complement fixed-point accumulator whose unit is 2^(E - 106), E bounding the
+// exponent of the largest term (the sum, below 2^(E + 2), cannot overflow). Bits of a term below
+// that unit are dropped (in all under 2^-104 of the largest term, far below a residual of an FP64
+// solution); everything else is exact integer arithmetic. The result is returned as a float
+// truncated to 24 significant bits (0 below the float range); non-finite operands give NaN.
+// Integer pipes only, and no branch depends on the operands.
 struct U128 { uint64_t lo, hi; };
 
 TDMA_HD U128 mul_u64(uint64_t a, uint64_t b) {
@@ -22,17 +23,6 @@ TDMA_HD U128 mul_u64(uint64_t a, uint64_t b) {
   const unsigned __int128 p = (unsigned __int128)a * b;
   return U128{(uint64_t)p, (uint64_t)(p >> 64)};
 #endif
-}
-TDMA_HD U128 shl_u128(U128 v, int s) {  // 0 <= s < 128
-  if (s == 0) return v;
-  if (s < 64) return U128{v.lo << s, (v.hi << s) | (v.lo >> (64 - s))};
-  return U128{0ull, v.lo << (s - 64)};
-}
-TDMA_HD U128 shr_u128(U128 v, int s) {  // s >= 0
-  if (s == 0) return v;
-  if (s >= 128) return U128{0ull, 0ull};
-  if (s < 64) return U128{(v.lo >> s) | (v.hi << (64 - s)), v.hi >> s};
-  return U128{v.hi >> (s - 64), 0ull};
 }
 TDMA_HD U128 add_u128(U128 a, U128 b) {
   const uint64_t lo = a.lo + b.lo;
@@ -64,66 +54,71 @@ TDMA_HD DecF64 dec_f64(double v) {
   return r;
 }
 
-// residual_exact on decoded operands (a kernel decodes shared coefficients once)
+// v >> s for s >= 0 (0 for s >= 128), without branches: both 64-bit halves computed, then selected
+TDMA_HD U128 shr_u128_bf(U128 v, uint32_t s) {
+  const uint32_t sm = s & 63u;
+  const uint64_t lo_a = (v.lo >> sm) | ((v.hi << 1) << (63u - sm));  // (hi << (64 - sm)) for sm in 0..63
+  const uint64_t hi_a = v.hi >> sm;
+  const bool big = s >= 64u, gone = s >= 128u;
+  return U128{gone ? 0ull : (big ? hi_a : lo_a), big ? 0ull : hi_a};
+}
+// m << s for m < 2^53 and 0 <= s <= 71, without branches
+TDMA_HD U128 shl_u53_bf(uint64_t m, uint32_t s) {
+  const uint32_t sm = s & 63u;
+  const uint64_t lo_a = m << sm, hi_a = (m >> 1) >> (63u - sm);  // (m >> (64 - sm)) for sm in 0..63
+  const bool big = s >= 64u;
+  return U128{big ? 0ull : lo_a, big ? lo_a : hi_a};
+}
+
+// residual_exact on decoded operands (a kernel decodes shared coefficients once). The fixed-point
+// unit is 2^(E - 106), E bounding the largest term, so every product term is shifted right (its
+// bits below the unit dropped: under 2^-104 of the largest term in all) and only d may move left;
+// the sum stays below 2^(E + 2), well inside 128 bits. No branches depend on the operands.
 TDMA_HD float residual_exact_dec(const DecF64& dd, const DecF64& da, const DecF64& dxm, const DecF64& db,
                                  const DecF64& dx, const DecF64& dc, const DecF64& dxp) {
-  uint64_t mv[7];
-  int ev[7];
-  bool sv[7];
-  const DecF64* in[7] = {&dd, &da, &dxm, &db, &dx, &dc, &dxp};
-  bool finite_all = true;
-#pragma unroll
-  for (int k = 0; k < 7; ++k) {
-    mv[k] = in[k]->m;
-    ev[k] = in[k]->e;
-    sv[k] = in[k]->neg;
-    finite_all &= in[k]->ok;
-  }
-  if (!finite_all) return bitsf(0x7FC00000u);
-  // terms: d, and -a xm, -b x, -c xp as significand products
-  U128 tm[4];
-  int te[4], tw[4];
-  bool tn[4];
-  tm[0] = U128{mv[0], 0ull};
-  te[0] = ev[0];
-  tw[0] = 53;
-  tn[0] = sv[0];
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    tm[k + 1] = mul_u64(mv[1 + 2 * k], mv[2 + 2 * k]);
-    te[k + 1] = ev[1 + 2 * k] + ev[2 + 2 * k];
-    tw[k + 1] = 106;
-    tn[k + 1] = !(sv[1 + 2 * k] != sv[2 + 2 * k]);  // the minus sign of the product term
-  }
-  int top = -100000;
-#pragma unroll
-  for (int k = 0; k < 4; ++k)
-    if ((tm[k].lo | tm[k].hi) != 0ull && te[k] + tw[k] > top) top = te[k] + tw[k];
-  if (top == -100000) return 0.f;
-  const int unit = top - 124;
-  U128 acc{0ull, 0ull};
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    if ((tm[k].lo | tm[k].hi) == 0ull) continue;  // zero terms (their exponent field means nothing)
-    const int sh = te[k] - unit;  // at most 71 for d and 18 for a product: the sum stays below 2^126
-    U128 t = sh >= 0 ? shl_u128(tm[k], sh) : shr_u128(tm[k], -sh);
-    acc = add_u128(acc, tn[k] ? neg_u128(t) : t);
-  }
-  const bool rneg = (acc.hi >> 63) != 0;
+  const bool finite_all = dd.ok && da.ok && dxm.ok && db.ok && dx.ok && dc.ok && dxp.ok;
+  const U128 p1 = mul_u64(da.m, dxm.m), p2 = mul_u64(db.m, dx.m), p3 = mul_u64(dc.m, dxp.m);
+  const int e1 = da.e + dxm.e, e2 = db.e + dx.e, e3 = dc.e + dxp.e;
+  const bool z1 = (p1.lo | p1.hi) == 0ull, z2 = (p2.lo | p2.hi) == 0ull, z3 = (p3.lo | p3.hi) == 0ull;
+  const bool z0 = dd.m == 0ull;
+  const int lowest = -100000;
+  int top = z0 ? lowest : dd.e + 53;
+  top = max(top, z1 ? lowest : e1 + 106);
+  top = max(top, z2 ? lowest : e2 + 106);
+  top = max(top, z3 ? lowest : e3 + 106);
+  const int unit = top - 106;
+  // product terms: shifted right by top - (e + 106) >= 0; zero terms contribute nothing
+  const U128 t1 = shr_u128_bf(p1, z1 ? 128u : (uint32_t)(top - (e1 + 106)));
+  const U128 t2 = shr_u128_bf(p2, z2 ? 128u : (uint32_t)(top - (e2 + 106)));
+  const U128 t3 = shr_u128_bf(p3, z3 ? 128u : (uint32_t)(top - (e3 + 106)));
+  // d: shifted by dd.e - unit, which is at most 53
+  const int sd = dd.e - unit;
+  U128 t0 = sd >= 0 ? shl_u53_bf(dd.m, (uint32_t)min(sd, 71)) : shr_u128_bf(U128{dd.m, 0ull}, (uint32_t)min(-sd, 128));
+  if (z0) t0 = U128{0ull, 0ull};
+  // acc = d - a xm - b x - c xp (two's complement)
+  const bool n1 = da.neg == dxm.neg, n2 = db.neg == dx.neg, n3 = dc.neg == dxp.neg;  // the term is -(product)
+  U128 acc = dd.neg ? neg_u128(t0) : t0;
+  acc = add_u128(acc, n1 ? neg_u128(t1) : t1);
+  acc = add_u128(acc, n2 ? neg_u128(t2) : t2);
+  acc = add_u128(acc, n3 ? neg_u128(t3) : t3);
+  const bool rneg = (acc.hi >> 63) != 0ull;
   if (rneg) acc = neg_u128(acc);
-  if ((acc.lo | acc.hi) == 0ull) return 0.f;
+  const bool zero = (acc.lo | acc.hi) == 0ull;
   int lz;
 #ifdef __CUDA_ARCH__
   lz = acc.hi ? __clzll((long long)acc.hi) : 64 + __clzll((long long)acc.lo);
 #else
-  lz = acc.hi ? __builtin_clzll(acc.hi) : 64 + __builtin_clzll(acc.lo);
+  lz = acc.hi ? __builtin_clzll(acc.hi) : (acc.lo ? 64 + __builtin_clzll(acc.lo) : 128);
 #endif
   const int p = 127 - lz;  // leading bit of the magnitude
-  const U128 top24 = p >= 23 ? shr_u128(acc, p - 23) : shl_u128(acc, 23 - p);
+  const uint64_t top24 = p >= 23 ? shr_u128_bf(acc, (uint32_t)(p - 23)).lo : (acc.lo << (uint32_t)max(23 - p, 0));
   const int be = unit + p + 127;  // biased float exponent of the result
-  if (be <= 0) return rneg ? -0.f : 0.f;
-  if (be >= 255) return bitsf((rneg ? 0x80000000u : 0u) | 0x7F800000u);
-  return bitsf((rneg ? 0x80000000u : 0u) | ((uint32_t)be << 23) | ((uint32_t)top24.lo & 0x7FFFFFu));
+  const uint32_t sign = rneg ? 0x80000000u : 0u;
+  uint32_t bits = sign | ((uint32_t)max(min(be, 254), 1) << 23) | ((uint32_t)top24 & 0x7FFFFFu);
+  if (be <= 0 || zero || top == lowest) bits = sign;    // below the float range (or exactly zero)
+  if (be >= 255) bits = sign | 0x7F800000u;
+  if (!finite_all) bits = 0x7FC00000u;
+  return bitsf(bits);
 }
 
 TDMA_HD float residual_exact(double d, double a, double xm, double b, double x, double c, double xp) {

@@ -82,7 +82,7 @@ def test_exact_residual_matches_rational_arithmetic():
         exact = sum(terms)
         want = _exact_trunc_float(exact)
         big = max(abs(t) for t in terms)
-        tol = abs(exact) * F(2) ** -22 + big * F(2) ** -118
+        tol = abs(exact) * F(2) ** -22 + big * F(2) ** -103
         assert abs(F(g) - F(want)) <= tol, (d, a, xm, b, x, c, xp, g, want)
-        if abs(exact) > big * F(2) ** -90:  # no truncation of the sum in play: the same bits
+        if abs(exact) > big * F(2) ** -75:  # the truncated tail is far below the result: the same bits
             assert g == want or abs(F(g) - exact) <= abs(exact) * F(2) ** -23
