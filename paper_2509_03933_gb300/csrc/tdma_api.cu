@@ -21,6 +21,7 @@
 #include "kernels_thomas.cuh"
 #include "kernels_ragged.cuh"
 #include "kernels_packed.cuh"
+#include "kernels_shared.cuh"
 #include "kernels_backward.cuh"
 #include "kernels_refine64.cuh"
 
@@ -139,7 +140,25 @@ bool refine_reg_config(const tdma_desc_t& d, int P_req, tdma_config_t& c) {
 // Thomas (P = 1, factors in the workspace) fills the GPU when there are enough lines.
 bool prefer_thomas(const tdma_desc_t& d) { return d.n > 1 && d.n_lines >= 65536; }
 
+// Lines sharing one set of coefficients (broadcast, no per-line shift) in FP64 or F32, one
+// partition: the factorisation is done once for all lines.
+bool shared_eligible(const tdma_desc_t& d) {
+  if (const char* e = std::getenv("TDMA_DISABLE_SHARED")) if (e[0] == '1') return false;
+  return d.n > 0 && d.coef_broadcast && !d.diag_shift && (d.precision == TDMA_F64 || d.precision == TDMA_F32) &&
+         d.partitions <= 1;
+}
+void shared_config(const tdma_desc_t& d, tdma_config_t& c) {
+  c = tdma_config_t{};
+  c.partitions = 1;
+  c.rows_per_thread = (int32_t)d.n;
+  c.lines_per_block = 128;
+  c.threads_per_block = 128;
+  c.blocks = (int32_t)((d.n_lines + 127) / 128);
+  c.variant = TDMA_VARIANT_SHARED;
+}
+
 size_t workspace_for(const tdma_desc_t& d, const tdma_config_t& c) {
+  if (c.variant == TDMA_VARIANT_SHARED) return (size_t)2 * d.n * (d.precision == TDMA_F64 ? 8 : 4);
   if (c.variant == TDMA_VARIANT_THOMAS) return thomas_workspace(d);
   if (c.variant == TDMA_VARIANT_DC_GLOBAL)
     return (size_t)c.blocks * c.threads_per_block * (size_t)std::max(0, c.rows_per_thread - 2) * (2 + d.nrhs) *
@@ -487,6 +506,8 @@ cudaError_t launch_forward(const tdma_plan_s* p, const Args& A, cudaStream_t s) 
     }
     case TDMA_VARIANT_THOMAS:
       return launch_thomas(p->desc.precision, p->desc.nrhs, A, c, s);
+    case TDMA_VARIANT_SHARED:
+      return launch_shared_any(p->desc.precision, p->desc.nrhs, false, A, s);
     case TDMA_VARIANT_PACKED: {
       // the per-line maxima start from zero (the kernel also leaves them zero)
       cudaError_t e = cudaMemsetAsync(p->pk.norms, 0, sizeof(uint32_t) * kPackNormWords * (size_t)p->desc.n_lines, s);
@@ -569,6 +590,7 @@ template <class CT, int NR>
 cudaError_t adjoint_solve(const tdma_plan_s* p, const Args& A, cudaStream_t s) {
   const tdma_config_t& c = p->cfg;
   const dim3 grid(c.blocks), block(c.threads_per_block);
+  if (c.variant == TDMA_VARIANT_SHARED) return launch_shared<CT, NR, true>(A, s);
   if (c.variant == TDMA_VARIANT_THOMAS) {
     thomas_kernel<CT, NR, true><<<grid, block, 0, s>>>(A, (CT*)A.ws);
     return cudaGetLastError();
@@ -864,6 +886,10 @@ std::vector<tdma_config_t> tune_candidates(const tdma_desc_t& d, bool allow_tma)
       if (P <= 64 && choose_block(d, P, r)) out.push_back(r);
     }
   } else {
+    if (use_thomas_variant(d) && shared_eligible(d)) {
+      shared_config(d, c);
+      out.push_back(c);
+    }
     if (use_thomas_variant(d)) {
       thomas_config(d, c);
       out.push_back(c);
@@ -1051,7 +1077,8 @@ tdma_status_t tdma_plan_create(tdma_plan_t* plan, const tdma_desc_t* desc, size_
       if (!ok) ok = choose_block(*desc, desc->partitions > 0 ? desc->partitions : default_partitions(*desc), c);
     } else if (use_thomas_variant(*desc) &&
                (desc->partitions == 1 || (desc->partitions == 0 && prefer_thomas(*desc)))) {
-      thomas_config(*desc, c);
+      if (shared_eligible(*desc)) shared_config(*desc, c);  // one factorisation for all lines
+      else thomas_config(*desc, c);
       ok = true;
     } else {
       ok = choose_block(*desc, desc->partitions > 0 ? desc->partitions : default_partitions(*desc), c);
