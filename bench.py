@@ -41,7 +41,8 @@ BYTES_F64 = 40.0    # a, b, c, d double in, x double out
 FP64_OPS_PEAK = 152 * 2 * 2.07e9  # FP64 pipe: 152 SMs x 2 ops/clk x 2.07 GHz (1.25 TFLOP/s, FMA = 2)
 KERNEL_OF_VARIANT = {0: "dc_kernel", 1: "thomas_kernel", 2: "refine_kernel", 3: "ragged_refine_kernel",
                      4: "refine_reg_kernel", 5: "refine_tma_fixed_kernel", 6: "refine_cluster_kernel",
-                     7: "dc_kernel", 8: "refine_tree_kernel", 9: "packed_refine_kernel"}
+                     7: "dc_kernel", 8: "refine_tree_kernel", 9: "packed_refine_kernel",
+                     10: "shared_stream_kernel"}
 
 
 def dist_env():
@@ -148,7 +149,7 @@ KERNEL_SOURCE = {"dc_kernel": "kernels_dc.cuh", "thomas_kernel": "kernels_thomas
                  "refine_kernel": "kernels_refine.cuh", "ragged_refine_kernel": "kernels_ragged.cuh",
                  "refine_reg_kernel": "kernels_refine_reg.cuh", "refine_tma_fixed_kernel": "kernels_refine_tma.cuh",
                  "refine_cluster_kernel": "kernels_refine_cluster.cuh", "refine_tree_kernel": "kernels_refine_tree.cuh",
-                 "packed_refine_kernel": "kernels_packed.cuh"}
+                 "packed_refine_kernel": "kernels_packed.cuh", "shared_stream_kernel": "kernels_shared.cuh"}
 
 
 def source_sha(kernel: str) -> str:
@@ -265,33 +266,49 @@ def suite_small_grid(stream, hbm_peak, flush):
     return out
 
 
-def suite_adi(stream, hbm_peak):
-    """512^3 ADI viscous sweeps x -> y -> z, 8 partitions per line, one CUDA graph per step."""
+def suite_adi(stream, hbm_peak, n=512):
+    """512^3 ADI viscous sweeps x -> y -> z, one CUDA graph per step: per-element coefficients
+    with 8 partitions per line, and the same operator as 1D coefficients shared by all lines
+    (one factorisation per sweep, per-line right-hand-side recurrences)."""
     import oracle
     import synth
     import paper_2509_03933_gb300 as tdma
     from scipy.fft import dstn, idstn
-    n, r = 512, 0.5
+    r = 0.5
     g = synth.grid_adi((n, n, n), seed=1, r=r, device="cuda")
     a, b, c, d = g["a"], g["b"], g["c"], g["d"]
-    u = d.clone()
-    plans = [tdma.Plan(*tdma.line_layout(u, ax), partitions=8) for ax in (2, 1, 0)]
-    graph = tdma.sweep_graph([(p, (a, b, c, u, u)) for p in plans])
-    per_axis = {}
-    for name, p in zip("xyz", plans):
-        per_axis[name] = _timed(lambda: p.solve(a, b, c, u, u), 10, 3, stream)
-    ms = _timed(graph.replay, 10, 3, stream)
-    u.copy_(d)
-    graph.replay()
-    torch.cuda.synchronize()
     lam = 1 + 4 * r * np.sin(np.pi * np.arange(1, n + 1) / (2 * (n + 1))) ** 2
     L = lam[:, None, None] * lam[None, :, None] * lam[None, None, :]
     ref = idstn(dstn(d.cpu().numpy(), type=1, workers=-1) / L, type=1, workers=-1)
     U = 3 * n ** 3
-    return {"ms_per_xyz_step": ms, "ms_per_sweep": per_axis, "unknowns_per_s": U / (ms * 1e-3),
-            "hbm_frac": BYTES_F64 * U / (ms * 1e-3) / 1e9 / hbm_peak,
-            "rel_l2_error_vs_closed_form": oracle.rel_l2(u.cpu().numpy(), ref),
-            "plans": [p.config for p in plans], "launches_per_step": 3}
+    u = d.clone()
+    out = {}
+    one = lambda v: torch.full((n,), v, dtype=torch.float64, device="cuda")
+    legs = (("per_element_P8", (a, b, c), dict(partitions=8)),
+            ("shared_coefficients", (one(-r), one(1 + 2 * r), one(-r)), dict(coef_broadcast=True)))
+    for name, coef, kw in legs:
+        plans = [tdma.Plan(*tdma.line_layout(u, ax), **kw) for ax in (2, 1, 0)]
+        graph = tdma.sweep_graph([(p, coef + (u, u)) for p in plans])
+        per_axis = {ax: _timed(lambda: p.solve(*coef, u, u), 10, 3, stream) for ax, p in zip("xyz", plans)}
+        ms = _timed(graph.replay, 10, 3, stream)
+        u.copy_(d)
+        graph.replay()
+        torch.cuda.synchronize()
+        leg = {"ms_per_xyz_step": ms, "ms_per_sweep": per_axis, "unknowns_per_s": U / (ms * 1e-3),
+               "hbm_frac": BYTES_F64 * U / (ms * 1e-3) / 1e9 / hbm_peak,
+               "rel_l2_error_vs_closed_form": oracle.rel_l2(u.cpu().numpy(), ref),
+               "plans": [p.config for p in plans]}
+        if kw.get("coef_broadcast"):
+            # d in, x out (16 B per unknown); 3 FP64-pipe operations per unknown
+            leg["launches_per_step"] = 6
+            leg["hbm_frac"] = 16.0 * U / (ms * 1e-3) / 1e9 / hbm_peak
+            leg["fp64_pipe_frac"] = 3.0 * U / (ms * 1e-3) / FP64_OPS_PEAK
+            leg["bytes_per_unknown"] = 16.0
+        else:
+            leg["launches_per_step"] = 3
+        out[name] = leg
+        del graph, plans
+    return out
 
 
 def suite_poisson(stream, hbm_peak):
@@ -434,6 +451,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-suite", action="store_true", help="skip the other workloads")
+    ap.add_argument("--only-adi", type=int, default=0, metavar="N",
+                    help="run only the ADI workload on an N^3 grid and print it (profiling runs)")
     ap.add_argument("--only-ragged", type=int, default=0, metavar="LINES",
                     help="run only the ragged workload with LINES lines (profiling runs) and print it")
     args = ap.parse_args()
@@ -441,6 +460,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_adi > 0:
+        hbm_peak, _ = peaks()
+        print(json.dumps({"adi": suite_adi(torch.cuda.current_stream(), hbm_peak, args.only_adi)}), flush=True)
+        return 0
     if args.only_ragged > 0:
         hbm_peak, _ = peaks()
         print(json.dumps({"ragged": suite_ragged(torch.cuda.current_stream(), hbm_peak, args.only_ragged)}), flush=True)
@@ -555,7 +578,7 @@ def main():
         flushbuf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
         suite = {}
         for name, fn in (("grid64_z_f64", lambda: suite_small_grid(stream, hbm_peak, lambda: _flush_l2(flushbuf))),
-                         ("adi512_xyz_f64_P8", lambda: suite_adi(stream, hbm_peak)),
+                         ("adi512_xyz_f64", lambda: suite_adi(stream, hbm_peak)),
                          ("poisson1024_z_complex", lambda: suite_poisson(stream, hbm_peak)),
                          ("ragged20000", lambda: suite_ragged(stream, hbm_peak))):
             try:

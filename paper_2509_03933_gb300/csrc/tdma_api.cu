@@ -158,7 +158,8 @@ void shared_config(const tdma_desc_t& d, tdma_config_t& c) {
 }
 
 size_t workspace_for(const tdma_desc_t& d, const tdma_config_t& c) {
-  if (c.variant == TDMA_VARIANT_SHARED) return (size_t)2 * d.n * (d.precision == TDMA_F64 ? 8 : 4);
+  if (c.variant == TDMA_VARIANT_SHARED)
+    return d.precision == TDMA_F64 ? shared_workspace_bytes<double>(d.n) : shared_workspace_bytes<float>(d.n);
   if (c.variant == TDMA_VARIANT_THOMAS) return thomas_workspace(d);
   if (c.variant == TDMA_VARIANT_DC_GLOBAL)
     return (size_t)c.blocks * c.threads_per_block * (size_t)std::max(0, c.rows_per_thread - 2) * (2 + d.nrhs) *
@@ -576,6 +577,8 @@ cudaError_t prepare_kernel(const tdma_plan_s* p) {
     }
     case TDMA_VARIANT_THOMAS:
       return prepare_thomas(p->desc.precision, p->desc.nrhs, sm);
+    case TDMA_VARIANT_SHARED:
+      return prepare_shared(p->desc.precision, p->desc.nrhs);
     case TDMA_VARIANT_RAGGED:
       return cudaSuccess;
     case TDMA_VARIANT_PACKED:

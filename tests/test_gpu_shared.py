@@ -70,6 +70,26 @@ def test_shared_matches_oracle_every_axis(precision, nrhs, axis):
     assert O.rel_l2(_lines(x, axis, nrhs), _oracle(a, b, c, d, axis, nrhs)) <= TOL[precision]
 
 
+@pytest.mark.parametrize("shape,nrhs", [((5, 7, 45), 1), ((5, 7, 45), 2), ((3, 11, 2), 1), ((1, 9, 1000), 2),
+                                         ((2, 1, 33), 1), ((64, 33, 31), 2)])
+def test_shared_unit_stride_ragged_chunks_and_partial_warps(shape, nrhs):
+    # lines along the contiguous axis go through shared memory in chunks of 32 values per line,
+    # one warp per 32 lines: line counts that leave a warp partly empty and lengths whose last
+    # chunk is partial
+    n = shape[2]
+    a, b, c = _coefficients(n, 80 + n)
+    d = _rhs(shape, 81, torch.float64, nrhs)
+    plan = _plan(d, 2, "f64", nrhs)
+    assert plan.config["variant"] == SHARED
+    x = torch.empty_like(d)
+    plan.solve(a, b, c, d, x)
+    assert plan.last_error()[0] == 0
+    ref = _oracle(a, b, c, d, 2, nrhs)
+    assert O.rel_l2(_lines(x, 2, nrhs), ref) <= 1e-12
+    plan.solve(a, b, c, d, d)  # x over d
+    assert O.rel_l2(_lines(d, 2, nrhs), ref) <= 1e-12
+
+
 @pytest.mark.parametrize("n", [2, 3, 5, 1000])
 def test_shared_short_and_long_lines(n):
     a, b, c = _coefficients(n, 30 + n)
