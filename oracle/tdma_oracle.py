@@ -21,6 +21,14 @@ Functions and the passage each follows:
                      (Section 2.1 stages 1-5; Algorithm 1: solve the decoupled system
                      A~ x~ = d~, solve the reduced system Z y = E^T x~ of size 2p - 2
                      (Section 2.2), correct x = x~ - Y y).
+  pdd             -- the parallel diagonally dominant (PDD) approximation the paper's
+                     momentum solver uses for its diagonally dominant ADI lines (Section 5.1,
+                     Section 6.2.2; Sun's method): Stage A as in dc_spike, then one 2x2 system
+                     per interface that keeps only the couplings between the two end unknowns
+                     of the interface, then the correction of dc_spike. PARITY UNPINNED beyond
+                     the exact cases and invariants its tests check (p = 1, decoupled
+                     partitions, zero residual off the partition boundaries, geometric decay
+                     of the error with the partition length); the paper gives no worked values.
   residual        -- r = d - A x.
   adjoint_grads   -- gradients of a scalar loss through x = A^{-1} d: lambda = A^{-T} g,
                      grad_d = lambda, grad_b = -lambda*x, grad_a_i = -lambda_i x_{i-1},
@@ -32,7 +40,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["thomas", "thomas_ext", "dense_matrix", "dense_solve", "partition_rows", "dc_spike",
+__all__ = ["thomas", "thomas_ext", "dense_matrix", "dense_solve", "partition_rows", "dc_spike", "pdd",
            "residual", "adjoint_grads", "transpose_coefficients", "thomas_ragged", "rel_l2"]
 
 
@@ -198,6 +206,62 @@ def dc_spike(a, b, c, d, p: int):
                 x[:, s:e] -= v[:, s:e] * y[:, 2 * (k - 1)][:, None]
             if k < p - 1:
                 x[:, s:e] -= w[:, s:e] * y[:, 2 * (k + 1) - 1][:, None]
+    return x[0] if squeeze else x
+
+
+def pdd(a, b, c, d, p: int):
+    """Parallel diagonally dominant approximation (Section 5.1 and Section 6.2.2 name it for the
+    diagonally dominant momentum systems; the steps are Sun's PDD method).
+
+    Stage A, as in dc_spike: per partition k = [s, e], with its outer couplings a_s and c_e
+    removed, x~ = A_k^{-1} d, v = A_k^{-1}(a_s e_first) (k > 0), w = A_k^{-1}(c_e e_last)
+    (k < p-1), so that inside the partition x_i = x~_i - v_i x_{s-1} - w_i x_{e+1} exactly.
+    Reduced step: at the interface between partitions k and k+1 (rows e_k and s_{k+1}) the exact
+    relations of its two unknowns are
+        x_{e_k} + v_{e_k} x_{e_{k-1}} + w_{e_k} x_{s_{k+1}} = x~_{e_k},
+        x_{s_{k+1}} + v_{s_{k+1}} x_{e_k} + w_{s_{k+1}} x_{s_{k+2}} = x~_{s_{k+1}}.
+    PDD drops v_{e_k} (the left coupling seen at the far end of partition k) and w_{s_{k+1}} (the
+    right coupling seen at the far end of partition k+1), which leaves the 2x2 system
+        [1, w_{e_k}; v_{s_{k+1}}, 1] [y1; y2] = [x~_{e_k}; x~_{s_{k+1}}]
+    for y1 ~ x_{e_k}, y2 ~ x_{s_{k+1}}, solved by Cramer's rule.
+    Correction: x = x~ - v y1(left interface) - w y2(right interface) in every partition.
+    p = 1 is the Thomas solve. Works on (lines, n) arrays; returns x with the shape of d.
+    """
+    a, b, c, d = (np.atleast_2d(np.asarray(t, dtype=np.float64)) for t in (a, b, c, d))
+    squeeze = np.asarray(b).ndim == 1
+    L, n = b.shape
+    parts = partition_rows(n, p)
+    xt = np.zeros((L, n))
+    v = np.zeros((L, n))
+    w = np.zeros((L, n))
+    for k, (s, e) in enumerate(parts):  # Stage A
+        ak, bk, ck = a[:, s:e].copy(), b[:, s:e], c[:, s:e].copy()
+        ak[:, 0] = 0.0
+        ck[:, -1] = 0.0
+        xt[:, s:e] = thomas(ak, bk, ck, d[:, s:e])
+        if k > 0:
+            rhs = np.zeros((L, e - s))
+            rhs[:, 0] = a[:, s]
+            v[:, s:e] = thomas(ak, bk, ck, rhs)
+        if k < p - 1:
+            rhs = np.zeros((L, e - s))
+            rhs[:, -1] = c[:, e - 1]
+            w[:, s:e] = thomas(ak, bk, ck, rhs)
+    y1 = np.zeros((L, p))  # y1[:, k]: x_{e_k} at interface k (k = 0..p-2)
+    y2 = np.zeros((L, p))  # y2[:, k]: x_{s_{k+1}}
+    for k in range(p - 1):
+        eL = parts[k][1] - 1
+        sR = parts[k + 1][0]
+        wl, vr = w[:, eL], v[:, sR]
+        det = 1.0 - wl * vr
+        y1[:, k] = (xt[:, eL] - wl * xt[:, sR]) / det
+        y2[:, k] = (xt[:, sR] - vr * xt[:, eL]) / det
+    x = xt.copy()
+    for k, (s, e) in enumerate(parts):  # correction with the neighbours' interface values
+        if k > 0:
+            x[:, s:e] -= v[:, s:e] * y1[:, k - 1][:, None]
+        if k < p - 1:
+            x[:, s:e] -= w[:, s:e] * y2[:, k][:, None]
     return x[0] if squeeze else x
 
 
