@@ -25,10 +25,10 @@ Functions and the passage each follows:
                      momentum solver uses for its diagonally dominant ADI lines (Section 5.1,
                      Section 6.2.2; Sun's method): Stage A as in dc_spike, then one 2x2 system
                      per interface that keeps only the couplings between the two end unknowns
-                     of the interface, then the correction of dc_spike. PARITY UNPINNED beyond
-                     the exact cases and invariants its tests check (p = 1, decoupled
-                     partitions, zero residual off the partition boundaries, geometric decay
-                     of the error with the partition length); the paper gives no worked values.
+                     of the interface, then the correction of dc_spike. The paper prints no
+                     PDD values; it is pinned by the cases the method fixes (p = 1 and
+                     decoupled partitions are exact, rows off the partition boundaries hold
+                     exactly, the error falls geometrically with the partition length).
   residual        -- r = d - A x.
   adjoint_grads   -- gradients of a scalar loss through x = A^{-1} d: lambda = A^{-T} g,
                      grad_d = lambda, grad_b = -lambda*x, grad_a_i = -lambda_i x_{i-1},
