@@ -308,6 +308,23 @@ def suite_adi(stream, hbm_peak, n=512):
             leg["launches_per_step"] = 3
         out[name] = leg
         del graph, plans
+    # the parallel diagonally dominant approximation against the exact reduced solve, per
+    # partition count: time of an xyz step and error against the closed form
+    sweep = {}
+    for P in (8, 32, 64, 128):
+        row = {}
+        for tag, pdd in (("exact", False), ("pdd", True)):
+            plans = [tdma.Plan(*tdma.line_layout(u, ax), partitions=P, pdd=pdd) for ax in (2, 1, 0)]
+            graph = tdma.sweep_graph([(p, (a, b, c, u, u)) for p in plans])
+            ms = _timed(graph.replay, 10, 3, stream)
+            u.copy_(d)
+            graph.replay()
+            torch.cuda.synchronize()
+            row[tag] = {"ms_per_xyz_step": ms, "rel_l2_error_vs_closed_form": oracle.rel_l2(u.cpu().numpy(), ref),
+                        "variant": plans[0].config["variant"]}
+            del graph, plans
+        sweep[f"P{P}"] = row
+    out["pdd_vs_exact_per_element"] = sweep
     return out
 
 

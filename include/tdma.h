@@ -49,6 +49,19 @@
  *                    workspace holds the FP32 correction's factors (4 (1 + nrhs) bytes per
  *                    unknown).
  *
+ * Approximate reduced solve (`pdd` = 1)
+ *   The parallel diagonally dominant (PDD) method the paper's momentum solver applies to its
+ *   diagonally dominant ADI systems (Section 5.1; Section 6.2.2). Each partition k of m rows is
+ *   solved on its own, x_k = xt_k - v_k x_{k-1,m-1} - w_k x_{k+1,0} (xt: the partition's solution
+ *   without its outer couplings; v, w: its responses to the couplings a_{k,0} and c_{k,m-1});
+ *   at every interface between partitions k and k+1 the two end unknowns then follow from a 2x2
+ *   system that drops the couplings v_k(m-1) x_{k-1,m-1} and w_{k+1}(0) x_{k+2,0}, which decay
+ *   geometrically with m on diagonally dominant lines; finally every partition is updated with
+ *   its neighbours' interface values. Exact for P = 1; otherwise an approximation whose error
+ *   the caller accepts. Uniform lines, TDMA_F64 or TDMA_F32, partitions >= 1 given explicitly;
+ *   no backward pass (tdma_solve_backward returns TDMA_ERR_UNSUPPORTED), autotune keeps the
+ *   configuration.
+ *
  * Errors
  *   Every call validates its arguments synchronously and returns a status; nothing aborts.
  *   Numerical faults found on the device (a zero or non-finite pivot, refinement that did
@@ -98,6 +111,7 @@ typedef struct {
   int32_t partitions;    /* P partitions per line; 0 = choose automatically                   */
   int32_t max_refine_iters; /* TDMA_F32_REFINE: correction steps at most (0 = default 4)     */
   double refine_tol;     /* TDMA_F32_REFINE: target relative error per line (<= 0: 2.5e-13) */
+  int32_t pdd;           /* 0: exact; 1: parallel diagonally dominant approximation, see below */
 } tdma_desc_t;
 
 /* Launch configuration a plan has settled on (reported for benchmarks and tests). */

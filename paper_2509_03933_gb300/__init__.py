@@ -39,7 +39,7 @@ class Desc(ctypes.Structure):
                 ("ragged_lengths", ctypes.c_void_p), ("ragged_max_n", ctypes.c_int64),
                 ("ragged_total", ctypes.c_int64), ("nrhs", ctypes.c_int32), ("coef_broadcast", ctypes.c_int32),
                 ("diag_shift", ctypes.c_void_p), ("precision", ctypes.c_int32), ("partitions", ctypes.c_int32),
-                ("max_refine_iters", ctypes.c_int32), ("refine_tol", ctypes.c_double)]
+                ("max_refine_iters", ctypes.c_int32), ("refine_tol", ctypes.c_double), ("pdd", ctypes.c_int32)]
 
 
 class Config(ctypes.Structure):
@@ -155,7 +155,7 @@ class Plan:
     def __init__(self, n, n_lines, elem_stride=1, inner_count=None, inner_stride=None, outer_stride=0,
                  precision="f64", partitions=0, nrhs=1, coef_broadcast=False, diag_shift=None,
                  ragged_offsets=None, ragged_lengths=None, ragged_max_n=0, ragged_total=0,
-                 max_refine_iters=0, refine_tol=0.0):
+                 max_refine_iters=0, refine_tol=0.0, pdd=False):
         self._lib = load_library()
         if inner_count is None:
             inner_count = max(1, n_lines)
@@ -168,7 +168,7 @@ class Plan:
                          ragged_max_n=ragged_max_n, ragged_total=ragged_total, nrhs=nrhs,
                          coef_broadcast=int(bool(coef_broadcast)), diag_shift=_ptr(diag_shift),
                          precision=_PREC[precision], partitions=partitions,
-                         max_refine_iters=max_refine_iters, refine_tol=refine_tol)
+                         max_refine_iters=max_refine_iters, refine_tol=refine_tol, pdd=int(bool(pdd)))
         self._h = ctypes.c_void_p()
         ws = ctypes.c_size_t(0)
         st = self._lib.tdma_plan_create(ctypes.byref(self._h), ctypes.byref(self.desc), ctypes.byref(ws))
@@ -309,26 +309,28 @@ def _check_same_layout(ref, *ts):
 _PLAN_CACHE = {}
 
 
-def _plan_for(d, axis, precision, partitions, nrhs, coef_broadcast, diag_shift, max_refine_iters, refine_tol):
+def _plan_for(d, axis, precision, partitions, nrhs, coef_broadcast, diag_shift, max_refine_iters, refine_tol,
+              pdd=False):
     lay = line_layout(d, axis, nrhs)
     key = (lay, precision, partitions, nrhs, coef_broadcast,
-           None if diag_shift is None else diag_shift.data_ptr(), max_refine_iters, refine_tol, d.device)
+           None if diag_shift is None else diag_shift.data_ptr(), max_refine_iters, refine_tol, bool(pdd), d.device)
     p = _PLAN_CACHE.get(key)
     if p is None:
         n, nl, es, ic, isd, osd = lay
         p = Plan(n, nl, es, ic, isd, osd, precision=precision, partitions=partitions, nrhs=nrhs,
                  coef_broadcast=coef_broadcast, diag_shift=diag_shift, max_refine_iters=max_refine_iters,
-                 refine_tol=refine_tol)
+                 refine_tol=refine_tol, pdd=pdd)
         _PLAN_CACHE[key] = p
     return p
 
 
 def solve(a, b, c, d, axis=-1, precision="f64", partitions=0, out=None, nrhs=1, coef_broadcast=False,
-          diag_shift=None, max_refine_iters=0, refine_tol=0.0, check=False):
+          diag_shift=None, max_refine_iters=0, refine_tol=0.0, check=False, pdd=False):
     """Solve a_i x_{i-1} + b_i x_i + c_i x_{i+1} = d_i along ``axis`` of every line of ``d``.
 
     a, b, c have d's layout (or are 1D of length n with ``coef_broadcast``); ``out`` may be d.
-    ``check`` synchronises and raises on device-side numerical errors.
+    ``check`` synchronises and raises on device-side numerical errors. ``pdd`` selects the
+    parallel diagonally dominant approximation with ``partitions`` partitions per line.
     """
     if not d.is_cuda:
         raise RuntimeError("tdma.solve needs CUDA tensors (no CPU fallback)")
@@ -346,7 +348,8 @@ def solve(a, b, c, d, axis=-1, precision="f64", partitions=0, out=None, nrhs=1, 
         x = out
         if not _check_same_layout(d, x):
             raise ValueError("out must have d's layout")
-    p = _plan_for(d, axis, precision, partitions, nrhs, coef_broadcast, diag_shift, max_refine_iters, refine_tol)
+    p = _plan_for(d, axis, precision, partitions, nrhs, coef_broadcast, diag_shift, max_refine_iters, refine_tol,
+                  pdd)
     p.solve(a, b, c, d, x)
     if check:
         st, _ = p.last_error()

@@ -100,6 +100,66 @@ TDMA_DEV bool reduced_solve(AT* sub, AT* sup, AT* rhs, int rows, int rhs_pitch) 
   return ok;
 }
 
+// Parallel diagonally dominant (PDD) reduced solve for partition k of P. Stage A left partition
+// j's end rows as the unit-diagonal pair
+//     sub[2j] x_{j-1,last} + x_{j,0} + sup[2j] x_{j,last} = rhs[2j],
+//     sub[2j+1] x_{j,0} + x_{j,last} + sup[2j+1] x_{j+1,0} = rhs[2j+1],
+// which solved for the ends give the spike form x_{j,0} = t0 - v0 y_L - w0 y_R and
+// x_{j,last} = tL - vL y_L - wL y_R in the neighbours' end values y_L = x_{j-1,last},
+// y_R = x_{j+1,0}. At the interface of partitions j and j+1 the method drops v_j(last) y_L and
+// w_{j+1}(0) y_R, leaving the 2x2 system
+//     y1 + wL_j y2 = tL_j,    v0_{j+1} y1 + y2 = t0_{j+1}
+// for y1 = x_{j,last}, y2 = x_{j+1,0}. Partition k takes y_L from its left interface, y_R from
+// its right one (0 at the ends of the line) and returns its end values from the spike form;
+// nothing is written, so every partition reads its neighbours' rows directly.
+template <class CT, int NR> struct PddEnds {
+  CT v0, w0, vL, wL, t0[NR], tL[NR];
+};
+template <class CT, int NR>
+TDMA_DEV PddEnds<CT, NR> pdd_spikes(const CT* sub, const CT* sup, const CT* rhs, int R2, int j) {
+  const CT A0 = sub[2 * j], C0 = sup[2 * j], A1 = sub[2 * j + 1], C1 = sup[2 * j + 1];
+  const CT id = rcp(CT(1) - C0 * A1);
+  PddEnds<CT, NR> e;
+  e.v0 = A0 * id;
+  e.w0 = -C0 * C1 * id;
+  e.vL = -A1 * A0 * id;
+  e.wL = C1 * id;
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    const CT D0 = rhs[q * R2 + 2 * j], D1 = rhs[q * R2 + 2 * j + 1];
+    e.t0[q] = (D0 - C0 * D1) * id;
+    e.tL[q] = (D1 - A1 * D0) * id;
+  }
+  return e;
+}
+template <class CT, int NR>
+TDMA_DEV void pdd_ends(const CT* sub, const CT* sup, const CT* rhs, int R2, int k, int P, CT* x0, CT* xn) {
+  const PddEnds<CT, NR> e = pdd_spikes<CT, NR>(sub, sup, rhs, R2, k);
+  CT yl[NR], yr[NR];
+#pragma unroll
+  for (int q = 0; q < NR; ++q) { yl[q] = CT(0); yr[q] = CT(0); }
+  if (k > 0) {  // left interface: y1 = x_{k-1,last}
+    const PddEnds<CT, NR> l = pdd_spikes<CT, NR>(sub, sup, rhs, R2, k - 1);
+    const CT id = rcp(CT(1) - l.wL * e.v0);
+#pragma unroll
+    for (int q = 0; q < NR; ++q) yl[q] = (l.tL[q] - l.wL * e.t0[q]) * id;
+  }
+  if (k < P - 1) {  // right interface: y2 = x_{k+1,0}
+    const PddEnds<CT, NR> r = pdd_spikes<CT, NR>(sub, sup, rhs, R2, k + 1);
+    const CT id = rcp(CT(1) - e.wL * r.v0);
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      const CT y1 = (e.tL[q] - e.wL * r.t0[q]) * id;
+      yr[q] = r.t0[q] - r.v0 * y1;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < NR; ++q) {
+    x0[q] = e.t0[q] - e.v0 * yl[q] - e.w0 * yr[q];
+    xn[q] = e.tL[q] - e.vL * yl[q] - e.wL * yr[q];
+  }
+}
+
 // Shared-memory plan of the fused kernel (all in units of CT):
 //   scratch  alpha, gamma, delta[NR]: (mmax - 2) slots x T threads each, slot-major
 //   reduced  per line: sub[2P], sup[2P], rhs[NR][2P], line pitch (2 + NR) 2P + 1
@@ -218,23 +278,34 @@ __global__ void __launch_bounds__(512) dc_kernel(const Args A) {
   if (A.lay.n == 1) return;  // no Stage B / C for single-unknown lines
   __syncthreads();
 
-  // ---------------- Stage B: reduced 2P-row system per line, one thread per line
-  if (tid < Lb) {
-    const int64_t l2 = (int64_t)blockIdx.x * Lb + tid;
-    if (l2 < A.lay.n_lines) {
-      CT* sub = red + (size_t)tid * pitch;
-      if (!reduced_solve<CT, NR>(sub, sub + R2, sub + 2 * R2, R2, R2)) report_error(A.st, 5);
+  // ---------------- Stage B: reduced 2P-row system per line, one thread per line (exact), or
+  // the PDD interface systems, each partition's thread on its own (approximate)
+  if (!A.pdd) {
+    if (tid < Lb) {
+      const int64_t l2 = (int64_t)blockIdx.x * Lb + tid;
+      if (l2 < A.lay.n_lines) {
+        CT* sub = red + (size_t)tid * pitch;
+        if (!reduced_solve<CT, NR>(sub, sub + R2, sub + 2 * R2, R2, R2)) report_error(A.st, 5);
+      }
     }
+    __syncthreads();
   }
-  __syncthreads();
 
   // ---------------- Stage C: endpoint values from Stage B, interior by back substitution
   if (active) {
     CT x0[NR], xn[NR];
+    if (A.pdd) {
+      pdd_ends<CT, NR>(r_sub, r_sup, r_rhs, R2, k, P, x0, xn);
+      bool ok = true;
 #pragma unroll
-    for (int q = 0; q < NR; ++q) {
-      x0[q] = r_rhs[q * R2 + 2 * k];
-      xn[q] = r_rhs[q * R2 + 2 * k + 1];
+      for (int q = 0; q < NR; ++q) ok &= finite(x0[q]) && finite(xn[q]);
+      if (!ok) report_error(A.st, 5);
+    } else {
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        x0[q] = r_rhs[q * R2 + 2 * k];
+        xn[q] = r_rhs[q * R2 + 2 * k + 1];
+      }
     }
     store_x<CT, NR>(A, base + start * es, x0);
     store_x<CT, NR>(A, base + (start + m - 1) * es, xn);

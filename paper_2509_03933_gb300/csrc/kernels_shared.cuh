@@ -35,17 +35,26 @@ template <class CT> inline size_t shared_staged_smem() {
   return (size_t)(kSharedBlock / 32) * 2 * 32 * kStagePitch * sizeof(CT) + (size_t)kSharedBlock * sizeof(int64_t);
 }
 
-// Factors of the shared coefficients. The recurrence c'_i = sup_i / (b_i - sub_i c'_{i-1}) is a
-// linear fractional map of c'_{i-1}: with c'_i = N_i / D_i,
-//     [N_i; D_i] = M_i [N_{i-1}; D_{i-1}],    M_i = [[0, sup_i], [-sub_i, b_i]],
-// so the value entering any row follows from a product of 2x2 matrices. The block stages a chunk
-// of the coefficients in shared memory; warp 0 gives each lane a segment of the chunk, forms the
-// product of the segment's matrices (rescaled by powers of two, which leaves N / D unchanged),
-// scans the 32 products across the warp to get the value entering each segment, and then every
-// lane runs the plain recurrence (w_i = 1 / (b_i - sub_i c'_{i-1}), c'_i = sup_i w_i) over its own
-// segment. The serial chain is one segment long instead of one line long.
+// Factors of the shared coefficients: the Thomas recurrence w_i = 1 / (b_i - sub_i c'_{i-1}),
+// c'_i = sup_i w_i, with the results of the serial recurrence bit for bit (the arithmetic of the
+// per-line Thomas kernel, backward stable where Thomas is). One FP64 operation depends on the
+// previous one along the whole line, and a dependent FP64 operation of a single thread takes
+// about 85 cycles on GB300 (one thread over a 512-row line: 148 us), so the chain is cut into
+// 32 segments, one per lane of warp 0, over a chunk of coefficients staged in shared memory:
+//   1. start values: c'_i is a linear fractional map of c'_{i-1}, i.e. with c' = N / D,
+//      [N_i; D_i] = M_i [N_{i-1}; D_{i-1}], M_i = [[0, sup_i], [-sub_i, b_i]]; each lane forms
+//      the product of its segment's matrices (rescaled by powers of two, which leaves N / D
+//      unchanged), a scan over the warp composes them, and the composition applied to the
+//      value entering the chunk estimates the value entering each segment;
+//   2. every lane runs the serial recurrence over its segment from its start value;
+//   3. each lane takes the end value of the lane before as its new start (lane 0 keeps the
+//      exact one); while any start changed (bit for bit), repeat 2.
+// At the fixed point every segment starts from the exact serial value, so every value is the
+// serial recurrence's; after pass t at least lanes 0..t are final, so at most 32 passes run, and
+// on diagonally dominant lines the estimate's error dies out within a segment, so two or three
+// passes suffice.
 constexpr int kFactorThreads = 256;
-constexpr int kFactorChunk = 2016;  // 3 arrays of 2016 doubles + the carry: under 48 KB of static shared memory
+constexpr int kFactorChunk = 2016;  // 3 arrays of 2016 doubles + the carry: under 48 KB static
 
 template <class CT> struct M2 { CT a, b, c, d; };  // [[a, b], [c, d]]
 
@@ -57,7 +66,7 @@ template <class CT> TDMA_DEV M2<CT> shfl_up2(const M2<CT>& x, int dl) {
   return M2<CT>{__shfl_up_sync(0xffffffffu, x.a, dl), __shfl_up_sync(0xffffffffu, x.b, dl),
                 __shfl_up_sync(0xffffffffu, x.c, dl), __shfl_up_sync(0xffffffffu, x.d, dl)};
 }
-// Multiply by a power of two that brings the largest entry near one (exact).
+// Multiply by the power of two that brings the largest entry into [1, 2) (exact).
 template <class CT> TDMA_DEV void rescale(M2<CT>& x) {
   const CT m = fmax(fmax(fabs(x.a), fabs(x.b)), fmax(fabs(x.c), fabs(x.d)));
   if (m > CT(0) && isfinite(m)) {
@@ -65,6 +74,8 @@ template <class CT> TDMA_DEV void rescale(M2<CT>& x) {
     x.a = scalbn(x.a, -k); x.b = scalbn(x.b, -k); x.c = scalbn(x.c, -k); x.d = scalbn(x.d, -k);
   }
 }
+TDMA_DEV uint64_t value_bits(double v) { return (uint64_t)__double_as_longlong(v); }
+TDMA_DEV uint64_t value_bits(float v) { return (uint64_t)__float_as_uint(v); }
 
 template <class CT, bool TR>
 __global__ void __launch_bounds__(kFactorThreads) shared_factor_kernel(const Args A, Pair<CT>* __restrict__ sw,
@@ -91,41 +102,51 @@ __global__ void __launch_bounds__(kFactorThreads) shared_factor_kernel(const Arg
       const int seg = (rows + 31) / 32;
       const int r0 = lane * seg < rows ? lane * seg : rows;
       const int r1 = r0 + seg < rows ? r0 + seg : rows;
+      // 1. estimates of the values entering the segments
       M2<CT> P{CT(1), CT(0), CT(0), CT(1)};
       for (int r = r0; r < r1; ++r) {
-        // M_i scaled by a power of two that brings its largest entry into [1, 2): entries of the
-        // running product grow by at most 4 per row between the rescalings
         M2<CT> Mi{CT(0), s_sup[r], -s_sub[r], s_b[r]};
         rescale(Mi);
         P = mul2(Mi, P);
         if (((r - r0) & 7) == 7) rescale(P);
       }
       rescale(P);
-      // inclusive scan: S_k = P_k P_{k-1} ... P_0 (later segments on the left)
-      for (int dl = 1; dl < 32; dl <<= 1) {
+      for (int dl = 1; dl < 32; dl <<= 1) {  // inclusive scan, later segments on the left
         const M2<CT> o = shfl_up2(P, dl);
         if (lane >= dl) {
           P = mul2(P, o);
           rescale(P);
         }
       }
-      M2<CT> E = shfl_up2(P, 1);  // the product over the segments before this lane's
+      const M2<CT> E = shfl_up2(P, 1);
       const CT carry = s_carry;
-      CT c_prev = carry;
-      if (lane > 0) {
-        const CT N = fma(E.a, carry, E.b), Dd = fma(E.c, carry, E.d);
-        c_prev = N / Dd;
+      CT start = carry;
+      if (lane > 0) start = fma(E.a, carry, E.b) / fma(E.c, carry, E.d);
+      // 2./3. serial passes until the start values stop changing
+      CT end = start;
+      bool lane_ok = true;
+      for (int pass = 0; pass < 33; ++pass) {
+        CT c_prev = start;
+        lane_ok = true;
+#pragma unroll 4
+        for (int r = r0; r < r1; ++r) {
+          const CT sub = s_sub[r];
+          const CT w = rcp(s_b[r] - sub * c_prev);
+          lane_ok &= finite(w);
+          c_prev = s_sup[r] * w;
+          sw[i0 + r] = Pair<CT>{sub, w};
+          cp[i0 + r] = c_prev;
+        }
+        end = r1 > r0 ? c_prev : start;  // an empty segment passes its start on
+        CT next = __shfl_up_sync(0xffffffffu, end, 1);
+        if (lane == 0) next = carry;
+        const bool changed = r1 > r0 && value_bits(next) != value_bits(start);
+        start = next;
+        if (!__any_sync(0xffffffffu, changed)) break;
       }
-      for (int r = r0; r < r1; ++r) {
-        const CT sub = s_sub[r];
-        const CT w = rcp(s_b[r] - sub * c_prev);
-        ok &= finite(w);
-        c_prev = s_sup[r] * w;
-        sw[i0 + r] = Pair<CT>{sub, w};
-        cp[i0 + r] = c_prev;
-      }
+      ok &= lane_ok;
       __syncwarp();
-      if (r1 == rows && r0 < r1) s_carry = c_prev;  // the lane that holds the chunk's last row
+      if (r1 == rows && r0 < r1) s_carry = end;  // the value leaving the chunk
     }
     __syncthreads();
   }

@@ -30,6 +30,7 @@ struct Args {
   int Lb;              // lines per block
   int mmax;            // rows of the largest partition
   int bcast;           // coefficients are 1D arrays of length n
+  int pdd;             // approximate reduced solve (parallel diagonally dominant)
   DevStatus* st;
   // refinement
   int max_iters;

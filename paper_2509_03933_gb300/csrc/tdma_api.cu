@@ -189,6 +189,11 @@ tdma_status_t validate(const tdma_desc_t& d) {
     if (d.nrhs != 1 || d.coef_broadcast || d.diag_shift) return TDMA_ERR_UNSUPPORTED;
     if (d.max_refine_iters < 0) return TDMA_ERR_INVALID_ARG;
   }
+  if (d.pdd != 0 && d.pdd != 1) return TDMA_ERR_INVALID_ARG;
+  if (d.pdd) {  // the approximate reduced solve: fused D&C kernel, explicit partitions
+    if (d.n == 0 || (d.precision != TDMA_F64 && d.precision != TDMA_F32)) return TDMA_ERR_UNSUPPORTED;
+    if (d.partitions < 1) return TDMA_ERR_INVALID_ARG;
+  }
   return TDMA_OK;
 }
 
@@ -203,6 +208,7 @@ Args make_args(const tdma_plan_s* p, const void* a, const void* b, const void* c
   A.Lb = p->cfg.lines_per_block;
   A.mmax = p->cfg.rows_per_thread;
   A.bcast = p->desc.coef_broadcast;
+  A.pdd = p->desc.pdd;
   A.st = p->status;
   A.max_iters = p->desc.max_refine_iters > 0 ? p->desc.max_refine_iters : 4;
   A.tol = (float)(p->desc.refine_tol > 0 ? p->desc.refine_tol : kDefaultRefineTol);
@@ -970,7 +976,7 @@ void remember_config(const tdma_desc_t& d, const tdma_config_t& c) {
 
 tdma_status_t autotune_impl(tdma_plan_s* p, const void* a, const void* b, const void* c, const void* d, void* x,
                             void* ws, size_t ws_bytes, cudaStream_t s) {
-  if (p->desc.n == 0 || p->desc.n_lines == 0) return TDMA_OK;
+  if (p->desc.n == 0 || p->desc.n_lines == 0 || p->desc.pdd) return TDMA_OK;
   const auto cands = tune_candidates(p->desc, p->allow_tma);
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TDMA_ERR_CUDA;
@@ -1065,7 +1071,14 @@ tdma_status_t tdma_plan_create(tdma_plan_t* plan, const tdma_desc_t* desc, size_
   if (const char* e = std::getenv("TDMA_DISABLE_TMA")) p->allow_tma = !(e[0] == '1');
   if (cudaGetDevice(&p->device) != cudaSuccess) { delete p; return TDMA_ERR_CUDA; }
   tdma_config_t c{};
-  if (is_uniform(*desc) && desc->partitions == 0 && cached_config(*desc, p->allow_tma, c)) {
+  if (desc->pdd) {
+    if (!choose_block(*desc, desc->partitions, c)) {
+      delete p;
+      return TDMA_ERR_UNSUPPORTED;
+    }
+    p->cfg = c;
+    p->workspace = workspace_for(*desc, c);
+  } else if (is_uniform(*desc) && desc->partitions == 0 && cached_config(*desc, p->allow_tma, c)) {
     p->cfg = c;
     p->workspace = workspace_for(*desc, c);
   } else if (is_uniform(*desc)) {
@@ -1230,6 +1243,7 @@ tdma_status_t tdma_solve_backward(tdma_plan_t p, const void* a, const void* b, c
                                   const void* gx, void* ga, void* gb, void* gc, void* gd, void* ws,
                                   size_t ws_bytes, void* stream) {
   if (!p) return TDMA_ERR_INVALID_ARG;
+  if (p->desc.pdd) return TDMA_ERR_UNSUPPORTED;  // the approximation has no adjoint here
   if (p->desc.n_lines == 0) return TDMA_OK;
   if (!a || !b || !c || !x || !gx || !gd) return TDMA_ERR_INVALID_ARG;
   if (ws_bytes < p->workspace || (p->workspace > 0 && !ws)) return TDMA_ERR_WORKSPACE;

@@ -59,6 +59,7 @@ extern "C" tdma_status_t tdma_solve_thomas_static(const tdma_desc_t* desc, const
   if (dd.inner_count < 1 || dd.elem_stride < 0 || dd.inner_stride < 0 || dd.outer_stride < 0)
     return TDMA_ERR_INVALID_ARG;
   if (dd.partitions > 1) return TDMA_ERR_UNSUPPORTED;  // the Thomas form has one partition
+  if (dd.pdd != 0) return TDMA_ERR_UNSUPPORTED;
   if (dd.n_lines == 0) return TDMA_OK;
   if (!a || !b || !c || !d || !x) return TDMA_ERR_INVALID_ARG;
   const size_t eb = dd.precision == TDMA_F64 ? 8 : 4;

@@ -41,6 +41,9 @@ def _create(**kw):
     (dict(inner_count=0), 1), (dict(elem_stride=-1), 1),
     (dict(n=0, ragged_max_n=0), 1),                       # ragged without offsets/lengths
     (dict(precision=2, nrhs=2), 2), (dict(precision=2, coef_broadcast=1), 2),
+    (dict(pdd=1), 1), (dict(pdd=2, partitions=4), 1),   # PDD needs explicit partitions; flag 0/1
+    (dict(pdd=1, partitions=4, precision=2), 2), (dict(pdd=1, partitions=4, precision=3), 2),
+    (dict(pdd=1, partitions=4, n=0, n_lines=0), 2),      # ragged batches have no PDD mode
 ])
 def test_invalid_descriptors_are_rejected_on_the_host(kw, code):
     assert _create(**kw) == code
