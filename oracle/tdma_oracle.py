@@ -29,6 +29,10 @@ Functions and the passage each follows:
                      PDD values; it is pinned by the cases the method fixes (p = 1 and
                      decoupled partitions are exact, rows off the partition boundaries hold
                      exactly, the error falls geometrically with the partition length).
+  poisson_fft     -- the FFT-based Poisson solve (Section 5.2): real FFT over every periodic
+                     (z, x) plane, one tridiagonal line per wavenumber pair along y with the
+                     diagonal shifted by the modified wavenumbers, inverse FFT (numpy.fft and
+                     thomas as the steps).
   residual        -- r = d - A x.
   adjoint_grads   -- gradients of a scalar loss through x = A^{-1} d: lambda = A^{-T} g,
                      grad_d = lambda, grad_b = -lambda*x, grad_a_i = -lambda_i x_{i-1},
@@ -40,7 +44,7 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["thomas", "thomas_ext", "dense_matrix", "dense_solve", "partition_rows", "dc_spike", "pdd",
+__all__ = ["thomas", "thomas_ext", "dense_matrix", "dense_solve", "partition_rows", "dc_spike", "pdd", "poisson_fft",
            "residual", "adjoint_grads", "transpose_coefficients", "thomas_ragged", "rel_l2"]
 
 
@@ -263,6 +267,40 @@ def pdd(a, b, c, d, p: int):
         if k < p - 1:
             x[:, s:e] -= w[:, s:e] * y2[:, k][:, None]
     return x[0] if squeeze else x
+
+
+def poisson_fft(q, dx, dz, a, b, c, pin_zero_mode=True):
+    """Discrete Poisson solve D_xx phi + D_yy phi + D_zz phi = q on a grid q[y][z][x] periodic in
+    x and z (Section 5.2: Fourier transforms in the two periodic directions leave
+    (D_yy - k_x'^2 - k_z'^2) Phi = Q, one tridiagonal system along y per wavenumber pair).
+
+    D_xx, D_zz are the periodic second differences (u_{i+1} - 2 u_i + u_{i-1}) / h^2, whose Fourier
+    symbols are -k'^2(l) = -(2 - 2 cos(2 pi l / N)) / h^2; D_yy is the tridiagonal (a, b, c) of
+    length ny. Steps: Q = rfft2(q) over (z, x); for every (kz, kx) solve the complex line with
+    Thomas (real and imaginary parts as two right-hand sides); phi = irfft2(Phi). With
+    pin_zero_mode the (0, 0) line's row 0 is replaced by Phi_0 = 0 (its system is singular when
+    D_yy has Neumann ends).
+    """
+    q = np.asarray(q, dtype=np.float64)
+    ny, nz, nx = q.shape
+    a, b, c = (np.asarray(t, dtype=np.float64) for t in (a, b, c))
+    Q = np.fft.rfft2(q, axes=(1, 2))                      # [ny][nz][nkx]
+    nkx = Q.shape[2]
+    k2x = (2.0 - 2.0 * np.cos(2.0 * np.pi * np.arange(nkx) / nx)) / dx ** 2
+    k2z = (2.0 - 2.0 * np.cos(2.0 * np.pi * np.arange(nz) / nz)) / dz ** 2
+    shift = -(k2z[:, None] + k2x[None, :]).reshape(-1)   # line l = kz * nkx + kx
+    L = nz * nkx
+    lines_a = np.broadcast_to(a, (L, ny)).copy()
+    lines_b = b[None, :] + shift[:, None]
+    lines_c = np.broadcast_to(c, (L, ny)).copy()
+    rhs = Q.reshape(ny, L).T                             # [L][ny] complex
+    D = np.stack([rhs.real, rhs.imag], axis=-1)          # [L][ny][2]
+    if pin_zero_mode:
+        lines_b[0, 0], lines_c[0, 0] = 1.0, 0.0
+        D[0, 0, :] = 0.0
+    X = thomas(lines_a, lines_b, lines_c, D)
+    Phi = (X[..., 0] + 1j * X[..., 1]).T.reshape(ny, nz, nkx)
+    return np.fft.irfft2(Phi, s=(nz, nx), axes=(1, 2))
 
 
 def residual(a, b, c, d, x, dtype=np.float64):
