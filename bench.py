@@ -372,6 +372,63 @@ def suite_poisson(stream, hbm_peak):
                      "rel_l2_error_vs_extended": oracle.rel_l2(got, refs), "modes_checked": int(len(modes)),
                      "plan": main.config}
         del main, zero
+    del p, d, x, d3, x3, shift
+    torch.cuda.empty_cache()
+    out["fft_pipeline"] = suite_poisson_fft(stream, n)
+    return out
+
+
+def suite_poisson_fft(stream, n=1024):
+    """The whole FFT-based Poisson solve on an n^3 grid q[y][z][x] (periodic x, z; stretched y
+    with Neumann ends): cuFFT over the (z, x) planes, the n (n/2 + 1) n wavenumber lines along y,
+    cuFFT back, through tdma_poisson_solve. Error: the discrete equation on sampled y planes
+    (normwise backward error; the pinned row excluded). The line solves alone are timed on a
+    buffer of the spectrum's layout."""
+    import synth
+    import paper_2509_03933_gb300 as tdma
+    a, c, b = synth.poisson_coefficients(n)
+    dx = dz = 2 * np.pi / n
+    q = synth.normal(7, synth.AID["d"], torch.arange(n ** 3, device="cuda")).reshape(n, n, n)
+    phi = torch.empty_like(q)
+    out = {}
+    for prec in ("f64", "f64r"):
+        solver = tdma.PoissonFFT(n, n, n, dx, dz, a, b, c, precision=prec)
+        ms = _timed(lambda: solver.solve(q, out=phi, stream=stream), 5, 3, stream)
+        solver.solve(q, out=phi, check=True)
+        A, B, C = (torch.from_numpy(t).cuda() for t in (a, b, c))
+        pmax = phi.abs().max().item()
+        worst = 0.0
+        for y in (0, 1, n // 2, n - 1):
+            pl = phi[y]
+            lap = (torch.roll(pl, -1, 1) - 2 * pl + torch.roll(pl, 1, 1)) / dx ** 2
+            lap += (torch.roll(pl, -1, 0) - 2 * pl + torch.roll(pl, 1, 0)) / dz ** 2 + B[y] * pl
+            if y > 0:
+                lap += A[y] * phi[y - 1]
+            if y < n - 1:
+                lap += C[y] * phi[y + 1]
+            r = lap - q[y]
+            if y == 0:
+                r = r - r.mean()
+            scale = (4 / dx ** 2 + 4 / dz ** 2 + abs(a[y]) + abs(b[y]) + abs(c[y])) * pmax
+            worst = max(worst, r.abs().max().item() / scale)
+        out[prec] = {"ms_per_solve": ms, "grid_points_per_s": n ** 3 / (ms * 1e-3),
+                     "backward_error_sampled_planes": worst, "workspace_GB": solver.workspace.numel() / 1e9}
+        del solver
+        torch.cuda.empty_cache()
+    # the wavenumber lines alone, in the spectrum's layout [y][kz][kx] (lines 1 .. L-1)
+    nkx = n // 2 + 1
+    L = n * nkx
+    spec = torch.zeros((n, L, 2), dtype=torch.float64, device="cuda")
+    k2x = (2 - 2 * np.cos(2 * np.pi * np.arange(nkx) / n)) / dx ** 2
+    k2z = (2 - 2 * np.cos(2 * np.pi * np.arange(n) / n)) / dz ** 2
+    shift = torch.from_numpy(-(k2z[:, None] + k2x[None, :]).reshape(-1)[1:].copy()).cuda()
+    plan = tdma.Plan(n, L - 1, elem_stride=L, inner_count=L - 1, inner_stride=1, nrhs=2, coef_broadcast=True,
+                     diag_shift=shift)
+    A, B, C = (torch.from_numpy(t).cuda() for t in (a, b, c))
+    lines = spec[:, 1:, :]
+    ms_lines = _timed(lambda: plan.solve(A, B, C, lines, lines, stream=stream), 5, 3, stream)
+    out["lines_only"] = {"ms": ms_lines, "plan": plan.config, "complex_unknowns": n * (L - 1)}
+    out["fft_share_f64"] = 1.0 - ms_lines / out["f64"]["ms_per_solve"]
     return out
 
 
@@ -468,6 +525,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-suite", action="store_true", help="skip the other workloads")
+    ap.add_argument("--only-poisson-fft", type=int, default=0, metavar="N",
+                    help="run only the FFT-based Poisson solve on an N^3 grid and print it (profiling runs)")
     ap.add_argument("--only-adi", type=int, default=0, metavar="N",
                     help="run only the ADI workload on an N^3 grid and print it (profiling runs)")
     ap.add_argument("--only-ragged", type=int, default=0, metavar="LINES",
@@ -477,6 +536,10 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_poisson_fft > 0:
+        print(json.dumps({"poisson_fft": suite_poisson_fft(torch.cuda.current_stream(), args.only_poisson_fft)}),
+              flush=True)
+        return 0
     if args.only_adi > 0:
         hbm_peak, _ = peaks()
         print(json.dumps({"adi": suite_adi(torch.cuda.current_stream(), hbm_peak, args.only_adi)}), flush=True)

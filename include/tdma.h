@@ -247,6 +247,51 @@ tdma_status_t tdma_solve_host(tdma_plan_t plan, const tdma_host_layout_t* layout
 tdma_status_t tdma_solve_thomas_static(const tdma_desc_t* desc, const void* a, const void* b,
                                        const void* c, const void* d, void* x, void* stream);
 
+/* ---- FFT-based Poisson solve on one GPU (Section 5.2; Section 6.1, Poisson-v1) ---------------
+ * Solves the discrete Poisson equation  D_xx phi + D_yy phi + D_zz phi = q  on a grid periodic in
+ * x and z, with the wall-normal operator D_yy given as a tridiagonal matrix (a, b, c along y):
+ * a 2D real FFT of every (z, x) plane turns it into one tridiagonal system along y per wavenumber
+ * pair, (D_yy - k'_x^2 - k'_z^2) Phi = Q with the modified wavenumbers of the second-order periodic
+ * differences k'^2(l) = (2 - 2 cos(2 pi l / N)) / h^2; those lines are solved by the batched
+ * solver (broadcast a, b, c with a per-line diagonal shift, complex right-hand side as two
+ * interleaved real ones); an inverse FFT returns phi.
+ *   Layout: q and phi are DEVICE arrays of ny x nz x nx doubles, x fastest (phi[y][z][x]). The
+ *   plane transforms then leave the spectrum as [y][kz][kx] (kx = 0..nx/2), so the lines along y
+ *   are adjacent in memory and strided by one plane: no transpose, no 2D-into-3D insertion (the
+ *   non-coalesced copy Poisson-v1 works around). phi may alias q.
+ *   Scaling: the FFT pair's 1 / (nx nz) is folded into the line coefficients (no extra pass).
+ *   Zero mode: with pin_zero_mode = 1 the (kx, kz) = (0, 0) line's row 0 is replaced by Phi_0 = 0
+ *   (the Neumann-ended D_yy makes that line singular); solved by its own one-line plan.
+ *   FFTs: cuFFT (D2Z / Z2D, batched over y); its plans and work areas are created in
+ *   tdma_poisson_create. tdma_poisson_solve allocates nothing. */
+typedef struct tdma_poisson_s* tdma_poisson_t;
+
+typedef struct {
+  int64_t nx, ny, nz;     /* grid points (nx even, nx, nz >= 2, ny >= 2)                      */
+  double dx, dz;          /* periodic spacings (> 0)                                          */
+  const double* a;        /* HOST, ny values: D_yy's sub-diagonal (a[0] ignored)              */
+  const double* b;        /* HOST, ny values: its diagonal                                    */
+  const double* c;        /* HOST, ny values: its super-diagonal (c[ny-1] ignored)            */
+  int32_t pin_zero_mode;  /* 1: pin the (0, 0) line as above; 0: solve it as given            */
+  tdma_precision_t precision; /* TDMA_F64, or TDMA_F64_REFINE for the wavenumber lines        */
+} tdma_poisson_desc_t;
+
+/* Copies the coefficients to the device, creates the cuFFT plans and the line plans, and reports
+ * the workspace tdma_poisson_solve needs (the spectrum, twice with TDMA_F64_REFINE, plus the line
+ * plans' workspaces). TDMA_ERR_INVALID_ARG for a bad descriptor, TDMA_ERR_UNSUPPORTED for another
+ * precision, TDMA_ERR_CUDA when cuFFT or CUDA fails. */
+tdma_status_t tdma_poisson_create(tdma_poisson_t* plan, const tdma_poisson_desc_t* desc, size_t* workspace_bytes);
+
+/* phi = the solution for right-hand side q (device arrays as above); enqueued on `stream`.
+ * Device-side numerical faults of the line solves are read by tdma_poisson_last_error. */
+tdma_status_t tdma_poisson_solve(tdma_poisson_t plan, const double* q, double* phi, void* workspace,
+                                 size_t workspace_bytes, void* stream);
+
+/* Synchronise `stream` and read (and clear) the line plans' device status. */
+tdma_status_t tdma_poisson_last_error(tdma_poisson_t plan, void* stream);
+
+tdma_status_t tdma_poisson_destroy(tdma_poisson_t plan);
+
 #ifdef __cplusplus
 }
 #endif

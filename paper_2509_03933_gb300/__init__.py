@@ -11,11 +11,12 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import torch
 
 from . import _build
 
-__all__ = ["Plan", "solve", "solve_ragged", "solve_backward", "TDMASolve", "line_layout", "TDMAError", "F64", "F32",
+__all__ = ["PoissonFFT", "Plan", "solve", "solve_ragged", "solve_backward", "TDMASolve", "line_layout", "TDMAError", "F64", "F32",
            "F32_REFINE", "load_library", "declared_symbols", "sweep_graph", "HostPipeline", "HostLayout"]
 
 F64, F32, F32_REFINE, F64_REFINE = 0, 1, 2, 3
@@ -40,6 +41,12 @@ class Desc(ctypes.Structure):
                 ("ragged_total", ctypes.c_int64), ("nrhs", ctypes.c_int32), ("coef_broadcast", ctypes.c_int32),
                 ("diag_shift", ctypes.c_void_p), ("precision", ctypes.c_int32), ("partitions", ctypes.c_int32),
                 ("max_refine_iters", ctypes.c_int32), ("refine_tol", ctypes.c_double), ("pdd", ctypes.c_int32)]
+
+
+class PoissonDesc(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int64), ("ny", ctypes.c_int64), ("nz", ctypes.c_int64), ("dx", ctypes.c_double),
+                ("dz", ctypes.c_double), ("a", ctypes.c_void_p), ("b", ctypes.c_void_p), ("c", ctypes.c_void_p),
+                ("pin_zero_mode", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
 
 class Config(ctypes.Structure):
@@ -89,6 +96,15 @@ def load_library(build: bool = True) -> ctypes.CDLL:
     lib.tdma_solve_host.argtypes = [_VP, ctypes.POINTER(HostLayout)] + [_VP] * 5 + [ctypes.c_int32, _VP, _VP,
                                                                                      ctypes.c_size_t, _VP]
     lib.tdma_solve_host.restype = st
+    lib.tdma_poisson_create.argtypes = [ctypes.POINTER(_VP), ctypes.POINTER(PoissonDesc),
+                                        ctypes.POINTER(ctypes.c_size_t)]
+    lib.tdma_poisson_create.restype = st
+    lib.tdma_poisson_solve.argtypes = [_VP, _VP, _VP, _VP, ctypes.c_size_t, _VP]
+    lib.tdma_poisson_solve.restype = st
+    lib.tdma_poisson_last_error.argtypes = [_VP, _VP]
+    lib.tdma_poisson_last_error.restype = st
+    lib.tdma_poisson_destroy.argtypes = [_VP]
+    lib.tdma_poisson_destroy.restype = st
     _LIB = lib
     return lib
 
@@ -234,6 +250,54 @@ class Plan:
         info = ctypes.c_int32(0)
         st = self._lib.tdma_last_device_error(self._h, _stream(stream), ctypes.byref(info))
         return st, info.value
+
+
+class PoissonFFT:
+    """FFT-based Poisson solve on one GPU (tdma_poisson_*): D_xx phi + D_yy phi + D_zz phi = q on an
+    (ny, nz, nx) grid stored [y][z][x], periodic in x and z with spacings dx, dz, and D_yy the
+    tridiagonal operator (a, b, c) along y (1D arrays of length ny, host or CPU tensors). cuFFT over
+    every (z, x) plane, one tridiagonal line per wavenumber pair along y, cuFFT back. With
+    ``pin_zero_mode`` the (0, 0) line's row 0 becomes Phi_0 = 0 (needed when D_yy has Neumann ends).
+    ``precision`` "f64" or "f64r" (exact-residual correction of the wavenumber lines)."""
+
+    def __init__(self, nx, ny, nz, dx, dz, a, b, c, pin_zero_mode=True, precision="f64", device="cuda"):
+        self._lib = load_library()
+        ha, hb, hc = (np.ascontiguousarray(np.asarray(t.cpu() if torch.is_tensor(t) else t, dtype=np.float64))
+                      for t in (a, b, c))
+        if not (ha.shape == hb.shape == hc.shape == (ny,)):
+            raise ValueError("a, b, c must be 1D of length ny")
+        self.desc = PoissonDesc(nx=nx, ny=ny, nz=nz, dx=dx, dz=dz, a=ha.ctypes.data, b=hb.ctypes.data,
+                                c=hc.ctypes.data, pin_zero_mode=int(bool(pin_zero_mode)), precision=_PREC[precision])
+        self._h = ctypes.c_void_p()
+        ws = ctypes.c_size_t(0)
+        with torch.cuda.device(torch.device(device)):
+            st = self._lib.tdma_poisson_create(ctypes.byref(self._h), ctypes.byref(self.desc), ctypes.byref(ws))
+        if st != 0:
+            raise TDMAError(st, "tdma_poisson_create")
+        self.shape = (ny, nz, nx)
+        self.workspace = torch.empty(max(1, ws.value), dtype=torch.uint8, device=device)
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None) and self._h.value:
+                self._lib.tdma_poisson_destroy(self._h)
+        except Exception:
+            pass
+
+    def solve(self, q, out=None, stream=None, check=False):
+        """phi for right-hand side q (a contiguous float64 CUDA tensor of shape (ny, nz, nx))."""
+        if not q.is_cuda or q.dtype != torch.float64 or tuple(q.shape) != self.shape or not q.is_contiguous():
+            raise ValueError(f"q must be a contiguous float64 CUDA tensor of shape {self.shape}")
+        phi = torch.empty_like(q) if out is None else out
+        st = self._lib.tdma_poisson_solve(self._h, _ptr(q), _ptr(phi), _ptr(self.workspace),
+                                          ctypes.c_size_t(self.workspace.numel()), _stream(stream))
+        if st != 0:
+            raise TDMAError(st, "tdma_poisson_solve")
+        if check:
+            st = self._lib.tdma_poisson_last_error(self._h, _stream(stream))
+            if st != 0:
+                raise TDMAError(st, "device")
+        return phi
 
 
 class HostPipeline:
