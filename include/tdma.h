@@ -292,6 +292,48 @@ tdma_status_t tdma_poisson_last_error(tdma_poisson_t plan, void* stream);
 
 tdma_status_t tdma_poisson_destroy(tdma_poisson_t plan);
 
+/* ---- Lines split across ranks (Section 2.1; Algorithm 2) --------------------------------------
+ * Every rank holds a slab of consecutive rows of every line (the paper's 1D decomposition along
+ * the solve axis). Per batch of lines [line0, line0 + count):
+ *   1. tdma_slab_reduce on every rank: Stage A over its slab (the slab is one partition). Writes,
+ *      per line, the slab's first and last rows as a unit-diagonal pair in the neighbouring slabs'
+ *      end unknowns: K = 4 + 2 nrhs doubles [sub0, sup0, sub1, sup1, rhs0[nrhs], rhs1[nrhs]] to
+ *      `reduced` ([count][K]), and the interior relations to `scratch`
+ *      (tdma_slab_scratch_bytes(desc, count) bytes, [array][row][line]; kept for step 4).
+ *   2. an all-to-all (the caller's; the paper's A2B): the rank that solves Stage B for a line
+ *      gathers the line's pairs from all W slabs, slab-major: gathered[W][lines][K].
+ *   3. tdma_slab_pairs_solve on that rank: the 2W-row unit-diagonal system of every gathered line
+ *      by Thomas in FP64; writes every slab's first and last values, ends[W][lines][2 nrhs]
+ *      (`work`: tdma_slab_pairs_work_bytes bytes of device scratch).
+ *   4. an all-to-all back (B2C), then tdma_slab_finish on every rank: Stage C over its slab from
+ *      its own two end values, ends[count][2 nrhs].
+ * All arrays are FP64 DEVICE arrays owned by the caller; the slab's a, b, c, d, x use the element
+ * addressing of tdma_desc_t with n = n_local rows (d, x with nrhs interleaved values). first /
+ * last mark the slab that holds the line's first / last row (its a_0 / c_{n-1} are ignored).
+ * n_local >= 2. Zero or non-finite pivots set *status to TDMA_ERR_NONFINITE (status: a device
+ * int32, may be NULL). The calls enqueue on `stream` and allocate nothing. */
+typedef struct {
+  int64_t n_local;        /* rows of this rank's slab (>= 2)                          */
+  int64_t n_lines;        /* lines in the local arrays                                */
+  int64_t elem_stride;    /* addressing as in tdma_desc_t, with n = n_local           */
+  int64_t inner_count;
+  int64_t inner_stride;
+  int64_t outer_stride;
+  int32_t nrhs;           /* 1 or 2                                                   */
+  int32_t first;          /* 1: this slab holds row 0 of every line                   */
+  int32_t last;           /* 1: this slab holds row n-1 of every line                 */
+} tdma_slab_desc_t;
+
+size_t tdma_slab_scratch_bytes(const tdma_slab_desc_t* desc, int64_t count);
+size_t tdma_slab_pairs_work_bytes(int32_t n_slabs, int64_t count, int32_t nrhs);
+tdma_status_t tdma_slab_reduce(const tdma_slab_desc_t* desc, const double* a, const double* b, const double* c,
+                               const double* d, int64_t line0, int64_t count, double* reduced, double* scratch,
+                               int32_t* status, void* stream);
+tdma_status_t tdma_slab_pairs_solve(int32_t n_slabs, int64_t count, int32_t nrhs, const double* gathered,
+                                    double* ends, double* work, int32_t* status, void* stream);
+tdma_status_t tdma_slab_finish(const tdma_slab_desc_t* desc, int64_t line0, int64_t count, const double* ends,
+                               const double* scratch, double* x, void* stream);
+
 #ifdef __cplusplus
 }
 #endif
