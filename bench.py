@@ -283,6 +283,19 @@ def suite_adi(stream, hbm_peak, n=512):
     U = 3 * n ** 3
     u = d.clone()
     out = {}
+    # CPU-baseline leg: the oracle's Thomas (FP64) and PDD on a sample of z lines (timed)
+    lines = synth.line_view(d[:, :8, :].cpu(), 0).numpy()  # 8 y-rows: 8 n lines of n
+    A = np.full_like(lines, -r)
+    B = np.full_like(lines, 1 + 2 * r)
+    t0 = time.perf_counter()
+    oracle.thomas(A, B, A, lines)
+    dt = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.pdd(A, B, A, lines, 8)
+    dt_pdd = time.perf_counter() - t0
+    out["cpu_baseline"] = {"value": lines.size / dt, "unit": "unknowns/s", "cores": 1, "kind": "oracle",
+                           "sample": f"{lines.shape[0]} z lines of n = {n} (Thomas, FP64)",
+                           "pdd_P8_value": lines.size / dt_pdd}
     one = lambda v: torch.full((n,), v, dtype=torch.float64, device="cuda")
     legs = (("per_element_P8", (a, b, c), dict(partitions=8)),
             ("shared_coefficients", (one(-r), one(1 + 2 * r), one(-r)), dict(coef_broadcast=True)))
@@ -386,11 +399,22 @@ def suite_poisson_fft(stream, n=1024):
     buffer of the spectrum's layout."""
     import synth
     import paper_2509_03933_gb300 as tdma
+    import oracle
     a, c, b = synth.poisson_coefficients(n)
     dx = dz = 2 * np.pi / n
     q = synth.normal(7, synth.AID["d"], torch.arange(n ** 3, device="cuda")).reshape(n, n, n)
     phi = torch.empty_like(q)
     out = {}
+    # CPU-baseline leg: the oracle's FFT-based solve (numpy FFTs + Thomas) on 32 y-rows' worth of
+    # a 128 x 128 x n grid (timed), scaled to grid points per second
+    ns = 128
+    ac, cc, bc = synth.poisson_coefficients(32)
+    qs = np.random.default_rng(7).standard_normal((32, ns, ns))
+    t0 = time.perf_counter()
+    oracle.poisson_fft(qs, 2 * np.pi / ns, 2 * np.pi / ns, ac, bc, cc)
+    dt = time.perf_counter() - t0
+    out["cpu_baseline"] = {"value": qs.size / dt, "unit": "grid points/s", "cores": 1, "kind": "oracle",
+                           "sample": f"32 x {ns} x {ns} grid (numpy FFTs + Thomas)"}
     for prec in ("f64", "f64r"):
         solver = tdma.PoissonFFT(n, n, n, dx, dz, a, b, c, precision=prec)
         ms = _timed(lambda: solver.solve(q, out=phi, stream=stream), 5, 3, stream)
