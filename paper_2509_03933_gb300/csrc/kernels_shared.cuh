@@ -12,9 +12,9 @@
 //   stream: adjacent lines are adjacent in memory (a strided axis), so one warp's access to a row
 //           is coalesced; rows are loaded kSharedAhead ahead of the recurrence in both sweeps.
 //   staged: unit-stride lines (the contiguous axis). Each warp owns 32 lines and moves them
-//           through shared memory in chunks of 32 elements per line: lane k copies element k of
-//           every line (coalesced, cp.async, the next chunk in flight during the recurrence over
-//           the current one), lane j runs the recurrence of line j on the chunk.
+//           through shared memory in chunks of 16 elements per line: a half-warp copies one
+//           line's chunk (coalesced 128-byte segments, cp.async, the next chunk in flight during
+//           the recurrence over the current one), lane j runs the recurrence of line j.
 #pragma once
 #include "layout.cuh"
 #include "kernels_dc.cuh"
@@ -23,8 +23,9 @@ namespace tdma {
 
 constexpr int kSharedBlock = 128;
 constexpr int kSharedAhead = 8;   // rows in flight per thread in the stream kernel
-constexpr int kStageElems = 32;   // elements per line per chunk in the staged kernel
-constexpr int kStagePitch = 33;   // odd pitch: lane j's row of the chunk falls in its own banks
+constexpr int kStageElems = 16;   // elements per line per chunk in the staged kernel (34 KB per
+                                  // block: 6 blocks per SM; 32 elements held 3)
+constexpr int kStagePitch = 17;   // odd pitch: lane j's row of the chunk falls in its own banks
 
 template <class CT> struct alignas(2 * sizeof(CT)) Pair { CT sub, w; };
 
@@ -261,8 +262,8 @@ template <int N> TDMA_DEV void stage_wait() { asm volatile("cp.async.wait_group 
 
 // Unit-stride lines: see the file comment. Chunk c of a line is its elements
 // [c * kStageElems, (c + 1) * kStageElems) of the n * NR interleaved values; lane k copies element
-// k of the chunk of every line of its warp, so the same lane writes x in the forward sweep and
-// reads it back in the backward sweep.
+// k mod E of the chunk of lines k / E, k / E + 32 / E, ... of its warp, so the same lane writes a
+// value of x in the forward sweep and reads it back in the backward sweep.
 template <class CT, int NR>
 __global__ void __launch_bounds__(kSharedBlock) shared_staged_kernel(const Args A, const Pair<CT>* __restrict__ sw,
                                                                      const CT* __restrict__ cp) {
@@ -281,19 +282,21 @@ __global__ void __launch_bounds__(kSharedBlock) shared_staged_kernel(const Args 
   const int nc = (int)((total + E - 1) / E);
   const CT* D = (const CT*)A.d;
   CT* X = (CT*)A.x;
+  constexpr int LPI = 32 / E;  // lines per copy instruction
+  const int e = lane % E, sub = lane / E;
   auto issue = [&](const CT* src, int c, int b) {
-    const int64_t k = (int64_t)c * E + lane;
+    const int64_t k = (int64_t)c * E + e;
     if (k < total) {
-      CT* t = tile + (size_t)b * 32 * PT + lane;
-      for (int j = 0; j < lines; ++j) stage_copy(t + j * PT, src + s_off[j] + k);
+      CT* t = tile + (size_t)b * 32 * PT + e;
+      for (int j = sub; j < lines; j += LPI) stage_copy(t + j * PT, src + s_off[j] + k);
     }
     stage_commit();
   };
   auto drain = [&](int c, int b) {
-    const int64_t k = (int64_t)c * E + lane;
+    const int64_t k = (int64_t)c * E + e;
     if (k < total) {
-      const CT* t = tile + (size_t)b * 32 * PT + lane;
-      for (int j = 0; j < lines; ++j) X[s_off[j] + k] = t[j * PT];
+      const CT* t = tile + (size_t)b * 32 * PT + e;
+      for (int j = sub; j < lines; j += LPI) X[s_off[j] + k] = t[j * PT];
     }
   };
   const bool mine = lane < lines;
