@@ -27,15 +27,15 @@ TDMA_DEV void report_iters(DevStatus* st, int32_t it) {
 }
 
 // ---- reciprocals ----------------------------------------------------------------------
-// FP64: MUFU seed (relative error < 2^-20) refined by Newton-Raphson for 1/w,
-// y <- y + y (1 - w y); each step squares the relative error (2^-40, then below one ulp).
+// FP64: MUFU seed y (relative error below 2^-20) refined by the series 1/w = y / (1 - e) with
+// e = 1 - w y, truncated after the quadratic term: y (1 + e + e^2) = (1/w) (1 - e^3), a relative
+// error below 2^-60 before the final rounding; three dependent FMAs (two Newton-Raphson steps
+// take four).
 TDMA_DEV double rcp(double w) {
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(w));
-  double e = fma(-w, y, 1.0);
-  y = fma(y, e, y);
-  e = fma(-w, y, 1.0);
-  return fma(y, e, y);
+  const double e = fma(-w, y, 1.0);
+  return fma(y, fma(e, e, e), y);
 }
 // FP32: the MUFU reciprocal (about one ulp).
 TDMA_DEV float rcp(float w) {

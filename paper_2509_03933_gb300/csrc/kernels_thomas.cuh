@@ -5,7 +5,7 @@
 // unknown than the partitioned sweep: w = b_i - a_i c'_{i-1}, c'_i = c_i / w,
 // d'_i = (d_i - a_i d'_{i-1}) / w, then x_i = d'_i - c'_i x_{i+1}. On GB300 the FP64 pipe bounds
 // the FP64 solve, so when a batch has enough lines to fill the GPU with one thread per line
-// this is the fastest FP64 form (9 FP64-pipe operations per unknown against about 15). The
+// this is the fastest FP64 form (8 FP64-pipe operations per unknown against about 14). The
 // forward sweep stores c' in the workspace (row-major [row][line], coalesced across adjacent
 // lines) and d' in x; the backward sweep reads both back in reverse order.
 #pragma once
