@@ -100,6 +100,97 @@ TDMA_DEV bool reduced_solve(AT* sub, AT* sup, AT* rhs, int rows, int rhs_pitch) 
   return ok;
 }
 
+// Reduced systems longer than this many rows are solved in two levels (below).
+constexpr int kTwoLevelRows = 32;
+constexpr int kTwoLevelSeg = 16;
+__host__ __device__ inline int two_level_groups(int R2) {
+  return R2 > kTwoLevelRows ? (R2 + kTwoLevelSeg - 1) / kTwoLevelSeg : 0;
+}
+
+// Two-level solve of the unit-diagonal reduced systems (R2 = 2P rows, NR right-hand sides) of the
+// lines of a block, in place: the solution replaces the right-hand sides. Line j's system sits at
+// red + j * pitch as sub[R2], sup[R2], rhs[NR][R2]. One thread per line over 2P rows is a chain
+// of 2P dependent reciprocals, and a dependent FP64 operation of one thread takes about 85 cycles
+// on GB300 (a 512-row system: about 150 us). Level 1: the rows are cut into G segments of
+// kTwoLevelSeg rows, one thread per segment, each reduced to its two end rows by the modified
+// Thomas sweep of Stage A (unit diagonal); level 2: one thread per line solves the 2G end rows
+// (kept after the Lr line regions); level 1 back: each segment's interior from its two end
+// values. Thread q * Lr + j works on segment q of line j; lines j >= lines_valid are skipped;
+// every thread of the block must call this.
+template <class CT, int NR>
+TDMA_DEV void reduced_two_level(CT* red, int pitch, int Lr, int lines_valid, int R2, DevStatus* st) {
+  constexpr int S = kTwoLevelSeg;
+  const int G = (R2 + S - 1) / S, tid = threadIdx.x;
+  const int j = tid % Lr, q = tid / Lr;
+  const bool act = q < G && j < lines_valid;
+  CT* r_sub = red + (size_t)j * pitch;
+  CT* r_sup = r_sub + R2;
+  CT* r_rhs = r_sup + R2;
+  CT* s2 = red + (size_t)Lr * pitch + (size_t)j * (2 + NR) * 2 * G;  // level-2 rows of line j
+  CT* c2 = s2 + 2 * G;
+  CT* h2 = c2 + 2 * G;  // NR blocks of 2G
+  const int r0 = q * S, len = R2 - r0 < S ? R2 - r0 : S;
+  bool ok = true;
+  if (act) {
+    const CT sub0 = r_sub[r0], sup0 = r_sup[r0];
+    CT h0[NR], delta[NR], F[NR];
+    CT alpha = CT(-1), gamma = CT(0), Gs = CT(0), Q = CT(1);
+#pragma unroll
+    for (int e = 0; e < NR; ++e) { h0[e] = r_rhs[e * R2 + r0]; delta[e] = CT(0); F[e] = CT(0); }
+    for (int t = 1; t < len; ++t) {
+      const int i = r0 + t;
+      const CT sb = r_sub[i], c = r_sup[i];
+      const CT r = rcp(CT(1) - sb * gamma);
+      ok &= finite(r);
+      const CT ar = sb * r;
+      alpha = -ar * alpha;
+      gamma = c * r;
+#pragma unroll
+      for (int e = 0; e < NR; ++e) delta[e] = r * r_rhs[e * R2 + i] - ar * delta[e];
+      if (t <= len - 2) {
+        r_sub[i] = alpha;
+        r_sup[i] = gamma;
+#pragma unroll
+        for (int e = 0; e < NR; ++e) {
+          r_rhs[e * R2 + i] = delta[e];
+          F[e] += Q * delta[e];
+        }
+        Gs += Q * alpha;
+        Q = -Q * gamma;
+      }
+    }
+    const CT rho = rcp(CT(1) - sup0 * Gs);
+    ok &= finite(rho);
+    s2[2 * q] = rho * sub0;
+    c2[2 * q] = rho * sup0 * Q;
+    s2[2 * q + 1] = alpha;
+    c2[2 * q + 1] = gamma;
+#pragma unroll
+    for (int e = 0; e < NR; ++e) {
+      h2[e * 2 * G + 2 * q] = rho * (h0[e] - sup0 * F[e]);
+      h2[e * 2 * G + 2 * q + 1] = delta[e];
+    }
+  }
+  __syncthreads();
+  if (tid < lines_valid) ok &= reduced_solve<CT, NR>(s2, c2, h2, 2 * G, 2 * G);
+  __syncthreads();
+  if (act) {
+#pragma unroll
+    for (int e = 0; e < NR; ++e) {
+      const CT xf = h2[e * 2 * G + 2 * q];
+      CT xn = h2[e * 2 * G + 2 * q + 1];
+      r_rhs[e * R2 + r0] = xf;
+      r_rhs[e * R2 + r0 + len - 1] = xn;
+      for (int t = len - 2; t >= 1; --t) {
+        const int i = r0 + t;
+        xn = r_rhs[e * R2 + i] - r_sub[i] * xf - r_sup[i] * xn;
+        r_rhs[e * R2 + i] = xn;
+      }
+    }
+  }
+  if (!ok) report_error(st, 5);
+}
+
 // Parallel diagonally dominant (PDD) reduced solve for partition k of P. Stage A left partition
 // j's end rows as the unit-diagonal pair
 //     sub[2j] x_{j-1,last} + x_{j,0} + sup[2j] x_{j,last} = rhs[2j],
@@ -167,7 +258,8 @@ template <class CT, int NR>
 __host__ __device__ inline size_t dc_smem_bytes(int T, int Lb, int P, int mmax) {
   const size_t slots = mmax > 2 ? (size_t)(mmax - 2) : 0;
   const size_t pitch = (size_t)(2 + NR) * 2 * P + 1;
-  return sizeof(CT) * ((2 + NR) * slots * T + (size_t)Lb * pitch);
+  const size_t level2 = (size_t)Lb * (2 + NR) * 2 * two_level_groups(2 * P);  // two-level Stage B
+  return sizeof(CT) * ((2 + NR) * slots * T + (size_t)Lb * pitch + level2);
 }
 
 constexpr int kChunk = 4;  // rows loaded ahead of the forward sweep
@@ -278,9 +370,14 @@ __global__ void __launch_bounds__(512) dc_kernel(const Args A) {
   if (A.lay.n == 1) return;  // no Stage B / C for single-unknown lines
   __syncthreads();
 
-  // ---------------- Stage B: reduced 2P-row system per line, one thread per line (exact), or
-  // the PDD interface systems, each partition's thread on its own (approximate)
-  if (!A.pdd) {
+  // ---------------- Stage B: reduced 2P-row system per line, one thread per line or in two
+  // levels above 32 rows (exact), or the PDD interface systems, each partition's thread on its
+  // own (approximate)
+  if (!A.pdd && R2 > kTwoLevelRows) {
+    const int64_t left = A.lay.n_lines - (int64_t)blockIdx.x * Lb;
+    reduced_two_level<CT, NR>(red, pitch, Lb, left < Lb ? (int)left : Lb, R2, A.st);
+    __syncthreads();
+  } else if (!A.pdd) {
     if (tid < Lb) {
       const int64_t l2 = (int64_t)blockIdx.x * Lb + tid;
       if (l2 < A.lay.n_lines) {

@@ -41,79 +41,6 @@ struct RaggedTables {
   int64_t scratch_elems;   // elements of each scratch array
 };
 
-// Reduced systems longer than this many rows are solved in two levels (below).
-constexpr int kTwoLevelRows = 32;
-constexpr int kTwoLevelSeg = 16;
-
-// Two-level solve of the unit-diagonal reduced systems (2P rows) of the cnt lines of a group, in
-// place: the solution replaces the right-hand sides. One thread per line over 2P rows is a chain
-// of 2P dependent reciprocals, and a dependent FP64 operation of one thread takes about 85 cycles
-// on GB300 (a 512-row system: about 150 us). Level 1: the rows are cut into segments of
-// kTwoLevelSeg rows, one thread per segment, and each segment is reduced to its two end rows by
-// the modified Thomas sweep of Stage A (unit diagonal); level 2: one thread per line solves the
-// 2G end rows; level 1 back: each segment's interior from its two end values. Threads q * cnt + j
-// (q < G) work on segment q of line j; all threads of the block must call this.
-template <class CT>
-TDMA_DEV void ragged_reduced_two_level(CT* red, int pitch, int cnt, int R2, DevStatus* st) {
-  constexpr int S = kTwoLevelSeg;
-  const int G = (R2 + S - 1) / S, tid = threadIdx.x;
-  const int j = tid % cnt, q = tid / cnt;
-  const bool act = q < G;
-  CT* r_sub = red + (size_t)j * pitch;
-  CT* r_sup = r_sub + R2;
-  CT* r_rhs = r_sup + R2;
-  CT* s2 = red + (size_t)cnt * pitch + (size_t)j * 6 * G;  // level-2 rows of line j
-  CT* c2 = s2 + 2 * G;
-  CT* h2 = c2 + 2 * G;
-  const int r0 = q * S, len = R2 - r0 < S ? R2 - r0 : S;
-  bool ok = true;
-  if (act) {
-    const CT sub0 = r_sub[r0], sup0 = r_sup[r0], h0 = r_rhs[r0];
-    CT alpha = CT(-1), gamma = CT(0), delta = CT(0), F = CT(0), Gs = CT(0), Q = CT(1);
-    for (int t = 1; t < len; ++t) {
-      const int i = r0 + t;
-      const CT sb = r_sub[i], c = r_sup[i], h = r_rhs[i];
-      const CT r = rcp(CT(1) - sb * gamma);
-      ok &= finite(r);
-      const CT ar = sb * r;
-      alpha = -ar * alpha;
-      gamma = c * r;
-      delta = r * h - ar * delta;
-      if (t <= len - 2) {
-        r_sub[i] = alpha;
-        r_sup[i] = gamma;
-        r_rhs[i] = delta;
-        F += Q * delta;
-        Gs += Q * alpha;
-        Q = -Q * gamma;
-      }
-    }
-    const CT rho = rcp(CT(1) - sup0 * Gs);
-    ok &= finite(rho);
-    s2[2 * q] = rho * sub0;
-    c2[2 * q] = rho * sup0 * Q;
-    h2[2 * q] = rho * (h0 - sup0 * F);
-    s2[2 * q + 1] = alpha;
-    c2[2 * q + 1] = gamma;
-    h2[2 * q + 1] = delta;
-  }
-  __syncthreads();
-  if (tid < cnt) ok &= reduced_solve<CT, 1>(s2, c2, h2, 2 * G, 2 * G);
-  __syncthreads();
-  if (act) {
-    const CT xf = h2[2 * q];
-    CT xn = h2[2 * q + 1];
-    r_rhs[r0] = xf;
-    r_rhs[r0 + len - 1] = xn;
-    for (int t = len - 2; t >= 1; --t) {
-      const int i = r0 + t;
-      xn = r_rhs[i] - r_sub[i] * xf - r_sup[i] * xn;
-      r_rhs[i] = xn;
-    }
-  }
-  if (!ok) report_error(st, 5);
-}
-
 template <class CT, bool TR = false>
 __global__ void __launch_bounds__(kRaggedThreads) ragged_dc_kernel(const Args A, const RaggedTables RT) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -191,7 +118,7 @@ __global__ void __launch_bounds__(kRaggedThreads) ragged_dc_kernel(const Args A,
     // ---- Stage B: one thread per line, or two levels for long reduced systems (the group's
     // lines all have P > 16 partitions, so n > 1)
     if (R2 > kTwoLevelRows) {
-      ragged_reduced_two_level<CT>(red, pitch, cnt, R2, A.st);
+      reduced_two_level<CT, 1>(red, pitch, cnt, cnt, R2, A.st);
     } else if (tid < cnt && n > 1) {
       if (!reduced_solve<CT, 1>(r_sub, r_sup, r_rhs, R2, R2)) report_error(A.st, 5);
     }
