@@ -42,7 +42,7 @@ struct RaggedTables {
 };
 
 template <class CT, bool TR = false>
-__global__ void __launch_bounds__(kRaggedThreads) ragged_dc_kernel(const Args A, const RaggedTables RT) {
+__global__ void __launch_bounds__(kRaggedThreads, 3) ragged_dc_kernel(const Args A, const RaggedTables RT) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   CT* red = reinterpret_cast<CT*>(smem_raw);
   __shared__ int s_g;
