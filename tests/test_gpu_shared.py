@@ -208,3 +208,42 @@ def test_shared_singular_pivot_sets_status():
     plan.solve(a, b, c, d, x)
     assert plan.last_error()[0] == 5
     assert plan.last_error()[0] == 0
+
+
+@pytest.mark.parametrize("axis", [0, 2])
+def test_factorisation_over_several_chunks(axis):
+    # 5000 rows: the factorisation runs over three chunks of staged coefficients, each cut into
+    # 32 segments whose start values are estimated and then made exact by passes
+    n = 5000
+    a, b, c = _coefficients(n, 90)
+    shape = (n, 40, 1) if axis == 0 else (1, 70, n)
+    d = _rhs(shape, 91, torch.float64, 1)
+    plan = _plan(d, axis, "f64", 1)
+    assert plan.config["variant"] == SHARED
+    x = torch.empty_like(d)
+    plan.solve(a, b, c, d, x)
+    assert plan.last_error()[0] == 0
+    assert O.rel_l2(_lines(x, axis, 1), _oracle(a, b, c, d, axis, 1)) <= 1e-12
+
+
+@pytest.mark.parametrize("diag", [2.0001, 2.5])
+def test_factorisation_equals_the_serial_recurrence(diag):
+    # tridiag(-1, diag, -1) over 4100 rows: on the weakly dominant line the segment estimates
+    # are far off and many passes run; either way the factors are those of the serial recurrence,
+    # so the solve agrees with the per-line Thomas kernel to rounding of the same operations
+    n, L = 4100, 256
+    a = torch.full((n,), -1.0, dtype=torch.float64, device="cuda")
+    b = torch.full((n,), diag, dtype=torch.float64, device="cuda")
+    d = _rhs((n, L), 92, torch.float64, 1)
+    p1 = _plan(d, 0, "f64", 1)
+    os.environ["TDMA_DISABLE_SHARED"] = "1"
+    try:
+        p2 = _plan(d, 0, "f64", 1)
+    finally:
+        del os.environ["TDMA_DISABLE_SHARED"]
+    assert (p1.config["variant"], p2.config["variant"]) == (SHARED, THOMAS)
+    x1, x2 = torch.empty_like(d), torch.empty_like(d)
+    p1.solve(a, b, a, d, x1)
+    p2.solve(a, b, a, d, x2)  # the per-line Thomas kernel on the same broadcast coefficients
+    torch.cuda.synchronize()
+    assert O.rel_l2(x1.cpu().numpy(), x2.cpu().numpy()) <= 1e-15
