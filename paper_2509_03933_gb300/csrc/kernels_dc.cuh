@@ -262,7 +262,7 @@ __host__ __device__ inline size_t dc_smem_bytes(int T, int Lb, int P, int mmax) 
   return sizeof(CT) * ((2 + NR) * slots * T + (size_t)Lb * pitch + level2);
 }
 
-constexpr int kChunk = 4;  // rows loaded ahead of the forward sweep
+constexpr int kChunk = 2;  // rows loaded ahead of the forward sweep
 
 // GS: the per-row Stage A scratch lives in the workspace (a [slot][thread] region per block)
 // instead of shared memory, for partitions too long to keep enough threads per SM on chip.
