@@ -22,7 +22,7 @@
 namespace tdma {
 
 constexpr int kSharedBlock = 128;
-constexpr int kSharedAhead = 8;   // rows in flight per thread in the stream kernel
+constexpr int kSharedAhead = 4;   // rows in flight per thread in the stream kernel
 constexpr int kStageElems = 16;   // elements per line per chunk in the staged kernel (34 KB per
                                   // block: 6 blocks per SM; 32 elements held 3)
 constexpr int kStagePitch = 17;   // odd pitch: lane j's row of the chunk falls in its own banks
