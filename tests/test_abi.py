@@ -65,3 +65,44 @@ def test_line_layout_of_grid_axes():
     assert tdma.line_layout(g, 2) == (6, 20, 1, 20, 6, 0)         # x lines: merged (z, y)
     c = torch.empty(4, 5, 6, 2)
     assert tdma.line_layout(c, 0, nrhs=2) == (4, 30, 30, 30, 1, 0)
+
+
+def test_poisson_descriptor_validation_on_the_host():
+    import numpy as np
+    lib = tdma.load_library()
+    coef = np.ones(8)
+    ptr = coef.ctypes.data
+
+    def create(**kw):
+        base = dict(nx=8, ny=8, nz=4, dx=1.0, dz=1.0, a=ptr, b=ptr, c=ptr, pin_zero_mode=1, precision=0)
+        base.update(kw)
+        h = ctypes.c_void_p()
+        ws = ctypes.c_size_t(0)
+        return lib.tdma_poisson_create(ctypes.byref(h), ctypes.byref(tdma.PoissonDesc(**base)), ctypes.byref(ws))
+
+    assert create(nx=7) == 1          # odd nx (real-to-complex transform of even length)
+    assert create(nz=1) == 1
+    assert create(ny=1) == 1
+    assert create(dx=0.0) == 1
+    assert create(a=None) == 1
+    assert create(pin_zero_mode=2) == 1
+    assert create(precision=1) == 2   # FP32 lines are not offered
+    assert lib.tdma_poisson_solve(None, None, None, None, 0, None) == 1
+    assert lib.tdma_poisson_destroy(None) == 0
+
+
+def test_slab_stage_validation_on_the_host():
+    from paper_2509_03933_gb300.split_line import SlabDesc, _bind
+    lib = _bind(tdma.load_library())
+    ok = dict(n_local=8, n_lines=10, elem_stride=10, inner_count=10, inner_stride=1, outer_stride=0, nrhs=1,
+              first=1, last=0)
+    d = SlabDesc(**ok)
+    assert lib.tdma_slab_scratch_bytes(ctypes.byref(d), 10) == 6 * 3 * 10 * 8
+    assert lib.tdma_slab_pairs_work_bytes(4, 10, 2) == 2 * 4 * 10 * 3 * 8
+    bad = SlabDesc(**dict(ok, n_local=1))
+    assert lib.tdma_slab_reduce(ctypes.byref(bad), None, None, None, None, 0, 10, None, None, None, None) == 1
+    assert lib.tdma_slab_reduce(ctypes.byref(d), None, None, None, None, 5, 10, None, None, None, None) == 1
+    assert lib.tdma_slab_reduce(ctypes.byref(d), None, None, None, None, 0, 0, None, None, None, None) == 0
+    assert lib.tdma_slab_pairs_solve(0, 10, 1, None, None, None, None, None) == 1
+    assert lib.tdma_slab_pairs_solve(2, 10, 3, None, None, None, None, None) == 1
+    assert lib.tdma_slab_finish(ctypes.byref(d), 0, 11, None, None, None, None) == 1
