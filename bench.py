@@ -456,6 +456,35 @@ def suite_poisson_fft(stream, n=1024):
     return out
 
 
+def suite_split_line(stream, n=512):
+    """The split-line stages and schedule on one rank (the multi-GPU exchange degenerates to a
+    copy): n^3 FP64 lines along z, the paper's batch-size estimator against timing every candidate
+    batch, and the fused one-partition Thomas kernel on the same problem."""
+    import oracle
+    import synth
+    import paper_2509_03933_gb300 as tdma
+    from paper_2509_03933_gb300.split_line import SlabStages, SplitLineSolver, choose_batch
+    g = synth.grid_general((n, n, n), 0, 3, device="cuda")
+    a, b, c, d = (g[k] for k in ("a", "b", "c", "d"))
+    L = n * n
+    x = torch.empty_like(d)
+    st = SlabStages(n, L, (L, L, 1, 0))
+    stage_times, measured = {}, {}
+    for batch in (L, L // 2, L // 4, L // 8):
+        sol = SplitLineSolver(st, L, batch)
+        stage_times[batch] = sol.measure_stages(a, b, c, d, x)
+        measured[batch] = _timed(lambda: sol.solve(a, b, c, d, x), 5, 3, stream)
+        del sol
+    best, est = choose_batch(L, stage_times)
+    ref = oracle.thomas(*(synth.line_view(t[:, :1, :].cpu(), 0).numpy() for t in (a, b, c, d)))
+    err = oracle.rel_l2(synth.line_view(x[:, :1, :].cpu(), 0).numpy(), ref)
+    plan = tdma.Plan(*tdma.line_layout(d, 0), partitions=1)
+    ms_thomas = _timed(lambda: plan.solve(a, b, c, d, x), 5, 3, stream)
+    return {"ms_per_solve_by_batch": measured, "estimated_ms_by_batch": est, "stage_ms_by_batch": stage_times,
+            "estimator_choice": best, "fastest_measured": min(measured, key=measured.get),
+            "rel_l2_error_first_y_row": err, "fused_thomas_ms": ms_thomas, "ranks": 1}
+
+
 def suite_ragged(stream, hbm_peak, n_lines=20000):
     """20000 lines, n log-uniform in [16, 16384], packed; FP32+refinement and FP64 in one
     persistent launch each; backward for loss = sum(w * x), w ~ N(0, 1)."""
@@ -551,6 +580,8 @@ def main():
     ap.add_argument("--no-suite", action="store_true", help="skip the other workloads")
     ap.add_argument("--only-poisson-fft", type=int, default=0, metavar="N",
                     help="run only the FFT-based Poisson solve on an N^3 grid and print it (profiling runs)")
+    ap.add_argument("--only-split-line", type=int, default=0, metavar="N",
+                    help="run only the split-line stages on one rank on an N^3 grid and print them")
     ap.add_argument("--only-adi", type=int, default=0, metavar="N",
                     help="run only the ADI workload on an N^3 grid and print it (profiling runs)")
     ap.add_argument("--only-ragged", type=int, default=0, metavar="LINES",
@@ -562,6 +593,10 @@ def main():
         return run_reference(args)
     if args.only_poisson_fft > 0:
         print(json.dumps({"poisson_fft": suite_poisson_fft(torch.cuda.current_stream(), args.only_poisson_fft)}),
+              flush=True)
+        return 0
+    if args.only_split_line > 0:
+        print(json.dumps({"split_line": suite_split_line(torch.cuda.current_stream(), args.only_split_line)}),
               flush=True)
         return 0
     if args.only_adi > 0:
@@ -684,7 +719,8 @@ def main():
         for name, fn in (("grid64_z_f64", lambda: suite_small_grid(stream, hbm_peak, lambda: _flush_l2(flushbuf))),
                          ("adi512_xyz_f64", lambda: suite_adi(stream, hbm_peak)),
                          ("poisson1024_z_complex", lambda: suite_poisson(stream, hbm_peak)),
-                         ("ragged20000", lambda: suite_ragged(stream, hbm_peak))):
+                         ("ragged20000", lambda: suite_ragged(stream, hbm_peak)),
+                         ("split_line512_1rank", lambda: suite_split_line(stream))):
             try:
                 suite[name] = fn()
             except Exception as exc:  # report, keep the headline line

@@ -103,6 +103,34 @@ class SlabStages:
         return err
 
 
+def pipeline_time(n_batches, t_a, t_x, t_c):
+    """Modelled time of the schedule of SplitLineSolver for n_batches equal batches whose stages
+    take t_a (Stage A), t_x (both exchanges and Stage B) and t_c (Stage C). The compute stream runs
+    A_0, A_1, C_0, A_2, C_1, ..., C_{nb-1} in that order; X_k starts when A_k and X_{k-1} are done;
+    C_k when X_k is done and the compute stream is free (the paper's pipelined scheduling model,
+    Section 4.2.3, for this two-stream form)."""
+    ac = xb = 0.0
+    x_end = []
+    for k in range(n_batches):
+        ac += t_a                       # A_k
+        xb = max(xb, ac) + t_x          # X_k
+        x_end.append(xb)
+        if k >= 1:
+            ac = max(ac, x_end[k - 1]) + t_c  # C_{k-1}
+    if n_batches:
+        ac = max(ac, x_end[-1]) + t_c   # C_{nb-1}
+    return ac
+
+
+def choose_batch(n_lines, stage_times):
+    """The batch size with the shortest modelled time, from per-batch stage times measured at a few
+    batch sizes ({batch: (t_a, t_x, t_c)}): the paper's estimator (Section 4.2.3), which times the
+    stages once per candidate instead of solving the whole domain with each."""
+    def est(b):
+        return pipeline_time(-(-n_lines // b), *stage_times[b])
+    return min(stage_times, key=est), {b: est(b) for b in stage_times}
+
+
 def shares(count, world):
     """Even distribution of a batch's lines over the ranks: contiguous [lo, hi) per rank."""
     return [(count * r // world, count * (r + 1) // world) for r in range(world)]
@@ -181,6 +209,45 @@ class SplitLineSolver:
         if pending is not None:
             self._finish(*pending, x)
         return x
+
+    def measure_stages(self, a, b, c, d, x, reps=3):
+        """Per-batch times (t_a, t_x, t_c) of the first batch, each stage timed alone with CUDA
+        events (median of ``reps``), the maximum over ranks. All ranks must call this."""
+        if not self.cuda:
+            raise RuntimeError("stage timing needs CUDA")
+        st, W, K, E = self.stages, self.world, self.stages.K, self.stages.E
+        cnt = min(self.batch, self.n_lines)
+        sl = self.slots[0]
+        sh = shares(cnt, W)
+        lo, hi = sh[self.rank]
+        own = hi - lo
+        stream = torch.cuda.current_stream()
+
+        def timed(fn):
+            out = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                fn()
+                e1.record(stream)
+                e1.synchronize()
+                out.append(e0.elapsed_time(e1))
+            return sorted(out)[len(out) // 2]
+
+        def exchange_and_b():
+            gath = sl["gath"][:W * own * K]
+            self._a2a(gath, sl["red"][:cnt * K], [own * K] * W, [(h - l) * K for l, h in sh])
+            ends = sl["ends"][:W * own * E]
+            st.pairs_solve(W, own, gath, ends, sl["work"])
+            self._a2a(sl["back"][:cnt * E], ends, [(h - l) * E for l, h in sh], [own * E] * W)
+
+        t_a = timed(lambda: st.reduce(a, b, c, d, 0, cnt, sl["red"], sl["scratch"]))
+        t_x = timed(exchange_and_b)
+        t_c = timed(lambda: st.finish(0, cnt, sl["back"][:cnt * E], sl["scratch"], x))
+        t = torch.tensor([t_a, t_x, t_c], dtype=torch.float64, device=self.stages.device)
+        if self.world > 1:
+            self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX, group=self.group)
+        return tuple(float(v) for v in t.tolist())
 
     def _finish(self, l0, cnt, sl, ev, x):
         with self._ctx(self.s_ac if self.cuda else None):

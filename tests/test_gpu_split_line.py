@@ -77,3 +77,28 @@ def test_singular_slab_sets_status():
     SplitLineSolver(st, L, 16).solve(*t, x)
     assert st.last_error() == 5
     assert st.last_error() == 0
+
+
+def test_batch_estimator_against_timing_every_candidate():
+    # the paper's estimator (stage times measured once per candidate batch, pipeline modelled)
+    # against timing the whole solve for every candidate, on one rank
+    from paper_2509_03933_gb300.split_line import choose_batch
+    n, L = 256, 65536
+    a, b, c, d = _problem(n, L, 1, 77)
+    t = [torch.from_numpy(v).cuda() for v in (a, b, c, d)]
+    x = torch.zeros_like(t[3])
+    st = SlabStages(n, L, (L, L, 1, 0))
+    stage_times, measured = {}, {}
+    for batch in (L, L // 4, L // 16):
+        sol = SplitLineSolver(st, L, batch)
+        stage_times[batch] = sol.measure_stages(*t, x)
+        sol.solve(*t, x)  # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        sol.solve(*t, x)
+        e1.record()
+        e1.synchronize()
+        measured[batch] = e0.elapsed_time(e1)
+    best, est = choose_batch(L, stage_times)
+    assert measured[best] <= 1.5 * min(measured.values())
+    assert O.rel_l2(x.cpu().numpy(), _ref(a, b, c, d, 1)) <= 1e-12

@@ -140,3 +140,24 @@ def test_even_shares_cover_every_line_once():
             assert sh[0][0] == 0 and sh[-1][1] == count
             assert all(sh[i][1] == sh[i + 1][0] for i in range(W - 1))
             assert max(h - l for l, h in sh) - min(h - l for l, h in sh) <= 1
+
+
+def test_pipeline_model():
+    from paper_2509_03933_gb300.split_line import pipeline_time, choose_batch
+    # no exchange cost: the compute stream runs every A and C back to back
+    assert pipeline_time(4, 1.0, 0.0, 1.0) == 8.0
+    # exchange-bound: one A, then the exchanges back to back, then one C
+    assert pipeline_time(3, 1.0, 5.0, 1.0) == 17.0
+    # one batch: nothing overlaps
+    assert pipeline_time(1, 2.0, 3.0, 4.0) == 9.0
+    assert pipeline_time(0, 1.0, 1.0, 1.0) == 0.0
+    # balanced stages: A_{k+1} and C_{k-1} hide X_k
+    assert pipeline_time(5, 1.0, 2.0, 1.0) == 1.0 + 5 * 2.0 + 1.0
+    # the estimator weighs per-batch costs that do not shrink with the batch (launch latency,
+    # exchange latency) against the tail of an underfilled pipeline
+    L = 1024
+    times = {b: (0.02 + b * 1e-3, 0.05 + b * 4e-4, 0.01 + b * 5e-4) for b in (16, 64, 256, 1024)}
+    best, est = choose_batch(L, times)
+    assert best == min(est, key=est.get)
+    assert est[1024] == pytest.approx(sum(times[1024]))  # one batch: the plain sum
+    assert best != 1024 and best != 16
