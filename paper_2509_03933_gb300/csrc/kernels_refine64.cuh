@@ -48,48 +48,108 @@ __global__ void __launch_bounds__(256) residual_exact_kernel(const Args A, float
 }
 
 // The FP32 correction A32 dx = r (A32: coefficients truncated to float) and x += dx, one thread
-// per line: forward elimination over R in place (c' to cw), back substitution into x.
+// per line: forward elimination over R in place (c' to cw), back substitution into x. Rows are
+// loaded kCorrAhead ahead of the recurrence in both sweeps (the loads of later rows are issued
+// before this row's stores, which the compiler may not reorder across: R, cw and x may alias).
+constexpr int kCorrAhead = 4;
+
 template <int NR>
 __global__ void __launch_bounds__(128) correction32_kernel(const Args A, float* __restrict__ cw, float* __restrict__ R) {
+  constexpr int K = kCorrAhead;
   const int64_t line = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (line >= A.lay.n_lines) return;
   const int64_t n = A.lay.n, es = A.lay.es, L = A.lay.n_lines;
   const int64_t base = A.lay.off(line);
   const double shift = A.shift ? ldg((const double*)A.shift + line) : 0.0;
   double* X = (double*)A.x;
+  float* Rl = R + line * NR;   // row i at Rl[i * L * NR + q]
+  float* cwl = cw + line;      // row i at cwl[i * L]
   float cp = 0.f, rp[NR];
 #pragma unroll
   for (int q = 0; q < NR; ++q) rp[q] = 0.f;
-  for (int64_t i = 0; i < n; ++i) {
-    const int64_t ci = A.bcast ? i : base + i * es;
-    const float a32 = i > 0 ? f64_to_f32_trunc(ldg((const double*)A.a + ci)) : 0.f;
-    const float b32 = f64_to_f32_trunc(ldg((const double*)A.b + ci) + shift);
-    const float c32 = i < n - 1 ? f64_to_f32_trunc(ldg((const double*)A.c + ci)) : 0.f;
-    const float w = rcp(fmaf(-a32, cp, b32));
-    cp = c32 * w;
-    cw[i * L + line] = cp;
+  float rb[K][NR];
 #pragma unroll
-    for (int q = 0; q < NR; ++q) {
-      float* r = R + (i * L + line) * NR + q;
-      rp[q] = fmaf(-a32, rp[q], *r) * w;
-      *r = rp[q];
+  for (int u = 0; u < K; ++u)
+    if (u < n) {
+#pragma unroll
+      for (int q = 0; q < NR; ++q) rb[u][q] = Rl[(int64_t)u * L * NR + q];
     }
+  for (int64_t i0 = 0; i0 < n; i0 += K) {
+    float nb[K][NR];
+#pragma unroll
+    for (int u = 0; u < K; ++u)
+      if (i0 + K + u < n) {
+#pragma unroll
+        for (int q = 0; q < NR; ++q) nb[u][q] = Rl[(i0 + K + u) * L * NR + q];
+      }
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+      const int64_t i = i0 + u;
+      if (i < n) {
+        const int64_t ci = A.bcast ? i : base + i * es;
+        const float a32 = i > 0 ? f64_to_f32_trunc(ldg((const double*)A.a + ci)) : 0.f;
+        const float b32 = f64_to_f32_trunc(ldg((const double*)A.b + ci) + shift);
+        const float c32 = i < n - 1 ? f64_to_f32_trunc(ldg((const double*)A.c + ci)) : 0.f;
+        const float w = rcp(fmaf(-a32, cp, b32));
+        cp = c32 * w;
+        cwl[i * L] = cp;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          rp[q] = fmaf(-a32, rp[q], rb[u][q]) * w;
+          Rl[i * L * NR + q] = rp[q];
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < K; ++u)
+#pragma unroll
+      for (int q = 0; q < NR; ++q) rb[u][q] = nb[u][q];
   }
+  // back substitution from row n-1 (dn = its d') down to row 0, rows K ahead
   float dn[NR];
   bool ok = true;
 #pragma unroll
   for (int q = 0; q < NR; ++q) dn[q] = rp[q];
-  for (int64_t i = n - 1; i >= 0; --i) {
-    const int64_t e = base + i * es;
-    if (i < n - 1) {
-      const float cpi = cw[i * L + line];
-#pragma unroll
-      for (int q = 0; q < NR; ++q) dn[q] = fmaf(-cpi, dn[q], R[(i * L + line) * NR + q]);
-    }
+  float cb[K], db[K][NR];
+  double xb[K][NR];
+  auto load_row = [&](int64_t i, float& c, float* d, double* xv) {
+    c = i < n - 1 ? cwl[i * L] : 0.f;
 #pragma unroll
     for (int q = 0; q < NR; ++q) {
-      ok &= isfinite(dn[q]);
-      X[e * NR + q] += f2d_fast(dn[q]);
+      d[q] = Rl[i * L * NR + q];
+      xv[q] = X[(base + i * es) * NR + q];
+    }
+  };
+#pragma unroll
+  for (int u = 0; u < K; ++u)
+    if (n - 1 - u >= 0) load_row(n - 1 - u, cb[u], db[u], xb[u]);
+  for (int64_t i0 = n - 1; i0 >= 0; i0 -= K) {
+    float nc[K], nd[K][NR];
+    double nx[K][NR];
+#pragma unroll
+    for (int u = 0; u < K; ++u)
+      if (i0 - K - u >= 0) load_row(i0 - K - u, nc[u], nd[u], nx[u]);
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+      const int64_t i = i0 - u;
+      if (i >= 0) {
+        const int64_t e = base + i * es;
+#pragma unroll
+        for (int q = 0; q < NR; ++q) {
+          if (i < n - 1) dn[q] = fmaf(-cb[u], dn[q], db[u][q]);
+          ok &= isfinite(dn[q]);
+          X[e * NR + q] = xb[u][q] + f2d_fast(dn[q]);
+        }
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+      cb[u] = nc[u];
+#pragma unroll
+      for (int q = 0; q < NR; ++q) {
+        db[u][q] = nd[u][q];
+        xb[u][q] = nx[u][q];
+      }
     }
   }
   if (!ok) report_error(A.st, 5);
