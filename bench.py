@@ -456,6 +456,34 @@ def suite_poisson_fft(stream, n=1024):
     return out
 
 
+def suite_x_axis(stream, hbm_peak, n=1024):
+    """The precision workload along the unit-stride x axis: general FP32-representable coefficients
+    on an n^3 grid (seed 3), lines along x, FP32 + refinement and FP64, errors against the oracle on
+    the lines of the first four z-planes."""
+    import oracle
+    import synth
+    import paper_2509_03933_gb300 as tdma
+    g = synth.grid_general((n, n, n), 2, SEED, device="cuda", fp32_coefficients=True)
+    g.pop("x_true")
+    d = g["d"]
+    x = torch.empty_like(d)
+    U = n ** 3
+    out = {}
+    sample = lambda t: synth.line_view(t[:4].double().cpu(), 2).numpy()
+    ref = oracle.thomas(*(sample(g[k]) for k in ("a32", "b32", "c32")), sample(d))
+    for prec, keys, nbytes in (("f32r", ("a32", "b32", "c32"), BYTES_F32R), ("f64", ("a", "b", "c"), BYTES_F64)):
+        plan = tdma.Plan(*tdma.line_layout(d, 2), precision=prec)
+        coef = tuple(g[k] for k in keys)
+        ms = _timed(lambda: plan.solve(*coef, d, x), 10, 3, stream)
+        out[prec] = {"ms_per_solve": ms, "unknowns_per_s": U / (ms * 1e-3),
+                     "hbm_frac": nbytes * U / (ms * 1e-3) / 1e9 / hbm_peak,
+                     "rel_l2_error": oracle.rel_l2(sample(x), ref), "status": plan.last_error()[0],
+                     "plan": plan.config}
+        del plan
+    out["l2"] = "inputs larger than L2"
+    return out
+
+
 def suite_split_line(stream, n=512):
     """The split-line stages and schedule on one rank (the multi-GPU exchange degenerates to a
     copy): n^3 FP64 lines along z, the paper's batch-size estimator against timing every candidate
@@ -582,6 +610,8 @@ def main():
                     help="run only the FFT-based Poisson solve on an N^3 grid and print it (profiling runs)")
     ap.add_argument("--only-split-line", type=int, default=0, metavar="N",
                     help="run only the split-line stages on one rank on an N^3 grid and print them")
+    ap.add_argument("--only-x-axis", type=int, default=0, metavar="N",
+                    help="run only the x-axis precision workload on an N^3 grid and print it")
     ap.add_argument("--only-adi", type=int, default=0, metavar="N",
                     help="run only the ADI workload on an N^3 grid and print it (profiling runs)")
     ap.add_argument("--only-ragged", type=int, default=0, metavar="LINES",
@@ -597,6 +627,11 @@ def main():
         return 0
     if args.only_split_line > 0:
         print(json.dumps({"split_line": suite_split_line(torch.cuda.current_stream(), args.only_split_line)}),
+              flush=True)
+        return 0
+    if args.only_x_axis > 0:
+        hbm_peak, _ = peaks()
+        print(json.dumps({"x_axis": suite_x_axis(torch.cuda.current_stream(), hbm_peak, args.only_x_axis)}),
               flush=True)
         return 0
     if args.only_adi > 0:
@@ -720,7 +755,8 @@ def main():
                          ("adi512_xyz_f64", lambda: suite_adi(stream, hbm_peak)),
                          ("poisson1024_z_complex", lambda: suite_poisson(stream, hbm_peak)),
                          ("ragged20000", lambda: suite_ragged(stream, hbm_peak)),
-                         ("split_line512_1rank", lambda: suite_split_line(stream))):
+                         ("split_line512_1rank", lambda: suite_split_line(stream)),
+                         ("x_axis1024_f32r_f64", lambda: suite_x_axis(stream, hbm_peak))):
             try:
                 suite[name] = fn()
             except Exception as exc:  # report, keep the headline line

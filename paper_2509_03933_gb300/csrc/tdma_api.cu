@@ -766,6 +766,8 @@ tdma_status_t build_ragged(tdma_plan_s* p) {
 // ordered longest first. Leaves the plan unchanged (returns false) when the batch does not
 // qualify: other precisions, a line longer than a chunk, overlapping lines, or
 // TDMA_DISABLE_PACKED=1.
+bool build_packed_tables(tdma_plan_s* p, const std::vector<int64_t>& off, const std::vector<int32_t>& len);
+
 bool build_packed(tdma_plan_s* p) {
   const tdma_desc_t& d = p->desc;
   if (const char* e = std::getenv("TDMA_DISABLE_PACKED")) if (e[0] == '1') return false;
@@ -777,6 +779,27 @@ bool build_packed(tdma_plan_s* p) {
   if (cudaMemcpy(len.data(), d.ragged_lengths, sizeof(int32_t) * L, cudaMemcpyDeviceToHost) != cudaSuccess ||
       cudaMemcpy(off.data(), d.ragged_offsets, sizeof(int64_t) * L, cudaMemcpyDeviceToHost) != cudaSuccess)
     return false;
+  return build_packed_tables(p, off, len);
+}
+
+// Uniform lines with unit element stride in FP32 + refinement: the same chunk kernel, with the
+// line offsets off(l) computed here (whole contiguous lines form the chunks; a gap between lines
+// ends a chunk). Taken when the plan chooses its own configuration.
+bool build_packed_uniform(tdma_plan_s* p) {
+  const tdma_desc_t& d = p->desc;
+  if (const char* e = std::getenv("TDMA_DISABLE_PACKED")) if (e[0] == '1') return false;
+  if (d.precision != TDMA_F32_REFINE || d.nrhs != 1 || d.coef_broadcast || d.diag_shift || d.elem_stride != 1 ||
+      d.partitions != 0 || d.n_lines < 1 || d.n > kPackChunk || d.n_lines >= (1ll << 31))
+    return false;
+  const int64_t L = d.n_lines;
+  std::vector<int32_t> len((size_t)L, (int32_t)d.n);
+  std::vector<int64_t> off((size_t)L);
+  for (int64_t l = 0; l < L; ++l) off[l] = (l / d.inner_count) * d.outer_stride + (l % d.inner_count) * d.inner_stride;
+  return build_packed_tables(p, off, len);
+}
+
+bool build_packed_tables(tdma_plan_s* p, const std::vector<int64_t>& off, const std::vector<int32_t>& len) {
+  const int64_t L = (int64_t)off.size();
   std::vector<int32_t> order((size_t)L);
   for (int64_t i = 0; i < L; ++i) order[i] = (int32_t)i;
   std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return off[x] < off[y]; });
@@ -977,7 +1000,8 @@ void remember_config(const tdma_desc_t& d, const tdma_config_t& c) {
 tdma_status_t autotune_impl(tdma_plan_s* p, const void* a, const void* b, const void* c, const void* d, void* x,
                             void* ws, size_t ws_bytes, cudaStream_t s) {
   if (p->desc.n == 0 || p->desc.n_lines == 0 || p->desc.pdd) return TDMA_OK;
-  const auto cands = tune_candidates(p->desc, p->allow_tma);
+  auto cands = tune_candidates(p->desc, p->allow_tma);
+  if (p->cfg.variant == TDMA_VARIANT_PACKED) cands.insert(cands.begin(), p->cfg);  // the plan's own chunk tables
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TDMA_ERR_CUDA;
   const tdma_config_t keep = p->cfg;
@@ -1083,7 +1107,10 @@ tdma_status_t tdma_plan_create(tdma_plan_t* plan, const tdma_desc_t* desc, size_
     p->workspace = workspace_for(*desc, c);
   } else if (is_uniform(*desc)) {
     bool ok = false;
-    if (desc->precision == TDMA_F32_REFINE) {
+    if (desc->precision == TDMA_F32_REFINE && build_packed_uniform(p)) {
+      c = p->cfg;  // unit-stride lines: the chunk kernel over whole contiguous lines
+      ok = true;
+    } else if (desc->precision == TDMA_F32_REFINE) {
       ok = p->allow_tma && (refine_tree_config(*desc, desc->partitions, c) ||
                             refine_cluster_config(*desc, desc->partitions, c));
       if (!ok) {

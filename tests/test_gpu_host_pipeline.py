@@ -3,6 +3,7 @@ staging slots on several streams must give exactly the on-device solve of the wh
 import pytest
 import torch
 
+import oracle as O
 import synth
 import paper_2509_03933_gb300 as tdma
 
@@ -29,8 +30,13 @@ def test_pipeline_matches_device_solve(precision, axis):
     hx = torch.empty(d.shape, dtype=d.dtype).pin_memory()
     pipe.solve(*h, hx)
     torch.cuda.synchronize()
-    # a slice solves whole lines with the same kernels as the full grid: identical results
-    assert torch.equal(hx, x_dev.cpu())
+    # a slice solves whole lines with the same kernels as the full grid: identical results, except
+    # for FP32 + refinement along the contiguous axis, where the chunk kernel cuts the lines it is
+    # given into chunks (a slice's chunks differ from the full grid's): equal to rounding there
+    if precision == "f32r" and axis == 2:
+        assert O.rel_l2(hx.numpy(), x_dev.cpu().numpy()) <= 1e-14
+    else:
+        assert torch.equal(hx, x_dev.cpu())
     assert pipe.plan.last_error()[0] == 0
 
 

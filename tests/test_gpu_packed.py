@@ -225,3 +225,24 @@ def test_packed_backward_second_correction():
         s = slice(o[l], o[l] + n[l])
         at, bt, ct = O.transpose_coefficients(h(a)[s], h(b)[s], h(c)[s])
         assert O.rel_l2(h(g[3])[s], O.thomas_ext(at, bt, ct, h(w)[s])) <= 1e-12
+
+
+@pytest.mark.parametrize("n,L,gap", [(1024, 300, 0), (CHUNK_ROWS, 3, 0), (5000, 40, 16), (37, 2000, 0), (2, 9, 3)])
+def test_uniform_unit_stride_lines_use_the_chunk_kernel(n, L, gap):
+    # uniform lines along the contiguous axis in FP32 + refinement: whole contiguous lines form
+    # the chunks (a gap between lines ends a chunk); x between the lines stays untouched
+    g = synth.grid_general((L, n + gap), 1, 20 + n, device="cuda", fp32_coefficients=True)
+    a, b, c = (g[k][:, :n] for k in ("a32", "b32", "c32"))
+    d = g["d"][:, :n]
+    plan = tdma.Plan(*tdma.line_layout(d, 1), precision="f32r")
+    assert plan.config["variant"] == PACKED
+    x = torch.full((L, n + gap), 7.0, dtype=torch.float64, device="cuda")
+    plan.solve(a, b, c, d, x[:, :n])
+    assert plan.last_error()[0] == 0
+    ref = O.thomas(*(t.double().cpu().numpy() for t in (a, b, c, d)))
+    assert O.rel_l2(x[:, :n].cpu().numpy(), ref) <= 1e-12
+    if gap:
+        assert bool((x[:, n:] == 7.0).all())
+    if n <= 5000:  # explicit partitions keep the partition kernels
+        fixed = tdma.Plan(*tdma.line_layout(d, 1), precision="f32r", partitions=1 if n < 4 else 2)
+        assert fixed.config["variant"] != PACKED
