@@ -22,6 +22,7 @@
 #include "kernels_ragged.cuh"
 #include "kernels_packed.cuh"
 #include "kernels_shared.cuh"
+#include "kernels_thomas_staged.cuh"
 #include "kernels_backward.cuh"
 #include "kernels_refine64.cuh"
 
@@ -512,6 +513,7 @@ cudaError_t launch_forward(const tdma_plan_s* p, const Args& A, cudaStream_t s) 
       return cudaErrorInvalidValue;
     }
     case TDMA_VARIANT_THOMAS:
+      if (A.lay.es == 1) return launch_thomas_staged(p->desc.precision, p->desc.nrhs, A, s);  // contiguous lines
       return launch_thomas(p->desc.precision, p->desc.nrhs, A, c, s);
     case TDMA_VARIANT_SHARED:
       return launch_shared_any(p->desc.precision, p->desc.nrhs, false, A, s);
@@ -582,6 +584,7 @@ cudaError_t prepare_kernel(const tdma_plan_s* p) {
       return cudaErrorInvalidValue;
     }
     case TDMA_VARIANT_THOMAS:
+      if (p->desc.elem_stride == 1) return prepare_thomas_staged(p->desc.precision, p->desc.nrhs);
       return prepare_thomas(p->desc.precision, p->desc.nrhs, sm);
     case TDMA_VARIANT_SHARED:
       return prepare_shared(p->desc.precision, p->desc.nrhs);
