@@ -13,7 +13,7 @@
 namespace tdma {
 
 constexpr int kTsWarps = 2;   // warps per block
-constexpr int kTsRows = 16;   // rows per chunk
+constexpr int kTsRows = 8;    // rows per chunk
 constexpr int kTsPitchC = kTsRows + 1;  // odd pitches: lane j's row of a tile in its own banks
 
 template <int NR> __host__ __device__ constexpr int ts_pitch_d() { return kTsRows * NR + 1; }
