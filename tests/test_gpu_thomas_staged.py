@@ -1,5 +1,5 @@
 """The one-partition Thomas sweep on unit-stride lines (staged through shared memory in chunks of
-16 rows, 32 lines per warp) against the oracle: both precisions, one and two right-hand sides,
+8 rows, 32 lines per warp) against the oracle: both precisions, one and two right-hand sides,
 line lengths with a partial last chunk, line counts that leave a warp partly empty, gaps between
 lines, and x written over d."""
 import numpy as np
