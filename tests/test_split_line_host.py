@@ -77,6 +77,33 @@ class SpikeStages:
         x[:, line0:line0 + count] = torch.from_numpy(sol.T.copy())
 
 
+class WideRecords(SpikeStages):
+    """The same stages with two right-hand sides' worth of record size (K = 8, E = 4): the extra
+    values are filler the stages write and check, so the schedule's record bookkeeping is tested
+    for sizes other than the first."""
+
+    K, E = 8, 4
+
+    def reduce(self, a, b, c, d, line0, count, red, scratch):
+        tmp = torch.zeros(count * 6, dtype=torch.float64)
+        super().reduce(a, b, c, d, line0, count, tmp, scratch)
+        rec = torch.cat([tmp.view(count, 6), torch.full((count, 2), 7.0, dtype=torch.float64)], dim=1)
+        red[:count * 8] = rec.reshape(-1)
+
+    def pairs_solve(self, W, count, gathered, ends, work):
+        g = gathered[:W * count * 8].view(W, count, 8)
+        assert bool((g[..., 6:] == 7.0).all())
+        out = torch.zeros(W * count * 2, dtype=torch.float64)
+        super().pairs_solve(W, count, g[..., :6].reshape(-1).clone(), out, work)
+        e = torch.cat([out.view(W, count, 2), torch.full((W, count, 2), -3.0, dtype=torch.float64)], dim=2)
+        ends[:W * count * 4] = e.reshape(-1)
+
+    def finish(self, line0, count, ends, scratch, x):
+        e = ends.view(count, 4)
+        assert bool((e[:, 2:] == -3.0).all())
+        super().finish(line0, count, e[:, :2].reshape(-1).clone(), scratch, x)
+
+
 def _problem(n, L, seed=12):
     rng = np.random.default_rng(seed)
     a = rng.uniform(-1, 0, (n, L))
@@ -96,7 +123,7 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _worker(rank, world, port, n, L, batch, q):
+def _worker(rank, world, port, n, L, batch, q, wide=False):
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     dist.init_process_group("gloo", rank=rank, world_size=world)
     try:
@@ -105,19 +132,20 @@ def _worker(rank, world, port, n, L, batch, q):
         r0, r1 = _rows(n, world, rank)
         slab = [torch.from_numpy(t[r0:r1].copy()) for t in (a, b, c, d)]
         x = torch.zeros_like(slab[3])
-        st = SpikeStages(r1 - r0, L, rank == 0, rank == world - 1)
+        st = (WideRecords if wide else SpikeStages)(r1 - r0, L, rank == 0, rank == world - 1)
         SplitLineSolver(st, L, batch).solve(*slab, x)
         q.put((rank, r0, x.numpy()))
     finally:
         dist.destroy_process_group()
 
 
-@pytest.mark.parametrize("world,n,L,batch", [(2, 40, 50, 16), (3, 31, 37, 8), (2, 8, 5, 64), (3, 12, 2, 1)])
-def test_split_line_schedule_on_gloo_ranks(world, n, L, batch):
+@pytest.mark.parametrize("world,n,L,batch,wide", [(2, 40, 50, 16, False), (3, 31, 37, 8, False),
+                                                  (2, 8, 5, 64, False), (3, 12, 2, 1, False), (3, 20, 23, 5, True)])
+def test_split_line_schedule_on_gloo_ranks(world, n, L, batch, wide):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_worker, args=(r, world, port, n, L, batch, q)) for r in range(world)]
+    procs = [ctx.Process(target=_worker, args=(r, world, port, n, L, batch, q, wide)) for r in range(world)]
     for p in procs:
         p.start()
     res = [q.get(timeout=180) for _ in procs]
