@@ -53,15 +53,17 @@ struct PackedChunk {
   int32_t M;      // rows per partition: partition k holds rows [k M, min((k + 1) M, rows))
   int32_t line0;  // position, in memory order, of the chunk's first line (its norm slot)
   int32_t nlines; // lines in the chunk
+  int32_t meta;   // block of the partition metadata (chunks of the same structure share one)
+  int32_t pad;
 };
 
-// Partition metadata (one pair of words per partition of every chunk):
+// Partition metadata (one pair of words per partition of every distinct chunk structure):
 //   x bits 0..19  bit t: row t of the partition starts a line
 //   x bit 20      the row after the partition's last row starts a line or lies past the chunk
 //   y             line of the partition's first row, counted from the chunk's first line
 struct PackedTables {
   const PackedChunk* chunks;
-  const uint2* meta;      // kPackC * kPackT pairs per chunk
+  const uint2* meta;      // kPackC * kPackT pairs per distinct chunk structure
   uint32_t* norms;        // kPackNormWords per line in memory order (see packed_first_verdict)
   int32_t n_chunks;
 };
@@ -600,7 +602,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
     const int seg0 = rank * kPackT * M;
     const int segn = max(0, min(ch.rows - seg0, kPackT * M));
     const int m = coord ? 0 : max(0, min(M, segn - tid * M));
-    const uint2 meta = coord ? make_uint2(0u, 0u) : PT.meta[(int64_t)g * (C * kPackT) + kp];
+    const uint2 meta = coord ? make_uint2(0u, 0u) : PT.meta[(int64_t)ch.meta * (C * kPackT) + kp];
     const uint32_t mask = meta.x & 0xFFFFFu;
     const int line = ch.line0 + (int)meta.y;
     // c = 0 on rows that end a line: row t ends one when row t + 1 starts one

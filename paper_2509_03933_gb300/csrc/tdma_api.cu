@@ -825,8 +825,9 @@ bool build_packed_tables(tdma_plan_s* p, const std::vector<int64_t>& off, const 
   std::stable_sort(spans.begin(), spans.end(), [](const Span& x, const Span& y) { return x.rows > y.rows; });
   constexpr int PPC = kPackC * kPackT;  // partitions per chunk
   std::vector<PackedChunk> chunks(spans.size());
-  std::vector<uint2> meta(spans.size() * (size_t)PPC);
-  std::vector<int32_t> starts;
+  std::vector<uint2> meta;  // one block of PPC pairs per distinct chunk structure
+  std::map<std::vector<int32_t>, int32_t> blocks;  // (rows, M, line starts) -> block
+  std::vector<int32_t> starts, key;
   for (size_t g = 0; g < spans.size(); ++g) {
     const Span& sp = spans[g];
     // rows per partition: the smallest compiled M with 896 M >= rows (identity rows fill the rest)
@@ -836,9 +837,20 @@ bool build_packed_tables(tdma_plan_s* p, const std::vector<int64_t>& off, const 
     TDMA_PACKED_M(TDMA_PICK_M)
 #undef TDMA_PICK_M
     if (M == 0) return false;
-    chunks[g] = PackedChunk{off[order[sp.first]], rows, M, (int32_t)sp.first, (int32_t)sp.count};
     starts.assign(1, 0);  // first row of every line of the chunk, relative to the chunk
     for (int64_t j = 1; j < sp.count; ++j) starts.push_back(starts.back() + len[order[sp.first + j - 1]]);
+    key.assign({rows, M});
+    key.insert(key.end(), starts.begin(), starts.end());
+    const auto found = blocks.find(key);
+    if (found != blocks.end()) {  // a chunk of the same structure (uniform lines): share its block
+      chunks[g] = PackedChunk{off[order[sp.first]], rows, M, (int32_t)sp.first, (int32_t)sp.count, found->second, 0};
+      continue;
+    }
+    const int32_t blk = (int32_t)blocks.size();
+    if ((int64_t)blk * PPC >= (1ll << 31)) return false;
+    blocks.emplace(key, blk);
+    meta.resize((size_t)(blk + 1) * PPC);
+    chunks[g] = PackedChunk{off[order[sp.first]], rows, M, (int32_t)sp.first, (int32_t)sp.count, blk, 0};
     size_t li = 0;  // line of the current row
     for (int k = 0; k < PPC; ++k) {
       const int r0 = k * M, r1 = std::min(rows, r0 + M);
@@ -852,7 +864,7 @@ bool build_packed_tables(tdma_plan_s* p, const std::vector<int64_t>& off, const 
       } else {
         li = starts.size() - 1;
       }
-      meta[g * PPC + k] = make_uint2(w, (uint32_t)li);
+      meta[(size_t)blk * PPC + k] = make_uint2(w, (uint32_t)li);
     }
   }
   const size_t b_chunks = sizeof(PackedChunk) * chunks.size();
