@@ -21,6 +21,16 @@ Functions and the passage each follows:
                      (Section 2.1 stages 1-5; Algorithm 1: solve the decoupled system
                      A~ x~ = d~, solve the reduced system Z y = E^T x~ of size 2p - 2
                      (Section 2.2), correct x = x~ - Y y).
+  modified_thomas_partition
+                  -- Stage A in the modified-Thomas form (Section 2.1: each partition reduced
+                     to its two end unknowns; the paper defers the stage equations to Sun 1989
+                     and to the PaScaL_TDMA form it cites): a forward sweep that keeps x_0 as a
+                     parameter, a backward sweep that expresses every row in x_0 and x_{m-1},
+                     and the elimination of x_1 from row 0.
+  reduced_system  -- the 2p-row unit-diagonal system of the partitions' end rows (the on-chip
+                     analogue of the paper's A2B step), stacked in partition order.
+  dc_modified     -- the three stages in that form: Stage A per partition, Stage B by Thomas on
+                     the reduced system, Stage C x_i = delta_i - alpha_i x_0 - gamma_i x_{m-1}.
   pdd             -- the parallel diagonally dominant (PDD) approximation the paper's
                      momentum solver uses for its diagonally dominant ADI lines (Section 5.1,
                      Section 6.2.2; Sun's method): Stage A as in dc_spike, then one 2x2 system
@@ -44,7 +54,8 @@ from __future__ import annotations
 
 import numpy as np
 
-__all__ = ["thomas", "thomas_ext", "dense_matrix", "dense_solve", "partition_rows", "dc_spike", "pdd", "poisson_fft",
+__all__ = ["thomas", "thomas_ext", "dense_matrix", "dense_solve", "partition_rows", "dc_spike",
+           "modified_thomas_partition", "reduced_system", "dc_modified", "pdd", "poisson_fft",
            "residual", "adjoint_grads", "transpose_coefficients", "thomas_ragged", "rel_l2"]
 
 
@@ -211,6 +222,135 @@ def dc_spike(a, b, c, d, p: int):
             if k < p - 1:
                 x[:, s:e] -= w[:, s:e] * y[:, 2 * (k + 1) - 1][:, None]
     return x[0] if squeeze else x
+
+
+def _rhs_row(t, i, extra):
+    """Row i of a right-hand-side array (one optional trailing RHS axis)."""
+    return t[..., i, :] if extra else t[..., i]
+
+
+def modified_thomas_partition(a, b, c, d):
+    """Stage A of one partition in the modified-Thomas form (Section 2.1, stages 1-2: each
+    partition is reduced to relations in its two end unknowns; Algorithm 1's decoupled solve).
+
+    Input: the m >= 2 rows of one partition (lines on the leading axes; d may carry one trailing
+    right-hand-side axis). a[..., 0] couples row 0 to the unknown just before the partition
+    (x_{-1}) and c[..., m-1] couples row m-1 to the one just after it (x_m); pass 0 at a line
+    end. Every row is divided by its diagonal and x_1 .. x_{m-2} are eliminated, so that
+        row 0:          alpha_0 x_{-1} + x_0 + gamma_0 x_{m-1} = delta_0
+        row i, 1..m-2:  alpha_i x_0 + x_i + gamma_i x_{m-1} = delta_i
+        row m-1:        alpha_{m-1} x_0 + x_{m-1} + gamma_{m-1} x_m = delta_{m-1}
+    Steps, in this order:
+      1. rows 0 and 1 divided by their diagonal: alpha = a / b, gamma = c / b, delta = d / b;
+      2. forward, i = 2..m-1, x_{i-1} eliminated with row i-1 (alpha_{i-1} x_0 + x_{i-1} +
+         gamma_{i-1} x_i = delta_{i-1}):  r = 1 / (b_i - a_i gamma_{i-1}),
+         alpha_i = -r a_i alpha_{i-1},  gamma_i = r c_i,  delta_i = r (d_i - a_i delta_{i-1});
+         after this step row i (i >= 1) reads alpha_i x_0 + x_i + gamma_i x_{i+1} = delta_i
+         (returned as the forward form);
+      3. backward, i = m-3 down to 1, x_{i+1} eliminated with row i+1 (already in x_0 and
+         x_{m-1}):  delta_i -= gamma_i delta_{i+1},  alpha_i -= gamma_i alpha_{i+1},
+         gamma_i = -gamma_i gamma_{i+1};
+      4. row 0, when m >= 3, x_1 eliminated with row 1:  r = 1 / (1 - gamma_0 alpha_1),
+         delta_0 = r (delta_0 - gamma_0 delta_1),  alpha_0 = r alpha_0,  gamma_0 = -r gamma_0 gamma_1.
+    Returns a dict of arrays shaped like b (delta like d): alpha, gamma, delta (the final form)
+    and alpha_fwd, gamma_fwd, delta_fwd (the forward form after step 2; row 0 as after step 1).
+    """
+    a, b, c, d = (np.asarray(t, dtype=np.float64) for t in (a, b, c, d))
+    m = b.shape[-1]
+    if m < 2:
+        raise ValueError("a partition needs at least 2 rows")
+    extra = d.ndim - b.ndim
+    if extra not in (0, 1):
+        raise ValueError("d may carry at most one trailing right-hand-side axis")
+    ex = (lambda v: v[..., None]) if extra else (lambda v: v)
+    al = np.empty(b.shape)
+    ga = np.empty(b.shape)
+    de = np.empty(d.shape)
+    for i in (0, 1):  # step 1
+        al[..., i] = a[..., i] / b[..., i]
+        ga[..., i] = c[..., i] / b[..., i]
+        de[(Ellipsis, i) + (slice(None),) * extra] = _rhs_row(d, i, extra) / ex(b[..., i])
+    for i in range(2, m):  # step 2
+        r = 1.0 / (b[..., i] - a[..., i] * ga[..., i - 1])
+        al[..., i] = -r * a[..., i] * al[..., i - 1]
+        ga[..., i] = r * c[..., i]
+        de[(Ellipsis, i) + (slice(None),) * extra] = ex(r) * (_rhs_row(d, i, extra)
+                                                              - ex(a[..., i]) * _rhs_row(de, i - 1, extra))
+    fwd = {"alpha_fwd": al.copy(), "gamma_fwd": ga.copy(), "delta_fwd": de.copy()}
+    for i in range(m - 3, 0, -1):  # step 3
+        de[(Ellipsis, i) + (slice(None),) * extra] = _rhs_row(de, i, extra) - ex(ga[..., i]) * _rhs_row(de, i + 1, extra)
+        al[..., i] = al[..., i] - ga[..., i] * al[..., i + 1]
+        ga[..., i] = -ga[..., i] * ga[..., i + 1]
+    if m >= 3:  # step 4
+        r = 1.0 / (1.0 - ga[..., 0] * al[..., 1])
+        de[(Ellipsis, 0) + (slice(None),) * extra] = ex(r) * (_rhs_row(de, 0, extra)
+                                                              - ex(ga[..., 0]) * _rhs_row(de, 1, extra))
+        al[..., 0] = r * al[..., 0]
+        ga[..., 0] = -r * ga[..., 0] * ga[..., 1]
+    out = {"alpha": al, "gamma": ga, "delta": de}
+    out.update(fwd)
+    return out
+
+
+def reduced_system(stages):
+    """The reduced system of a line split into partitions (Section 2.2; its assembly is the
+    paper's A2B step, here on one device): for partition k with Stage A result ``stages[k]``
+    (modified_thomas_partition), unknown 2k is its first unknown and 2k+1 its last; row 2k is
+    the partition's row 0 and row 2k+1 its row m-1, both with unit diagonal:
+        row 2k:    alpha_0 y_{2k-1} + y_{2k} + gamma_0 y_{2k+1} = delta_0
+        row 2k+1:  alpha_{m-1} y_{2k} + y_{2k+1} + gamma_{m-1} y_{2k+2} = delta_{m-1}
+    Returns (sub, sup, rhs) with the rows on the last axis (rhs with its trailing RHS axis).
+    """
+    sub, sup, rhs = [], [], []
+    for st in stages:
+        extra = st["delta"].ndim - st["alpha"].ndim
+        for i in (0, -1):
+            sub.append(st["alpha"][..., i])
+            sup.append(st["gamma"][..., i])
+            rhs.append(_rhs_row(st["delta"], i, extra))
+    rows_axis = -2 if rhs[0].ndim > sub[0].ndim else -1
+    return np.stack(sub, axis=-1), np.stack(sup, axis=-1), np.stack(rhs, axis=rows_axis)
+
+
+def dc_modified(a, b, c, d, p: int):
+    """Divide-and-conquer solve in the modified-Thomas form (Section 2.1's three stages):
+    Stage A, modified_thomas_partition on every partition of partition_rows(n, p) with the
+    line's a_0 and c_{n-1} set to 0; Stage B, thomas on the 2p-row reduced_system (unit
+    diagonal); Stage C, x_i = delta_i - alpha_i x_0 - gamma_i x_{m-1} inside every partition
+    (its two end unknowns taken from Stage B). Lines on the leading axes; d may carry one
+    trailing right-hand-side axis. Returns x shaped like d.
+    """
+    a, b, c, d = (np.asarray(t, dtype=np.float64) for t in (a, b, c, d))
+    n = b.shape[-1]
+    extra = d.ndim - b.ndim
+    if n == 1:
+        return d / (b[..., None] if extra else b)
+    parts = partition_rows(n, p)
+    stages = []
+    for k, (s, e) in enumerate(parts):  # Stage A
+        ak, ck = a[..., s:e].copy(), c[..., s:e].copy()
+        if k == 0:
+            ak[..., 0] = 0.0
+        if k == len(parts) - 1:
+            ck[..., -1] = 0.0
+        dk = d[..., s:e, :] if extra else d[..., s:e]
+        stages.append(modified_thomas_partition(ak, b[..., s:e], ck, dk))
+    sub, sup, rhs = reduced_system(stages)  # Stage B
+    ends = thomas(sub, np.ones(sub.shape), sup, rhs)
+    x = np.empty(d.shape)
+    ex = (lambda v: v[..., None]) if extra else (lambda v: v)
+    for k, ((s, e), st) in enumerate(zip(parts, stages)):  # Stage C
+        x0 = _rhs_row(ends, 2 * k, extra)
+        xl = _rhs_row(ends, 2 * k + 1, extra)
+        for i in range(e - s):
+            if i == 0:
+                v = x0
+            elif i == e - s - 1:
+                v = xl
+            else:
+                v = _rhs_row(st["delta"], i, extra) - ex(st["alpha"][..., i]) * x0 - ex(st["gamma"][..., i]) * xl
+            x[(Ellipsis, s + i) + (slice(None),) * extra] = v
+    return x
 
 
 def pdd(a, b, c, d, p: int):

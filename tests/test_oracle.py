@@ -207,6 +207,60 @@ def test_extended_precision_sweep_agrees_and_is_tighter():
     assert O.rel_l2(x64, xe) < 1e-10
 
 
+def _exact_thomas(a, b, c, d):
+    """The Thomas recurrences in exact rational arithmetic (every float input is a rational)."""
+    n = len(b)
+    a, b, c, d = ([Fraction(float(v)) for v in t] for t in (a, b, c, d))
+    cp, dp = [Fraction(0)] * n, [Fraction(0)] * n
+    cp[0], dp[0] = c[0] / b[0], d[0] / b[0]
+    for i in range(1, n):
+        w = b[i] - a[i] * cp[i - 1]
+        cp[i] = c[i] / w if i < n - 1 else Fraction(0)
+        dp[i] = (d[i] - a[i] * dp[i - 1]) / w
+    x = [Fraction(0)] * n
+    x[-1] = dp[-1]
+    for i in range(n - 2, -1, -1):
+        x[i] = dp[i] - cp[i] * x[i + 1]
+    return np.array([float(v) for v in x])
+
+
+def _pinned_zero_mode(n, seed):
+    from synth import poisson_coefficients
+    a, c, b = poisson_coefficients(n, 2.0)
+    b, c = b.copy(), c.copy()
+    b[0], c[0] = 1.0, 0.0
+    d = np.random.default_rng(seed).normal(size=n)
+    d[0] = 0.0
+    return a, b, c, d
+
+
+@pytest.mark.parametrize("n,seed", [(64, 1), (96, 2), (128, 3), (256, 4)])
+def test_extended_precision_is_tighter_than_fp64_against_exact_rationals(n, seed):
+    # The pinned Poisson zero mode (Neumann ends on the tanh-stretched grid, row 0 replaced by
+    # x_0 = 0) shrunk to n rows: badly conditioned enough that FP64 elimination is visibly off the
+    # exact solution, which exact rational arithmetic gives. The extended sweep must be at least
+    # 10x closer; it fails if it silently runs in float64.
+    if np.finfo(np.longdouble).nmant <= 52:
+        pytest.skip("numpy.longdouble is float64 on this platform: no extended precision to pin")
+    a, b, c, d = _pinned_zero_mode(n, seed)
+    exact = _exact_thomas(a, b, c, d)
+    e64 = O.rel_l2(O.thomas(a, b, c, d), exact)
+    eext = O.rel_l2(O.thomas_ext(a, b, c, d), exact)
+    assert e64 > 5e-15  # the case discriminates: FP64 is measurably off
+    assert eext <= e64 / 10
+    assert eext <= 4e-16  # only the final rounding to float64 is left
+
+
+def test_extended_pin_catches_a_float64_sweep(monkeypatch):
+    # planted mistake: the extended sweep loses its precision (dtype dropped to float64)
+    import oracle.tdma_oracle as T
+    monkeypatch.setattr(T, "thomas_ext", lambda a, b, c, d: T.thomas(a, b, c, d).astype(np.float64))
+    a, b, c, d = _pinned_zero_mode(128, 3)
+    exact = _exact_thomas(a, b, c, d)
+    e64 = O.rel_l2(O.thomas(a, b, c, d), exact)
+    assert not O.rel_l2(T.thomas_ext(a, b, c, d), exact) <= e64 / 10
+
+
 # ---------------------------------------------------------------- gradients
 def test_adjoint_grads_match_central_differences():
     rng = np.random.default_rng(21)
