@@ -10,8 +10,11 @@ so no flush is needed between steps.
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
-Prints one JSON line (rank 0). Under torchrun every rank solves its own copy of the workload
-(independent problems: weak scaling, no collective on the data path).
+Prints one JSON line (rank 0). Under torchrun the ranks shard the lines of one grid (lines are
+independent: no collective on the data path): with ``--scaling weak`` (default) the grid has
+N x 1024 y-rows and rank r solves y-rows [r 1024, (r + 1) 1024), so per-GPU work is fixed; with
+``--scaling strong`` the 1024^3 grid's y-rows are split evenly. ``value`` is the unknowns of all
+ranks over the slowest rank's time.
 """
 from __future__ import annotations
 
@@ -38,7 +41,7 @@ UNIT = "unknowns/s"
 SEED = 3
 BYTES_F32R = 28.0   # a, b, c float (12) + d double (8) in, x double (8) out
 BYTES_F64 = 40.0    # a, b, c, d double in, x double out
-FP64_OPS_PEAK = 152 * 2 * 2.07e9  # FP64 pipe: 152 SMs x 2 ops/clk x 2.07 GHz (1.25 TFLOP/s, FMA = 2)
+FP64_OPS_NOMINAL = 152 * 2 * 2.07e9  # FP64 pipe, nominal: 152 SMs x 2 ops/clk x 2.07 GHz (1.25 TFLOP/s)
 KERNEL_OF_VARIANT = {0: "dc_kernel", 1: "thomas_kernel", 2: "refine_kernel", 3: "ragged_refine_kernel",
                      4: "refine_reg_kernel", 5: "refine_tma_fixed_kernel", 6: "refine_cluster_kernel",
                      7: "dc_kernel", 8: "refine_tree_kernel", 9: "packed_refine_kernel",
@@ -174,14 +177,90 @@ def source_sha(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
-def make_workload(n: int, device, ny=None):
-    """The n^3 grid, or its first ny y-rows (same lines, fewer of them) for small profiling runs."""
+def rank_rows(ny: int, rank: int, world: int, scaling: str):
+    """(y0, y1, ny_global): the y-rows [y0, y1) of the global grid that ``rank`` solves.
+
+    Lines run along z, so a y-row is n whole lines and ranks never share a line. ``weak``: the
+    global grid has world * ny y-rows, ny per rank (per-GPU work fixed as the world grows);
+    ``strong``: the global grid has ny y-rows, split by shard_range."""
+    if scaling == "weak":
+        return rank * ny, (rank + 1) * ny, world * ny
+    y0, y1 = shard_range(ny, rank, world)
+    return y0, y1, ny
+
+
+def make_workload(n: int, device, ny=None, y0: int = 0, ny_global=None):
+    """Y-rows [y0, y0 + ny) of the general grid with n x max(n, ny_global) x n points (lines along z).
+    The default is the whole n^3 grid; fewer rows give the same lines of it (profiling runs); a
+    global grid taller than n (weak scaling over ranks) is one larger grid, each rank drawing its
+    own block of it."""
     import synth
     ny = n if ny is None else ny
-    g = synth.grid_general((n, ny, n), 0, SEED, device=device, fp32_coefficients=True, full_shape=(n, n, n),
-                           origin=(0, 0, 0))
+    full_ny = max(n, ny_global or 0)
+    g = synth.grid_general((n, ny, n), 0, SEED, device=device, fp32_coefficients=True, full_shape=(n, full_ny, n),
+                           origin=(0, y0, 0))
     g.pop("x_true")
     return g
+
+
+def fp64_peak(device, sampler=None):
+    """Measured FP64 FMA throughput of this GPU (the library's probe kernel: 8 independent FMA chains
+    per thread, 8 blocks of 256 threads per SM), best of 5 launches timed with CUDA events after 3
+    warm-up launches; with ``sampler`` running, the median SM clock gives FMAs per clock per SM."""
+    import paper_2509_03933_gb300 as tdma
+    props = torch.cuda.get_device_properties(device)
+    sms = props.multi_processor_count
+    blocks = sms * 8
+    out = torch.empty(blocks, dtype=torch.float64, device=device)
+    stream = torch.cuda.current_stream(device)
+    for _ in range(3):
+        tdma.probe_fp64_fma(blocks, 256, 1 << 13, out, stream)
+    times = []
+    count = 0
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        count = tdma.probe_fp64_fma(blocks, 256, 1 << 14, out, stream)
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
+    rate = count / min(times)
+    res = {"fma_per_s": rate, "sms": sms, "launch_s": min(times), "fmas_per_launch": count,
+           "nominal_fma_per_s": FP64_OPS_NOMINAL, "how": "tdma_probe_fp64_fma: 8 blocks x 256 threads per SM, "
+           "8 independent FMA chains per thread, best of 5 (CUDA events)"}
+    if sampler is not None:
+        clk = sampler.summary()
+        if clk.get("sm_mhz"):
+            res["sm_mhz"] = clk["sm_mhz"]
+            res["fma_per_clock_per_sm"] = rate / (sms * clk["sm_mhz"] * 1e6)
+    return res
+
+
+def cpu_oracle_baseline(n: int, ys: int, device_grid, reps_all: int = 3):
+    """The C oracle (FP64 Thomas, oracle/thomas_c.c) timed on the host: one thread, then all the
+    threads OpenMP gives it, on the first ``ys`` y-rows of the grid (ys n lines of n, copied to the
+    host in the grid's [z][y][x] layout: lines adjacent, rows ys n apart). Returns (baseline dict,
+    its solution as a [lines, n] array)."""
+    from oracle import c_thomas
+    host = [device_grid[k][:, :ys, :].double().cpu().numpy() for k in ("a32", "b32", "c32", "d")]
+    x = np.empty_like(host[3])
+    lines = ys * n
+    args = (n, lines, lines, 1, *host, x)
+    t0 = time.perf_counter()
+    c_thomas.solve_strided(*args, threads=1)
+    t1 = time.perf_counter() - t0
+    threads = c_thomas.max_threads()
+    best = float("inf")
+    for _ in range(reps_all):
+        t0 = time.perf_counter()
+        c_thomas.solve_strided(*args, threads=threads)
+        best = min(best, time.perf_counter() - t0)
+    units = lines * n
+    base = {"value": units / best, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{lines} lines x {n} (first {ys} y-rows of the grid, z axis), C FP64 Thomas "
+                      f"(oracle/thomas_c.c, OpenMP over blocks of 8 adjacent lines), best of {reps_all}",
+            "single_core_value": units / t1, "os_cpu_count": os.cpu_count(), "cpu_model": c_thomas.cpu_model()}
+    return base, np.moveaxis(x, 0, -1).reshape(lines, n)
 
 
 def sample_oracle_lines(g, ys: int):
@@ -266,7 +345,7 @@ def suite_small_grid(stream, hbm_peak, flush):
     return out
 
 
-def suite_adi(stream, hbm_peak, n=512):
+def suite_adi(stream, hbm_peak, fp64_probe=None, n=512):
     """512^3 ADI viscous sweeps x -> y -> z, one CUDA graph per step: per-element coefficients
     with 8 partitions per line, and the same operator as 1D coefficients shared by all lines
     (one factorisation per sweep, per-line right-hand-side recurrences)."""
@@ -315,7 +394,9 @@ def suite_adi(stream, hbm_peak, n=512):
             # d in, x out (16 B per unknown); 3 FP64-pipe operations per unknown
             leg["launches_per_step"] = 6
             leg["hbm_frac"] = 16.0 * U / (ms * 1e-3) / 1e9 / hbm_peak
-            leg["fp64_pipe_frac"] = 3.0 * U / (ms * 1e-3) / FP64_OPS_PEAK
+            peak = fp64_probe["fma_per_s"] if fp64_probe else FP64_OPS_NOMINAL
+            leg["fp64_pipe_frac"] = 3.0 * U / (ms * 1e-3) / peak
+            leg["fp64_pipe_peak_kind"] = "measured (FP64 FMA probe)" if fp64_probe else "nominal"
             leg["bytes_per_unknown"] = 16.0
         else:
             leg["launches_per_step"] = 3
@@ -560,32 +641,38 @@ def suite_ragged(stream, hbm_peak, n_lines=20000):
 
 
 def run_reference(args):
-    """The oracle (CPU, numpy, one core) on bounded samples of the same workload."""
+    """The oracle on the host's cores: the C FP64 Thomas (oracle/thomas_c.c, OpenMP over blocks of
+    adjacent lines, all threads) on a bounded sample of the same workload per step."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return 0
-    import oracle
     import synth
+    from oracle import c_thomas
     n = args.n
     ys = max(1, args.ref_lines // n)
     g = synth.grid_general((n, ys, n), 0, SEED, fp32_coefficients=True, full_shape=(n, n, n), origin=(0, 0, 0))
-    lv = lambda t: synth.line_view(t.double(), 0).numpy()
-    a, b, c, d = lv(g["a32"]), lv(g["b32"]), lv(g["c32"]), lv(g["d"])
-    units = a.size
+    a, b, c, d = (g[k].double().numpy() for k in ("a32", "b32", "c32", "d"))  # [z][y][x]: lines adjacent
+    x = np.empty_like(d)
+    lines = ys * n
+    threads = c_thomas.max_threads()
+    step = lambda: c_thomas.solve_strided(n, lines, lines, 1, a, b, c, d, x, threads=threads)
     for _ in range(args.warmup):
-        oracle.thomas(a, b, c, d)
+        step()
     t = time.perf_counter()
     for _ in range(args.steps):
-        oracle.thomas(a, b, c, d)
+        step()
     dt = (time.perf_counter() - t) / max(1, args.steps)
+    units = lines * n
     value = units / dt
-    sample = f"{ys * n} lines x {n} (first {ys} y-rows of the {n}^3 grid, z axis) per step"
+    sample = (f"{lines} lines x {n} (first {ys} y-rows of the {n}^3 grid, z axis) per step, C FP64 Thomas "
+              f"(oracle/thomas_c.c), {threads} OpenMP threads")
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "config": {"workload": f"general-coefficient {n}^3 grid, lines along z, seed {SEED}, "
                                   "FP32-representable coefficients", "lines": n * n, "n": n},
-           "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+           "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                            "os_cpu_count": os.cpu_count(), "cpu_model": c_thomas.cpu_model()},
            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
     return 0
@@ -599,10 +686,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1024)
     ap.add_argument("--ny", type=int, default=0, help="solve only the first ny y-rows (profiling runs)")
+    ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
+                    help="N > 1: weak = ny y-rows per rank of a taller grid; strong = the grid's y-rows split")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--e2e-batches", type=int, default=8, help="slices of lines in the pipelined host solve")
     ap.add_argument("--cpu-lines", type=int, default=32768, help="lines in the CPU oracle sample")
-    ap.add_argument("--ref-lines", type=int, default=4096, help="lines per reference-arm step")
+    ap.add_argument("--ref-lines", type=int, default=32768, help="lines per reference-arm step")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-suite", action="store_true", help="skip the other workloads")
@@ -636,7 +725,7 @@ def main():
         return 0
     if args.only_adi > 0:
         hbm_peak, _ = peaks()
-        print(json.dumps({"adi": suite_adi(torch.cuda.current_stream(), hbm_peak, args.only_adi)}), flush=True)
+        print(json.dumps({"adi": suite_adi(torch.cuda.current_stream(), hbm_peak, None, args.only_adi)}), flush=True)
         return 0
     if args.only_ragged > 0:
         hbm_peak, _ = peaks()
@@ -653,9 +742,12 @@ def main():
 
     dev = torch.device("cuda", local if ws > 1 else 0)
     n = args.n
-    ny = args.ny if args.ny > 0 else n
+    ny_arg = args.ny if args.ny > 0 else n
+    y0, y1, ny_global = rank_rows(ny_arg, rank, ws, args.scaling)
+    ny = y1 - y0  # this rank's y-rows (its lines: ny n of n unknowns)
     U = n * ny * n
-    g = make_workload(n, dev, ny)
+    U_all = n * ny_global * n  # every rank's lines, each solved by exactly one rank
+    g = make_workload(n, dev, ny, y0, ny_global)
     a32, b32, c32, d = g["a32"], g["b32"], g["c32"], g["d"]
     x = torch.empty_like(d)
     stream = torch.cuda.current_stream()
@@ -678,49 +770,50 @@ def main():
 
     # ---------------- the plain FP64 solve of the same problem
     a, b, c = g["a"], g["b"], g["c"]
-    total_d, per_d = time_steps(lambda: plan_d.solve(a, b, c, d, x), max(3, args.steps // 3), args.warmup, stream)
+    k_d = max(3, args.steps // 3)
+    barrier()
+    total_d, per_d = time_steps(lambda: plan_d.solve(a, b, c, d, x), k_d, args.warmup, stream)
+    barrier()
     st_d, _ = plan_d.last_error()
-    ms_d = reduce_max(total_d / max(3, args.steps // 3), dev)
+    ms_d = reduce_max(total_d / k_d, dev)
     x_d = x
 
-    if rank != 0:
-        barrier()
-        return 0
-
-    hbm_peak, peak_kind = peaks()
-    kern_ms = sorted(per_r)[len(per_r) // 2]
-    achieved = BYTES_F32R * U / (kern_ms * 1e-3) / 1e9
-    kname = KERNEL_OF_VARIANT.get(plan_r.config["variant"], "refine_kernel")
-    trec = traffic_record(kname)
-    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-            "traffic": (trec["dram_bytes"] * (U / trec["unknowns"])) if trec else None,
-            "peak_kind": f"{peak_kind} (STREAM-style copy)", "algorithmic_bytes_per_unknown": BYTES_F32R,
-            "kernel": kname, "kernel_ms": kern_ms}
-
-    # ---------------- CPU oracle on a bounded sample (also the per-result error check)
-    cpu = None
-    err = {}
-    import oracle
-    ys = min(ny, max(1, args.cpu_lines // n))
-    oa, ob, oc, od = sample_oracle_lines(g, ys)
-    if not args.no_cpu:
-        t0 = time.perf_counter()
-        ref = oracle.thomas(oa, ob, oc, od)
-        dt = time.perf_counter() - t0
-        cpu = {"value": oa.size / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
-               "sample": f"{ys * n} lines x {n} (first {ys} y-rows of the grid), numpy Thomas, FP64"}
-    else:
-        ref = oracle.thomas(oa[:256], ob[:256], oc[:256], od[:256])
     import synth
-    nl = ref.shape[0]
-    got_r = synth.line_view(x_r[:, :ys, :].cpu(), 0).numpy()[:nl]
-    got_d = synth.line_view(x_d[:, :ys, :].cpu(), 0).numpy()[:nl]
-    err = {"f32r": oracle.rel_l2(got_r, ref), "f64": oracle.rel_l2(got_d, ref), "lines_checked": int(nl),
-           "f32r_status": st, "f64_status": st_d, "f32r_corrections_max": iters}
+    import oracle
+    hbm_peak, peak_kind = peaks()
+    fp64_probe = roof = cpu = ref = None
+    err = {}
+    ys = min(ny, max(1, args.cpu_lines // n))
+    if rank == 0:
+        # the FP64 pipe's measured peak (the FP64 kernels' second roofline)
+        with ClockSampler(local if ws > 1 else 0) as clk64:
+            fp64_probe = fp64_peak(dev, clk64)
+        kern_ms = sorted(per_r)[len(per_r) // 2]
+        achieved = BYTES_F32R * U / (kern_ms * 1e-3) / 1e9
+        kname = KERNEL_OF_VARIANT.get(plan_r.config["variant"], "refine_kernel")
+        trec = traffic_record(kname)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
+                "traffic": (trec["dram_bytes"] * (U / trec["unknowns"])) if trec else None,
+                "peak_kind": f"{peak_kind} (STREAM-style copy)", "algorithmic_bytes_per_unknown": BYTES_F32R,
+                "kernel": kname, "kernel_ms": kern_ms}
+        # ---------------- CPU oracle on a bounded sample (rank 0 at N = 1; also the error check)
+        if not args.no_cpu and ws == 1:
+            cpu, ref = cpu_oracle_baseline(n, ys, g)
+        else:
+            ys = 1
+            oa, ob, oc, od = sample_oracle_lines(g, ys)
+            ref = oracle.thomas(oa[:256], ob[:256], oc[:256], od[:256])
+        nl = ref.shape[0]
+        got_r = synth.line_view(x_r[:, :ys, :].cpu(), 0).numpy()[:nl]
+        got_d = synth.line_view(x_d[:, :ys, :].cpu(), 0).numpy()[:nl]
+        line_err = lambda got: float(np.max(np.linalg.norm(got - ref, axis=1) / np.linalg.norm(ref, axis=1)))
+        err = {"f32r": oracle.rel_l2(got_r, ref), "f64": oracle.rel_l2(got_d, ref), "lines_checked": int(nl),
+               "f32r_worst_line": line_err(got_r), "f64_worst_line": line_err(got_d),
+               "f32r_status": st, "f64_status": st_d, "f32r_corrections_max": iters}
 
-    # ---------------- end to end: pinned host buffers, copies inside the timed region, through the
-    # pipelined host solve (slices of lines in flight on two streams: host-to-device copies,
-    # solves and device-to-host copies of different slices overlap)
+    # ---------------- end to end on every rank (its own lines): pinned host buffers, copies inside
+    # the timed region, through the pipelined host solve (slices of lines in flight on two streams:
+    # host-to-device copies, solves and device-to-host copies of different slices overlap)
     e2e = None
     if not args.no_e2e:
         del g, a, b, c
@@ -736,13 +829,20 @@ def main():
         a32 = b32 = c32 = d = x = None  # the pipeline stages slices in its own device buffers
         torch.cuda.empty_cache()
         pipe = tdma.HostPipeline(shape, axis=0, precision="f32r", batches=args.e2e_batches, slots=2, device=dev)
+        barrier()
         tot, _ = time_steps(lambda: pipe.solve(h["a"], h["b"], h["c"], h["d"], hx), args.e2e_steps, 2, stream)
-        got_e = synth_lines_check(hx, ys, nl, ref)
-        e2e = {"value": U / (tot / args.e2e_steps * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi,
-               "d2h_bytes_per_step": bo, "steps": args.e2e_steps, "ms_per_step": tot / args.e2e_steps,
-               "api": f"HostPipeline(batches={args.e2e_batches}, slots=2) -> tdma_solve_host",
-               "rel_l2_error": got_e}
+        barrier()
+        ms_e = reduce_max(tot / args.e2e_steps, dev)
+        e2e = {"value": U_all / (ms_e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi * ws,
+               "d2h_bytes_per_step": bo * ws, "steps": args.e2e_steps, "ms_per_step": ms_e,
+               "api": f"HostPipeline(batches={args.e2e_batches}, slots=2) -> tdma_solve_host"}
+        if rank == 0:
+            e2e["rel_l2_error"] = synth_lines_check(hx, ys, ref.shape[0], ref)
         del pipe, h, hx
+
+    if rank != 0:
+        barrier()
+        return 0
 
     cfg_d = plan_d.config
     suite = None
@@ -752,7 +852,7 @@ def main():
         flushbuf = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
         suite = {}
         for name, fn in (("grid64_z_f64", lambda: suite_small_grid(stream, hbm_peak, lambda: _flush_l2(flushbuf))),
-                         ("adi512_xyz_f64", lambda: suite_adi(stream, hbm_peak)),
+                         ("adi512_xyz_f64", lambda: suite_adi(stream, hbm_peak, fp64_probe)),
                          ("poisson1024_z_complex", lambda: suite_poisson(stream, hbm_peak)),
                          ("ragged20000", lambda: suite_ragged(stream, hbm_peak)),
                          ("split_line512_1rank", lambda: suite_split_line(stream)),
@@ -766,18 +866,26 @@ def main():
     cfg_r = plan_r.config
     # FP64-pipe instructions per unknown: Thomas 8 (5 + a 3-FMA reciprocal), partitioned sweep 14
     fp64_ops = 8.0 if cfg_d["variant"] == 1 else 14.0
+    fp64_peak_ops = fp64_probe["fma_per_s"]
+    shard = (f"rank r of {ws} solves y-rows [{ny} r, {ny} (r + 1))" if args.scaling == "weak"
+             else f"the {ny_global} y-rows split evenly over {ws} ranks") if ws > 1 else "one rank"
     out = {
-        "metric": METRIC, "value": ws * U / (ms_r * 1e-3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_r, "higher_is_better": True, "scaling": "weak",
+        "metric": METRIC, "value": U_all / (ms_r * 1e-3), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_r, "higher_is_better": True,
+        "scaling": args.scaling if ws > 1 else "weak",
         "vs_baseline": None, "dtype": "f32 sweeps + extra-precise residual, f64 in/out", "data": "synthetic",
-        "config": {"workload": f"general-coefficient {n}x{ny}x{n} grid, {n * ny} lines of n={n} along z "
-                               f"(stride {n * ny}), seed {SEED}, FP32-representable coefficients", "lines": n * ny, "n": n,
-                   "l2": "inputs (30 GB) larger than L2", "plan": cfg_r},
-        "fp64": {"value": ws * U / (ms_d * 1e-3), "unit": UNIT, "ms_per_step": ms_d, "plan": cfg_d,
+        "config": {"workload": f"general-coefficient {n}x{ny_global}x{n} grid, {n * ny_global} lines of n={n} along z "
+                               f"(stride {n * ny} per rank), seed {SEED}, FP32-representable coefficients",
+                   "lines": n * ny_global, "n": n, "sharding": shard,
+                   "l2": "inputs (30 GB per rank) larger than L2", "plan": cfg_r},
+        "fp64": {"value": U_all / (ms_d * 1e-3), "unit": UNIT, "ms_per_step": ms_d, "plan": cfg_d,
                  "roofline": {"bound": "alu", "achieved": fp64_ops * U / (ms_d * 1e-3) / 1e9,
-                              "peak": FP64_OPS_PEAK / 1e9, "unit": "Gop/s (FP64 pipe)",
-                              "frac": fp64_ops * U / (ms_d * 1e-3) / FP64_OPS_PEAK,
-                              "hbm_frac": BYTES_F64 * U / (ms_d * 1e-3) / 1e9 / hbm_peak}},
+                              "peak": fp64_peak_ops / 1e9, "unit": "G FP64-pipe instructions/s",
+                              "peak_kind": "measured (FP64 FMA probe, this run)",
+                              "frac": fp64_ops * U / (ms_d * 1e-3) / fp64_peak_ops,
+                              "ops_per_unknown": fp64_ops,
+                              "hbm_frac": BYTES_F64 * U / (ms_d * 1e-3) / 1e9 / hbm_peak},
+                 "fp64_peak_probe": fp64_probe},
         "error": err,
         "roofline": roof,
         "cpu_baseline": cpu,

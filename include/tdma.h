@@ -236,14 +236,17 @@ tdma_status_t tdma_solve_host(tdma_plan_t plan, const tdma_host_layout_t* layout
  * 32 MiB array compiled into the library, present on every GPU that loads it until the
  * process exits. Takes the same descriptor fields as tdma_plan_create for uniform lines
  * (n >= 1; precision TDMA_F64 or TDMA_F32; nrhs, coef_broadcast and diag_shift as there;
- * partitions 0 or 1) and the same device arrays as tdma_solve; enqueues on `stream`.
- * Returns TDMA_ERR_WORKSPACE when n * n_lines factors (8 bytes each in FP64, 4 in FP32) exceed
- * the array, TDMA_ERR_INVALID_ARG / TDMA_ERR_UNSUPPORTED as tdma_plan_create and tdma_solve do.
- * Device-side numerical faults are not recorded (no status block): a zero pivot leaves
- * non-finite values in x. The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before any stream
- * capture. All calls share the array: calls that could run at the same time on the GPU
- * (other streams, other host threads) race on it and must not be issued. */
+ * partitions 0 or 1) and the same device arrays as tdma_solve; x may alias d; enqueues on
+ * `stream`. Returns TDMA_ERR_WORKSPACE when n * n_lines factors (8 bytes each in FP64, 4 in FP32)
+ * exceed the array; TDMA_ERR_INVALID_ARG for a bad descriptor (n < 1, negative counts or strides,
+ * partitions < 0, nrhs not 1 or 2, an unknown precision, a NULL array); TDMA_ERR_UNSUPPORTED for
+ * what the plan-based solve supports but this entry does not (TDMA_F32_REFINE, TDMA_F64_REFINE,
+ * partitions > 1, pdd, misaligned arrays). Device-side numerical faults are not recorded (no
+ * status block): a zero pivot leaves non-finite values in x. The first call on a device, and the
+ * first after that device's context was replaced (cudaDeviceReset), looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture. All calls share the array: calls that could run at the same time on the GPU (other
+ * streams, other host threads) race on it and must not be issued. */
 tdma_status_t tdma_solve_thomas_static(const tdma_desc_t* desc, const void* a, const void* b,
                                        const void* c, const void* d, void* x, void* stream);
 
@@ -333,6 +336,17 @@ tdma_status_t tdma_slab_pairs_solve(int32_t n_slabs, int64_t count, int32_t nrhs
                                     double* ends, double* work, int32_t* status, void* stream);
 tdma_status_t tdma_slab_finish(const tdma_slab_desc_t* desc, int64_t line0, int64_t count, const double* ends,
                                const double* scratch, double* x, void* stream);
+
+/* ---- Measurement --------------------------------------------------------------------------------
+ * FP64 fused multiply-add throughput of the current GPU (the paper has no counterpart; it serves the
+ * FP64 roofline of the solve kernels, whose sweeps run on the FP64 pipe). Launches `blocks` blocks of
+ * `threads` threads (a multiple of 32, at most 1024); every thread runs 8 independent chains of `iters`
+ * FP64 FMAs. The caller times the launch on `stream` (e.g. with CUDA events) and divides *fma_count
+ * (set on success to blocks * threads * iters * 8) by the time. `out`: a device array of `blocks`
+ * doubles, written only in the impossible case that keeps the chains from being optimised away.
+ * TDMA_ERR_INVALID_ARG for bad sizes, TDMA_ERR_CUDA when the launch fails. */
+tdma_status_t tdma_probe_fp64_fma(int32_t blocks, int32_t threads, int64_t iters, double* out, int64_t* fma_count,
+                                  void* stream);
 
 #ifdef __cplusplus
 }

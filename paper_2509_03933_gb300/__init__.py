@@ -17,7 +17,7 @@ import torch
 from . import _build
 
 __all__ = ["PoissonFFT", "Plan", "solve", "solve_ragged", "solve_backward", "TDMASolve", "line_layout", "TDMAError", "F64", "F32",
-           "F32_REFINE", "load_library", "declared_symbols", "sweep_graph", "HostPipeline", "HostLayout"]
+           "F32_REFINE", "load_library", "declared_symbols", "probe_fp64_fma", "sweep_graph", "HostPipeline", "HostLayout"]
 
 F64, F32, F32_REFINE, F64_REFINE = 0, 1, 2, 3
 _PREC = {"f64": F64, "f32": F32, "f32r": F32_REFINE, "f64r": F64_REFINE, F64: F64, F32: F32, F32_REFINE: F32_REFINE,
@@ -105,8 +105,24 @@ def load_library(build: bool = True) -> ctypes.CDLL:
     lib.tdma_poisson_last_error.restype = st
     lib.tdma_poisson_destroy.argtypes = [_VP]
     lib.tdma_poisson_destroy.restype = st
+    lib.tdma_probe_fp64_fma.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _VP,
+                                        ctypes.POINTER(ctypes.c_int64), _VP]
+    lib.tdma_probe_fp64_fma.restype = st
     _LIB = lib
     return lib
+
+
+def probe_fp64_fma(blocks: int, threads: int = 256, iters: int = 1 << 14, out=None, stream=None) -> int:
+    """Enqueue the library's FP64 FMA throughput probe on ``stream``; returns the number of FMAs it
+    runs (the caller times the launch). ``out``: a CUDA float64 tensor of >= ``blocks`` values."""
+    lib = load_library()
+    if out is None:
+        out = torch.empty(blocks, dtype=torch.float64, device="cuda")
+    count = ctypes.c_int64(0)
+    st = lib.tdma_probe_fp64_fma(int(blocks), int(threads), int(iters), _ptr(out), ctypes.byref(count), _stream(stream))
+    if st != 0:
+        raise TDMAError(st, "tdma_probe_fp64_fma")
+    return int(count.value)
 
 
 def declared_symbols() -> list:

@@ -30,8 +30,15 @@ TDMA_DEV void report_iters(DevStatus* st, int32_t it) {
 // FP64: MUFU seed y (relative error below 2^-20) refined by the series 1/w = y / (1 - e) with
 // e = 1 - w y, truncated after the quadratic term: y (1 + e + e^2) = (1/w) (1 - e^3), a relative
 // error below 2^-60 before the final rounding; three dependent FMAs (two Newton-Raphson steps
-// take four).
+// take four). The seed flushes subnormals to zero, in its input (w subnormal) and in its output
+// (|w| >= 2^1022, whose reciprocal lies below the normal range), so those w, and zeros,
+// infinities and NaN, take the IEEE division instead: a pivot beyond the normal range then gives
+// its correctly rounded reciprocal, a zero or subnormal pivot an infinite one, and an infinite or
+// NaN pivot NaN, so that the callers' finiteness checks see them. The test is on the exponent
+// bits (integer pipe); no normal pivot below 2^1022 takes the division.
 TDMA_DEV double rcp(double w) {
+  const unsigned ex = ((unsigned)__double2hiint(w) >> 20) & 0x7FFu;
+  if (ex - 1u >= 0x7FCu) return ex == 0x7FFu ? w - w : 1.0 / w;
   double y;
   asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(w));
   const double e = fma(-w, y, 1.0);

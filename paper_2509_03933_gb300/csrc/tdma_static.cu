@@ -16,6 +16,8 @@
 #include <cstdint>
 #include <mutex>
 
+#include <cuda.h>
+
 #include "tdma.h"
 #include "kernels_thomas.cuh"
 
@@ -26,21 +28,45 @@ constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_thomas_scratch[kStaticScratchBytes];
 
-// Device address of g_thomas_scratch, looked up once per device with that device current.
+// Device address of g_thomas_scratch, looked up with the device current, once per device and
+// context: the address belongs to the module loaded into a context, so a new primary context (after
+// cudaDeviceReset) gets its own lookup. cudaGetSymbolAddress allocates nothing.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+
+CtxGetCurrentFn ctx_get_current() {
+  static CtxGetCurrentFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* ptr = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &ptr, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<CtxGetCurrentFn>(ptr);
+  });
+  return fn;
+}
+
 std::mutex g_mu;
 void* g_scratch_addr[kMaxDevices] = {};
+CUcontext g_scratch_ctx[kMaxDevices] = {};
 
 cudaError_t scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  const CtxGetCurrentFn get = ctx_get_current();
+  CUcontext ctx = nullptr;
+  // a context not yet current on this thread reads as null: the lookup below makes it current
+  const bool have_ctx = get && get(&ctx) == CUDA_SUCCESS && ctx != nullptr;
   std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
+  if (!have_ctx || !g_scratch_addr[dev] || g_scratch_ctx[dev] != ctx) {
     void* ptr = nullptr;
     e = cudaGetSymbolAddress(&ptr, g_thomas_scratch);
     if (e != cudaSuccess) return e;
+    if (!have_ctx && get && get(&ctx) != CUDA_SUCCESS) ctx = nullptr;
     g_scratch_addr[dev] = ptr;
+    g_scratch_ctx[dev] = ctx;  // null: not known, looked up again next time
   }
   *out = g_scratch_addr[dev];
   return cudaSuccess;
@@ -55,7 +81,9 @@ extern "C" tdma_status_t tdma_solve_thomas_static(const tdma_desc_t* desc, const
   if (!desc) return TDMA_ERR_INVALID_ARG;
   const tdma_desc_t& dd = *desc;
   if (dd.n < 1 || dd.n_lines < 0 || (dd.nrhs != 1 && dd.nrhs != 2)) return TDMA_ERR_INVALID_ARG;
+  if (dd.precision == TDMA_F32_REFINE || dd.precision == TDMA_F64_REFINE) return TDMA_ERR_UNSUPPORTED;
   if (dd.precision != TDMA_F64 && dd.precision != TDMA_F32) return TDMA_ERR_INVALID_ARG;
+  if (dd.partitions < 0) return TDMA_ERR_INVALID_ARG;
   if (dd.inner_count < 1 || dd.elem_stride < 0 || dd.inner_stride < 0 || dd.outer_stride < 0)
     return TDMA_ERR_INVALID_ARG;
   if (dd.partitions > 1) return TDMA_ERR_UNSUPPORTED;  // the Thomas form has one partition

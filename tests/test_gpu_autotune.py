@@ -9,6 +9,7 @@ import torch
 
 import oracle as O
 import synth
+from parity import rel_err
 import paper_2509_03933_gb300 as tdma
 
 pytestmark = pytest.mark.gpu
@@ -34,7 +35,7 @@ def test_autotune_choice_is_valid_and_cached(precision, shape, axis):
     assert plan.last_error()[0] == 0
     ref = O.thomas(*(synth.line_view(t.double().cpu(), axis).numpy() for t in (a, b, c, d)))
     tol = {"f64": 1e-12, "f32": 1e-5, "f32r": 1e-12}[precision]
-    assert O.rel_l2(synth.line_view(x.double().cpu(), axis).numpy(), ref) <= tol
+    assert rel_err(synth.line_view(x.double().cpu(), axis).numpy(), ref) <= tol
     plan2 = tdma.Plan(*lay, precision=precision)
     assert (plan2.config["variant"], plan2.config["partitions"]) == (cfg["variant"], cfg["partitions"])
 

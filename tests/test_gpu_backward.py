@@ -5,6 +5,7 @@ import pytest
 import torch
 
 import oracle as O
+from parity import rel_err
 import synth
 import paper_2509_03933_gb300 as tdma
 
@@ -24,7 +25,7 @@ def test_f64_gradients_match_oracle(axis, partitions):
     ga, gb, gc, gd = tdma.solve_backward(a, b, c, x, w, axis=axis, partitions=partitions)
     ref = O.adjoint_grads(_lines(a, axis), _lines(b, axis), _lines(c, axis), _lines(x, axis), _lines(w, axis))
     for got, want in zip((ga, gb, gc, gd), ref):
-        assert O.rel_l2(_lines(got, axis), want) <= 1e-12
+        assert rel_err(_lines(got, axis), want) <= 1e-12
 
 
 def test_f32_and_refined_gradients():
@@ -36,14 +37,14 @@ def test_f32_and_refined_gradients():
     w = torch.randn_like(x)
     ref = O.adjoint_grads(la(a32), la(b32), la(c32), la(x), la(w))
     ga, gb, gc, gd = tdma.solve_backward(a32, b32, c32, x, w, axis=0, precision="f32r")
-    assert O.rel_l2(la(gd), ref[3]) <= 1e-12          # lambda, refined in FP64
+    assert rel_err(la(gd), ref[3]) <= 1e-12          # lambda, refined in FP64
     for got, want in zip((ga, gb, gc), ref[:3]):      # stored as float
-        assert O.rel_l2(la(got), want) <= 1e-6
+        assert rel_err(la(got), want) <= 1e-6
     x32 = tdma.solve(a32, b32, c32, d.float(), axis=0, precision="f32")
     ga, gb, gc, gd = tdma.solve_backward(a32, b32, c32, x32, w.float(), axis=0, precision="f32")
     ref = O.adjoint_grads(la(a32), la(b32), la(c32), la(x32), la(w))
     for got, want in zip((ga, gb, gc, gd), ref):
-        assert O.rel_l2(la(got), want) <= 1e-5
+        assert rel_err(la(got), want) <= 1e-5
 
 
 def test_broadcast_complex_gradients_are_summed_over_lines():
@@ -69,7 +70,7 @@ def test_broadcast_complex_gradients_are_summed_over_lines():
         for k, gk in enumerate((ra, rb, rc)):
             sums[k] += gk.sum(axis=0)
         lam[..., r] = rl
-    assert O.rel_l2(gd.cpu().numpy().transpose(1, 0, 2), lam) <= 1e-12
+    assert rel_err(gd.cpu().numpy().transpose(1, 0, 2), lam) <= 1e-12
     for got, want in zip((ga, gb, gc), sums):
         assert O.rel_l2(got.cpu().numpy(), want) <= 1e-11
 

@@ -1,7 +1,7 @@
 """Forward-solve parity of the CUDA path against the CPU oracle (element by element).
 
-Tolerances (relative L2 over the compared lines): FP64 <= 1e-12, FP32 <= 1e-5,
-FP32 + refinement <= 1e-12, as the FP64 oracle demands of each precision.
+Tolerances (relative L2, pooled over the compared lines and for every single line): FP64 <= 1e-12,
+FP32 <= 1e-5, FP32 + refinement <= 1e-12, as the FP64 oracle demands of each precision.
 """
 import numpy as np
 import pytest
@@ -9,6 +9,7 @@ import torch
 
 import oracle as O
 import synth
+from parity import rel_err
 import paper_2509_03933_gb300 as tdma
 
 pytestmark = pytest.mark.gpu
@@ -41,7 +42,7 @@ def _grid_case(shape, axis, seed, precision, partitions):
 def test_config0_z_axis_f64(partitions):
     # 64^3 grid, 4096 lines of n = 64 along the strided z axis, seed 0
     x, ref = _grid_case((64, 64, 64), 0, 0, "f64", partitions)
-    assert O.rel_l2(x, ref) <= TOL["f64"]
+    assert rel_err(x, ref) <= TOL["f64"]
     assert np.max(np.abs(x - ref)) <= 1e-12 * np.abs(ref).max()
 
 
@@ -53,7 +54,7 @@ def test_axes_and_uneven_partitions_f64(axis, partitions):
     if partitions > 1 and n // partitions < 2:
         pytest.skip("partition too small")
     x, ref = _grid_case(shape, axis, 7 + axis, "f64", partitions)
-    assert O.rel_l2(x, ref) <= TOL["f64"]
+    assert rel_err(x, ref) <= TOL["f64"]
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 4, 5, 7, 31, 32, 33, 63, 64, 65, 257, 1000])
@@ -61,14 +62,14 @@ def test_axes_and_uneven_partitions_f64(axis, partitions):
 def test_line_lengths_and_ragged_tails(n, precision):
     # 37 lines: not a multiple of the lines per block; unit-stride rows
     x, ref = _grid_case((37, n), 1, 11 + n, precision, 0)
-    assert O.rel_l2(x, ref) <= TOL[precision]
+    assert rel_err(x, ref) <= TOL[precision]
 
 
 @pytest.mark.parametrize("precision", ["f32", "f32r"])
 @pytest.mark.parametrize("axis,partitions", [(0, 0), (0, 4), (2, 8), (1, 3)])
 def test_float_paths_on_grid(precision, axis, partitions):
     x, ref = _grid_case((48, 24, 40), axis, 3, precision, partitions)
-    assert O.rel_l2(x, ref) <= TOL[precision]
+    assert rel_err(x, ref) <= TOL[precision]
 
 
 def test_refinement_reports_corrections_and_beats_fp32():
@@ -81,9 +82,9 @@ def test_refinement_reports_corrections_and_beats_fp32():
     st, iters = plan.last_error()
     assert st == 0 and 1 <= iters <= 4
     ref = O.thomas(*(_np_lines(t, 0) for t in (a, b, c, d)))
-    e_r = O.rel_l2(_np_lines(x, 0), ref)
+    e_r = rel_err(_np_lines(x, 0), ref)
     x32 = tdma.solve(a, b, c, d.float(), axis=0, precision="f32")
-    e_32 = O.rel_l2(_np_lines(x32, 0), ref)
+    e_32 = rel_err(_np_lines(x32, 0), ref)
     assert e_r <= 1e-12 and e_32 > 1e3 * e_r
 
 
@@ -92,7 +93,7 @@ def test_x_aliases_d():
     a, b, c, d = (g[k].cuda() for k in ("a", "b", "c", "d"))
     ref = O.thomas(*(_np_lines(t, 2) for t in (a, b, c, d)))
     tdma.solve(a, b, c, d, axis=2, partitions=4, out=d)
-    assert O.rel_l2(_np_lines(d, 2), ref) <= 1e-12
+    assert rel_err(_np_lines(d, 2), ref) <= 1e-12
 
 
 def test_strided_subset_of_lines():
@@ -103,7 +104,7 @@ def test_strided_subset_of_lines():
     full = torch.zeros(40, 6, 16, dtype=torch.float64, device="cuda")
     x = full[:, :, ::2]
     tdma.solve(a, b, c, d, axis=0, partitions=4, out=x)
-    assert O.rel_l2(_np_lines(x.contiguous(), 0), ref) <= 1e-12
+    assert rel_err(_np_lines(x.contiguous(), 0), ref) <= 1e-12
     assert torch.count_nonzero(full[:, :, 1::2]) == 0  # lines in between untouched
 
 
@@ -145,7 +146,7 @@ def test_poisson_lines_broadcast_complex():
     dn = d.cpu().numpy().transpose(1, 0, 2)  # [lines, n, 2]
     ref = O.thomas_ext(a, b, c, dn)
     got = x.cpu().numpy().transpose(1, 0, 2)
-    assert O.rel_l2(got, ref) <= 1e-12
+    assert rel_err(got, ref) <= 1e-12
 
 
 @pytest.mark.parametrize("n,lines", [(1024, 64), (512, 48), (256, 40), (64, 100), (1024, 37), (256, 6)])
@@ -154,9 +155,9 @@ def test_refine_tile_kernels_z_lines(n, lines):
     # counts divisible by 4 take the TMA-staged tile; others the plain-load fallback; 6 lines
     # leave a partial last block.
     x, ref = _grid_case((n, lines), 0, 17 + n, "f32r", 0)
-    assert O.rel_l2(x, ref) <= TOL["f32r"]
+    assert rel_err(x, ref) <= TOL["f32r"]
     x, ref = _grid_case((n, lines), 0, 17 + n, "f32", 0)
-    assert O.rel_l2(x, ref) <= TOL["f32"]
+    assert rel_err(x, ref) <= TOL["f32"]
 
 
 @pytest.mark.parametrize("tree", [True, False])
@@ -178,7 +179,7 @@ def test_cluster_refine_kernels(monkeypatch, tree, n, lines):
     st, iters = plan.last_error()
     assert st == 0 and iters == 1
     ref = O.thomas(*(_np_lines(t, 0) for t in (a, b, c, d)))
-    assert O.rel_l2(_np_lines(x, 0), ref) <= TOL["f32r"]
+    assert rel_err(_np_lines(x, 0), ref) <= TOL["f32r"]
 
 
 @pytest.mark.parametrize("tree", [True, False])
@@ -201,16 +202,16 @@ def test_cluster_refine_more_corrections_and_in_place(monkeypatch, tree):
     plan.solve(a, b, c, d, x)
     st, iters = plan.last_error()
     assert st == 0 and iters >= 2
-    assert O.rel_l2(_np_lines(x, 0), ref) <= TOL["f32r"]
+    assert rel_err(_np_lines(x, 0), ref) <= TOL["f32r"]
     dd = d.clone()
     plan.solve(a, b, c, dd, dd)  # in place
     assert plan.last_error()[0] == 0
-    assert O.rel_l2(_np_lines(dd, 0), ref) <= TOL["f32r"]
+    assert rel_err(_np_lines(dd, 0), ref) <= TOL["f32r"]
     stiff = tdma.Plan(*tdma.line_layout(d, 0), precision="f32r", max_refine_iters=3, refine_tol=1e-30)
     stiff.solve(a, b, c, d, x)
     st, iters = stiff.last_error()
     assert st == 7 and iters == 3
-    assert O.rel_l2(_np_lines(x, 0), ref) <= TOL["f32r"]
+    assert rel_err(_np_lines(x, 0), ref) <= TOL["f32r"]
 
 
 @pytest.mark.parametrize("partitions", [1, 4])
@@ -220,7 +221,7 @@ def test_fp64_refine_mode_general_and_badly_conditioned(partitions):
     g = synth.grid_general((64, 8, 24), 0, 61)
     a, b, c, d = (g[k].cuda() for k in ("a", "b", "c", "d"))
     xr = tdma.solve(a, b, c, d, axis=0, precision="f64r", partitions=partitions, check=True)
-    assert O.rel_l2(_np_lines(xr, 0), ref) <= 1e-14
+    assert rel_err(_np_lines(xr, 0), ref) <= 1e-14
     # the pinned Poisson zero mode (condition number ~1e9) against extended precision
     pz = synth.poisson_lines(2, 2, 1024, seed=2, device="cuda", rhs=True)
     dz = pz["d"].view(1024, 4, 2)[:, :1, :]

@@ -1,0 +1,68 @@
+"""Accuracy envelope of FP32 storage + refinement (TDMA_F32_REFINE) over the condition number.
+
+The float sweeps contract the error by about kappa * 2^-24 per correction, and the residual is
+formed in float pairs, accurate to about 2^-48 of its terms, so the attainable accuracy is about
+kappa * 2^-48 of |x|. Lines are FP32-representable (coefficients rounded to float define the
+problem) with a diagonal-dominance margin eps that sets kappa from about 10^2 to 10^6. For every
+case the solve must either meet 1e-12 against the extended-precision oracle (per line and pooled)
+or report TDMA_ERR_NOT_CONVERGED: a status of 0 with a larger error is a silent failure and fails
+the test. Well-conditioned cases must converge. Covered for the kernel of strided lines (lines
+along the slowest axis) and for the chunk kernel (unit-stride lines)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle as O
+from parity import per_line, rel_err
+import paper_2509_03933_gb300 as tdma
+
+pytestmark = pytest.mark.gpu
+
+N = 1024
+
+
+def _lines(eps, lines, seed):
+    """FP32-representable lines [lines, N] with couplings in [0.5, 1] and b = |a| + |c| + eps (1 + U)."""
+    rng = np.random.default_rng(seed)
+    a = -(0.5 + 0.5 * rng.uniform(size=(lines, N)))
+    c = -(0.5 + 0.5 * rng.uniform(size=(lines, N)))
+    b = np.abs(a) + np.abs(c) + eps * (1.0 + rng.uniform(size=(lines, N)))
+    a, b, c = (t.astype(np.float32).astype(np.float64) for t in (a, b, c))
+    d = rng.uniform(-1, 1, (lines, N))
+    return a, b, c, d
+
+
+def _kappa(a, b, c):
+    return float(np.linalg.cond(O.dense_matrix(a, b, c)))
+
+
+EPS = [3e-2, 3e-3, 3e-4, 3e-5, 0.0]  # kappa about 1e2 .. 1e6
+
+
+@pytest.mark.parametrize("layout", ["strided", "unit_stride"])
+@pytest.mark.parametrize("eps", EPS)
+def test_f32_refine_meets_1e12_or_reports_not_converged(layout, eps):
+    lines = 256
+    a, b, c, d = _lines(eps, lines, 1000 + int(eps * 1e6))
+    kappa = _kappa(a[0], b[0], c[0])
+    ref = O.thomas_ext(a, b, c, d)
+    if layout == "strided":  # [N][lines]: lines along the slowest axis
+        t = [torch.from_numpy(np.ascontiguousarray(v.T)) for v in (a, b, c, d)]
+        axis, back = 0, (lambda x: x.T)
+    else:  # [lines][N]: unit-stride lines
+        t = [torch.from_numpy(np.ascontiguousarray(v)) for v in (a, b, c, d)]
+        axis, back = 1, (lambda x: x)
+    A, B, C = (v.float().cuda() for v in t[:3])
+    D = t[3].cuda()
+    plan = tdma.Plan(*tdma.line_layout(D, axis), precision="f32r")
+    x = torch.empty_like(D)
+    plan.solve(A, B, C, D, x)
+    st, iters = plan.last_error()
+    err = rel_err(back(x.cpu().numpy()), ref)
+    worst_line = float(per_line(back(x.cpu().numpy()), ref).max())
+    info = f"kappa {kappa:.2e}, status {st}, corrections {iters}, error {err:.2e} (worst line {worst_line:.2e})"
+    assert st in (0, 7), info
+    if st == 0:
+        assert err <= 1e-12, "silent failure: " + info
+    if kappa < 2e3:
+        assert st == 0, info  # well-conditioned lines converge

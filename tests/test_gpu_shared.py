@@ -10,6 +10,7 @@ import pytest
 import torch
 
 import oracle as O
+from parity import rel_err
 import synth
 import paper_2509_03933_gb300 as tdma
 
@@ -67,7 +68,7 @@ def test_shared_matches_oracle_every_axis(precision, nrhs, axis):
     x = torch.empty_like(d)
     plan.solve(a, b, c, d, x)
     assert plan.last_error()[0] == 0
-    assert O.rel_l2(_lines(x, axis, nrhs), _oracle(a, b, c, d, axis, nrhs)) <= TOL[precision]
+    assert rel_err(_lines(x, axis, nrhs), _oracle(a, b, c, d, axis, nrhs)) <= TOL[precision]
 
 
 @pytest.mark.parametrize("shape,nrhs", [((5, 7, 45), 1), ((5, 7, 45), 2), ((3, 11, 2), 1), ((1, 9, 1000), 2),
@@ -85,9 +86,9 @@ def test_shared_unit_stride_ragged_chunks_and_partial_warps(shape, nrhs):
     plan.solve(a, b, c, d, x)
     assert plan.last_error()[0] == 0
     ref = _oracle(a, b, c, d, 2, nrhs)
-    assert O.rel_l2(_lines(x, 2, nrhs), ref) <= 1e-12
+    assert rel_err(_lines(x, 2, nrhs), ref) <= 1e-12
     plan.solve(a, b, c, d, d)  # x over d
-    assert O.rel_l2(_lines(d, 2, nrhs), ref) <= 1e-12
+    assert rel_err(_lines(d, 2, nrhs), ref) <= 1e-12
 
 
 @pytest.mark.parametrize("n", [2, 3, 5, 1000])
@@ -98,7 +99,7 @@ def test_shared_short_and_long_lines(n):
     assert plan.config["variant"] == SHARED
     x = torch.empty_like(d)
     plan.solve(a, b, c, d, x)
-    assert O.rel_l2(_lines(x, 0, 1), _oracle(a, b, c, d, 0, 1)) <= 1e-12
+    assert rel_err(_lines(x, 0, 1), _oracle(a, b, c, d, 0, 1)) <= 1e-12
 
 
 def test_shared_in_place_and_repeated():
@@ -113,7 +114,7 @@ def test_shared_in_place_and_repeated():
     plan.solve(a, b, c, d, x2)
     assert torch.equal(x1, x2)
     plan.solve(a, b, c, d, d)  # x over d
-    assert O.rel_l2(_lines(d, 0, 2), ref) <= 1e-12
+    assert rel_err(_lines(d, 0, 2), ref) <= 1e-12
 
 
 def test_many_lines_choose_shared_automatically_and_agree_with_thomas():
@@ -136,7 +137,7 @@ def test_many_lines_choose_shared_automatically_and_agree_with_thomas():
     assert O.rel_l2(x1.cpu().numpy(), x2.cpu().numpy()) <= 1e-14
     idx = np.random.default_rng(0).choice(L, 64, replace=False)
     ref = _oracle(a, b, c, d[:, idx].contiguous(), 0, 1)
-    assert O.rel_l2(x1[:, idx].cpu().numpy().T, ref) <= 1e-12
+    assert rel_err(x1[:, idx].cpu().numpy().T, ref) <= 1e-12
 
 
 @pytest.mark.parametrize("precision", ["f64", "f32"])
@@ -167,7 +168,7 @@ def test_shared_backward_sums_gradients_over_lines(precision, nrhs):
             sums[k] += gk.sum(axis=0)
         lam[..., r] = rl
     got = _lines(gd, 0, nrhs)
-    assert O.rel_l2(got, lam[..., 0] if nrhs == 1 else lam) <= TOL[precision]
+    assert rel_err(got, lam[..., 0] if nrhs == 1 else lam) <= TOL[precision]
     tol = 1e-11 if precision == "f64" else 1e-4
     for g, want in zip((ga, gb, gc), sums):
         assert O.rel_l2(g.double().cpu().numpy(), want) <= tol
@@ -223,7 +224,7 @@ def test_factorisation_over_several_chunks(axis):
     x = torch.empty_like(d)
     plan.solve(a, b, c, d, x)
     assert plan.last_error()[0] == 0
-    assert O.rel_l2(_lines(x, axis, 1), _oracle(a, b, c, d, axis, 1)) <= 1e-12
+    assert rel_err(_lines(x, axis, 1), _oracle(a, b, c, d, axis, 1)) <= 1e-12
 
 
 @pytest.mark.parametrize("diag", [2.0001, 2.5])
