@@ -44,10 +44,17 @@
  *                    badly conditioned lines where plain FP64 elimination stops a few 1e-12
  *                    short: the residual r = d - A x is formed exactly (integer arithmetic on
  *                    the 53-bit significands) and the correction A dx = r is solved in FP32.
+ *                    With coef_broadcast, only the lines that need it are corrected: a line whose
+ *                    condition-number bound ||A||_inf / delta is below refine_kappa keeps the plain
+ *                    FP64 result (delta: the smallest diagonal-dominance margin of a row,
+ *                    |b_i| - |a_i| - |c_i|, which bounds ||A^-1||_inf by 1 / delta for a diagonally
+ *                    dominant A; a line without a positive margin is always corrected). The lines
+ *                    are picked on the device at every solve (tdma_plan_corrected_lines reports how
+ *                    many). Per-element coefficients: every line is corrected.
  *                    Lines whose residuals fall below the float range (right-hand sides under
  *                    about 1e-22) keep the plain FP64 accuracy. x must not alias d; the
  *                    workspace holds the FP32 correction's factors (4 (1 + nrhs) bytes per
- *                    unknown).
+ *                    unknown) and the list of corrected lines.
  *
  * Approximate reduced solve (`pdd` = 1)
  *   The parallel diagonally dominant (PDD) method the paper's momentum solver applies to its
@@ -112,6 +119,8 @@ typedef struct {
   int32_t max_refine_iters; /* TDMA_F32_REFINE: correction steps at most (0 = default 4)     */
   double refine_tol;     /* TDMA_F32_REFINE: target relative error per line (<= 0: 2.5e-13) */
   int32_t pdd;           /* 0: exact; 1: parallel diagonally dominant approximation, see below */
+  double refine_kappa;   /* TDMA_F64_REFINE with coef_broadcast: lines whose condition-number bound
+                            is below this keep the plain FP64 result (0: 1e5; < 0: correct all)  */
 } tdma_desc_t;
 
 /* Launch configuration a plan has settled on (reported for benchmarks and tests). */
@@ -190,6 +199,11 @@ tdma_status_t tdma_plan_get_config(tdma_plan_t plan, tdma_config_t* config);
  * the first device-side error recorded since the last call. If `info` is not NULL it
  * receives the largest number of refinement corrections any line used. */
 tdma_status_t tdma_last_device_error(tdma_plan_t plan, void* stream, int32_t* info);
+
+/* Synchronise `stream` and report in *lines how many lines the last TDMA_F64_REFINE solve of the plan
+ * corrected (the rest kept the plain FP64 result); 0 for other precisions. Does not clear the plan's
+ * status block. */
+tdma_status_t tdma_plan_corrected_lines(tdma_plan_t plan, void* stream, int64_t* lines);
 
 /* Static, human-readable name of a status code. */
 const char* tdma_status_string(tdma_status_t status);

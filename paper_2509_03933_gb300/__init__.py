@@ -40,7 +40,8 @@ class Desc(ctypes.Structure):
                 ("ragged_lengths", ctypes.c_void_p), ("ragged_max_n", ctypes.c_int64),
                 ("ragged_total", ctypes.c_int64), ("nrhs", ctypes.c_int32), ("coef_broadcast", ctypes.c_int32),
                 ("diag_shift", ctypes.c_void_p), ("precision", ctypes.c_int32), ("partitions", ctypes.c_int32),
-                ("max_refine_iters", ctypes.c_int32), ("refine_tol", ctypes.c_double), ("pdd", ctypes.c_int32)]
+                ("max_refine_iters", ctypes.c_int32), ("refine_tol", ctypes.c_double), ("pdd", ctypes.c_int32),
+                ("refine_kappa", ctypes.c_double)]
 
 
 class PoissonDesc(ctypes.Structure):
@@ -108,6 +109,8 @@ def load_library(build: bool = True) -> ctypes.CDLL:
     lib.tdma_probe_fp64_fma.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _VP,
                                         ctypes.POINTER(ctypes.c_int64), _VP]
     lib.tdma_probe_fp64_fma.restype = st
+    lib.tdma_plan_corrected_lines.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_int64)]
+    lib.tdma_plan_corrected_lines.restype = st
     _LIB = lib
     return lib
 
@@ -187,7 +190,7 @@ class Plan:
     def __init__(self, n, n_lines, elem_stride=1, inner_count=None, inner_stride=None, outer_stride=0,
                  precision="f64", partitions=0, nrhs=1, coef_broadcast=False, diag_shift=None,
                  ragged_offsets=None, ragged_lengths=None, ragged_max_n=0, ragged_total=0,
-                 max_refine_iters=0, refine_tol=0.0, pdd=False):
+                 max_refine_iters=0, refine_tol=0.0, pdd=False, refine_kappa=0.0):
         self._lib = load_library()
         if inner_count is None:
             inner_count = max(1, n_lines)
@@ -200,7 +203,8 @@ class Plan:
                          ragged_max_n=ragged_max_n, ragged_total=ragged_total, nrhs=nrhs,
                          coef_broadcast=int(bool(coef_broadcast)), diag_shift=_ptr(diag_shift),
                          precision=_PREC[precision], partitions=partitions,
-                         max_refine_iters=max_refine_iters, refine_tol=refine_tol, pdd=int(bool(pdd)))
+                         max_refine_iters=max_refine_iters, refine_tol=refine_tol, pdd=int(bool(pdd)),
+                         refine_kappa=refine_kappa)
         self._h = ctypes.c_void_p()
         ws = ctypes.c_size_t(0)
         st = self._lib.tdma_plan_create(ctypes.byref(self._h), ctypes.byref(self.desc), ctypes.byref(ws))
@@ -261,6 +265,15 @@ class Plan:
             self._ws = ws if ws.numel() >= self.workspace_bytes else None
         return cfg
 
+    def corrected_lines(self, stream=None) -> int:
+        """Lines the last TDMA_F64_REFINE solve corrected (the rest kept the plain FP64 result);
+        synchronises the stream."""
+        lines = ctypes.c_int64(0)
+        st = self._lib.tdma_plan_corrected_lines(self._h, _stream(stream), ctypes.byref(lines))
+        if st != 0:
+            raise TDMAError(st, "tdma_plan_corrected_lines")
+        return int(lines.value)
+
     def last_error(self, stream=None):
         """(status, max refinement corrections used); synchronises the stream."""
         info = ctypes.c_int32(0)
@@ -274,9 +287,10 @@ class PoissonFFT:
     tridiagonal operator (a, b, c) along y (1D arrays of length ny, host or CPU tensors). cuFFT over
     every (z, x) plane, one tridiagonal line per wavenumber pair along y, cuFFT back. With
     ``pin_zero_mode`` the (0, 0) line's row 0 becomes Phi_0 = 0 (needed when D_yy has Neumann ends).
-    ``precision`` "f64" or "f64r" (exact-residual correction of the wavenumber lines)."""
+    ``precision`` "f64r" (default: the wavenumber lines whose condition-number bound reaches 1e5, the
+    lowest modes, corrected from an exact residual) or "f64" (plain FP64 elimination)."""
 
-    def __init__(self, nx, ny, nz, dx, dz, a, b, c, pin_zero_mode=True, precision="f64", device="cuda"):
+    def __init__(self, nx, ny, nz, dx, dz, a, b, c, pin_zero_mode=True, precision="f64r", device="cuda"):
         self._lib = load_library()
         ha, hb, hc = (np.ascontiguousarray(np.asarray(t.cpu() if torch.is_tensor(t) else t, dtype=np.float64))
                       for t in (a, b, c))

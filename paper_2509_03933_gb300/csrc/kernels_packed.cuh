@@ -45,7 +45,7 @@ constexpr uint32_t kPackWaitPolls = 1u << 16;
 // Per-line words of the norm table (float bits of non-negative values): [0] max |dx| and [1] max
 // |x_0| of the first correction (zero at launch, written once); [2] max |dx|, [3] max |x| of a
 // further correction and [4] the previous max |dx| (reset by the line's owner after each use).
-constexpr int kPackNormWords = 5;
+constexpr int kPackNormWords = 6;
 
 struct PackedChunk {
   int64_t base;   // element index of the chunk's first row
@@ -266,10 +266,12 @@ TDMA_DEV void packed_coord_b(const float* wsl, float4* dsl, float* csl, uint64_t
 // starts its line; a warp whose rows all belong to one line reduces first and makes one pair.
 struct LineMax {
   unsigned pdx, px;
+  unsigned unc;  // first correction: nonzero if this partition's rows do not certify the floor
   int cur;   // line of the rows being accumulated
   int slot;  // first of the two words written (0: first correction, 2: further ones)
-  TDMA_DEV void init(uint32_t mask, int m, int line, int slot_) {
+  TDMA_DEV void init(uint32_t mask, int m, int line, int slot_, unsigned unc_ = 0u) {
     pdx = px = 0u;
+    unc = unc_;
     slot = slot_;
     cur = line + __popc(mask & ~1u & ((1u << m) - 1u));
   }
@@ -279,6 +281,7 @@ struct LineMax {
     if (t > 0 && ((mask >> t) & 1u)) {  // row t starts line `cur`: its piece is complete
       atomicMax(&norms[kPackNormWords * cur + slot], pdx);
       atomicMax(&norms[kPackNormWords * cur + slot + 1], px);
+      if (unc) atomicMax(&norms[kPackNormWords * cur + 5], unc);
       pdx = px = 0u;
       --cur;
     }
@@ -291,28 +294,30 @@ struct LineMax {
       for (int o = 16; o >= 1; o >>= 1) {
         pdx = max(pdx, __shfl_xor_sync(~0u, pdx, o));
         px = max(px, __shfl_xor_sync(~0u, px, o));
+        unc = max(unc, __shfl_xor_sync(~0u, unc, o));
       }
       const int l0 = __shfl_sync(~0u, cur, 0);
       if (lane == 0) {
         atomicMax(&norms[kPackNormWords * l0 + slot], pdx);
         atomicMax(&norms[kPackNormWords * l0 + slot + 1], px);
+        if (unc) atomicMax(&norms[kPackNormWords * l0 + 5], unc);
       }
     } else if (m > 0) {
       atomicMax(&norms[kPackNormWords * cur + slot], pdx);
       atomicMax(&norms[kPackNormWords * cur + slot + 1], px);
+      if (unc) atomicMax(&norms[kPackNormWords * cur + 5], unc);
     }
   }
 };
 
-// Stop rule of the refinement, as in the other refinement kernels: a line is done when its
+// Stop rule of the refinement, as in the other refinement kernels (refine_done): a line whose
+// rows certify the float-pair residual's floor (word 5 of its table entry is 0) is done when its
 // estimated error rho |dx| <= tol |x| with rho = |dx| / |dx_prev| (|dx_prev| = |x_0| after the first
-// correction). A non-finite norm ends the line with status 5.
-TDMA_DEV bool line_rule(uint32_t gdx, uint32_t gx, uint32_t prev, float tol, bool& bad) {
+// correction); another line when |dx| <= tol |x|. A non-finite norm ends the line with status 5.
+TDMA_DEV bool line_rule(uint32_t gdx, uint32_t gx, uint32_t prev, float tol, bool certified, bool& bad) {
   bad = !(bits_finite(gdx) && bits_finite(gx));
   if (bad) return true;
-  const float dxn = __uint_as_float(gdx), xn = __uint_as_float(gx), pv = __uint_as_float(prev);
-  const float ratio = pv > 0.f ? dxn / pv : 0.f;
-  return ratio * dxn <= tol * xn || dxn == 0.f;
+  return refine_done(__uint_as_float(gdx), __uint_as_float(gx), __uint_as_float(prev), tol, certified);
 }
 
 // After the first correction: every CTA of the cluster reads the norms of all lines of the chunk
@@ -324,9 +329,9 @@ TDMA_DEV bool packed_first_verdict(const PackedChunk& ch, const uint32_t* norms,
   bool more = false;
   for (int l = threadIdx.x; l < ch.nlines; l += blockDim.x) {
     const uint32_t* nl = norms + (int64_t)kPackNormWords * (ch.line0 + l);
-    const uint32_t gdx = ld_relaxed_u32(nl), gx = ld_relaxed_u32(nl + 1);
+    const uint32_t gdx = ld_relaxed_u32(nl), gx = ld_relaxed_u32(nl + 1), unc = ld_relaxed_u32(nl + 5);
     bool bad;
-    const bool done = line_rule(gdx, gx, gx, tol, bad);
+    const bool done = line_rule(gdx, gx, gx, tol, unc == 0u, bad);
     if (bad && reporter) report_error(st, 5);
     if (!done) {
       if (last_pass) { if (reporter) report_error(st, 7); }
@@ -349,11 +354,12 @@ TDMA_DEV bool packed_later_verdict(uint32_t mask, int m, int line, uint32_t* nor
     uint32_t* nl = norms + (int64_t)kPackNormWords * L;
     const uint32_t gdx = ld_relaxed_u32(nl + 2), gx = ld_relaxed_u32(nl + 3);
     const uint32_t prev = ld_relaxed_u32(nl + (first_later ? 0 : 4));
+    const uint32_t unc = ld_relaxed_u32(nl + 5);
     nl[2] = 0u;
     nl[3] = 0u;
     nl[4] = gdx;
     bool bad;
-    const bool done = line_rule(gdx, gx, prev, tol, bad);
+    const bool done = line_rule(gdx, gx, prev, tol, unc == 0u, bad);
     if (bad) report_error(st, 5);
     if (!done) {
       if (last_pass) report_error(st, 7);
@@ -426,16 +432,20 @@ __device__ __noinline__ void packed_later_pass(const PackedTables& PT, const flo
 template <int MM>
 TDMA_DEV void packed_passes(const float* ra, const float* rb, const float* rc, const double* rd, float2* rd2,
                             float2* rx, float* wsl0, const float4* dsl0, float* wsl1, const float4* dsl1, int w,
-                            int lane, bool edge_s, bool edge_e, uint32_t mask, int line, uint32_t* norms) {
+                            int lane, bool edge_s, bool edge_e, uint32_t mask, int line, uint32_t* norms,
+                            float keep) {
   Sweep<MM> S;
   float x0[MM];
   float u0, v0;
+  float dom = -INFINITY;  // max over this partition's rows of dom_excess
   {
 #pragma unroll
     for (int t = 0; t < MM; ++t) {
       const ff dd = split_f64_fast(rd[t * kPackPitch]);
       rd2[t * kPackPitch] = make_float2(dd.h, dd.l);  // same thread, same 8 bytes
-      S.row(t, ra[t * kPackPitch], rb[t * kPackPitch], rc[t * kPackPitch], dd.h);
+      const float a = ra[t * kPackPitch], b = rb[t * kPackPitch], c = rc[t * kPackPitch];
+      dom = fmaxf(dom, dom_excess(a, b, c, keep));
+      S.row(t, a, b, c, dd.h);
     }
     const Blk blk = S.block();
     float u, v;
@@ -463,7 +473,7 @@ TDMA_DEV void packed_passes(const float* ra, const float* rb, const float* rc, c
     const float xs = edge_s ? e.xs : Sweep<MM>::first(blk, u, v);
     const float xe = edge_e ? e.xe : Sweep<MM>::last(blk, u, v);
     LineMax nm;
-    nm.init(mask, MM, line, 0);
+    nm.init(mask, MM, line, 0, __float_as_uint(fmaxf(dom, 0.f)));
     S.solve_visit(xs, xe, [&](int t, float dxv) {
       rx[t * kPackPitch] = make_float2(x0[t], dxv);
       nm.add(t, mask, dxv, x0[t], norms);
@@ -560,6 +570,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
   __shared__ __align__(16) float csl[2][C * 8];  // CTA blocks of the cluster, by pass parity
   __shared__ uint32_t s_more;                    // epoch stamp: some line of the chunk needs more
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const float keep = certify_keep(A.tol);
   const bool coord = w == kPackW;
   const int rank = (int)cluster_rank();
   const int kp = rank * kPackT + tid;  // partition index within the chunk (compute threads)
@@ -637,7 +648,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
 #define TDMA_PASSES(MM)                                                                             \
   case MM:                                                                                           \
     packed_passes<MM>(ra, rb, rc, rd, rd2, tx + tid, wsl[0], dsl[0], wsl[1], dsl[1], w, lane, edge_s, edge_e, \
-                      mask, line, PT.norms);                                                         \
+                      mask, line, PT.norms, keep);                                                   \
     break;
         TDMA_PACKED_M(TDMA_PASSES)
 #undef TDMA_PASSES

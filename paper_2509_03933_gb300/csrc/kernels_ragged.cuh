@@ -181,6 +181,9 @@ __global__ void __launch_bounds__(kRaggedThreads) ragged_refine_kernel(const Arg
     if (tid < cnt) { s_nrm[2 * tid] = 0u; s_nrm[2 * tid + 1] = 0u; }
     int it = 0;
     bool line_done = false;
+    const float keep = certify_keep(A.tol);
+    float dom = -INFINITY;  // max over this partition's rows of dom_excess
+    bool certified = true;  // the group's rows certify the floor
     for (;; ++it) {
       // ---- Stage A
       if (active) {
@@ -196,6 +199,7 @@ __global__ void __launch_bounds__(kRaggedThreads) ragged_refine_kernel(const Arg
           float a = (k == 0 && t == 0) ? 0.f : (TR ? ldg(pc + t - 1) : ldg(pa + t));
           const float b = ldg(pb + t);
           float c = (k == P - 1 && t == m - 1) ? 0.f : (TR ? ldg(pa + t + 1) : ldg(pc + t));
+          if (it == 0) dom = fmaxf(dom, dom_excess(a, b, c, keep));
           const ff dd = split_f64(ldg(pd + t));
           float rhs;
           if (it == 0) {
@@ -240,7 +244,7 @@ __global__ void __launch_bounds__(kRaggedThreads) ragged_refine_kernel(const Arg
           R[3 * R2 + 2 * k + 1] = delta;
         }
       }
-      __syncthreads();
+      if (__syncthreads_or(it == 0 && dom > 0.f)) certified = false;
       // ---- Stage B: one thread per line
       if (tid < cnt && n > 1) {
         const bool ok = (it == 0) ? reduced_factor_solve<float>(R, R + R2, R + 2 * R2, R + 3 * R2, R2)
@@ -283,8 +287,7 @@ __global__ void __launch_bounds__(kRaggedThreads) ragged_refine_kernel(const Arg
         s_nrm[2 * tid] = 0u;
         s_nrm[2 * tid + 1] = 0u;
         if (it > 0) {
-          const float ratio = s_prev[tid] > 0.f ? dxn / s_prev[tid] : 0.f;
-          line_done = (ratio * dxn <= A.tol * xn) || dxn == 0.f;
+          line_done = refine_done(dxn, xn, s_prev[tid], A.tol, certified);
         } else {
           line_done = (xn == 0.f);
         }

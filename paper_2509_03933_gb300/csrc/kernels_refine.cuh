@@ -17,9 +17,20 @@
 // halves in FP64. Stage B (the reduced endpoint solve) runs in FP64 when SB64 is set.
 //
 // Convergence (per line, infinity norms): with dx_0 = x_0, rho_t = |dx_t| / |dx_{t-1}| is the
-// observed contraction and rho_t |dx_t| estimates the error left after the update; a line is
-// done once rho_t |dx_t| <= tol |x|. The block stops when all of its lines are done or after
-// max_iters corrections; lines still above the tolerance then raise TDMA_ERR_NOT_CONVERGED.
+// observed contraction and rho_t |dx_t| estimates the error left after the update. That estimate
+// knows nothing of the accuracy floor of the float-pair residual: its rounding errors, about 2^-48
+// of the residual's terms, reach x amplified by the condition number, and the refinement cannot
+// get below about kappa 2^-52 |x| (measured; kappa 2^-48 in the worst case). A line is therefore
+// done once rho_t |dx_t| <= tol |x| only when its floor is certified below tol: every row is
+// diagonally dominant with 1 - (|a_i| + |c_i|) / |b_i| >= theta and 2^-51 / theta <= tol, which
+// bounds the condition number of the row-scaled matrix by 1 / theta (Varah 1975: a row-diagonally
+// dominant matrix has ||A^-1||_inf <= 1 / min_i (|a_ii| - sum_j |a_ij|)). Other lines are done only
+// when the last correction itself is below tol |x| (at the floor the corrections stay at its level,
+// so such lines end with TDMA_ERR_NOT_CONVERGED instead of a result short of the tolerance). The
+// certificate is evaluated per line where the kernel gathers its lines' norms anyway and per block
+// elsewhere (a block with one uncertified row applies the strict rule to all of its lines). The
+// block stops when all of its lines are done or after max_iters corrections; lines still above the
+// tolerance then raise TDMA_ERR_NOT_CONVERGED.
 #pragma once
 #include "layout.cuh"
 #include "kernels_dc.cuh"
@@ -80,6 +91,20 @@ TDMA_DEV float narrow(float v) { return v; }
 TDMA_DEV float narrow(double v) { return __double2float_rn(v); }
 
 struct Coef { float a, b, c; double d; };
+
+// ---- certified stop rule (see the header)
+constexpr float kRefineFloor = 4.440892098500626e-16f;  // 2^-51: twice the measured floor per unit condition
+// keep = 1 - 2^-51 / tol; a row is certified when |a| + |c| <= keep |b|
+TDMA_DEV float certify_keep(float tol) { return 1.f - kRefineFloor / tol; }
+// |a| + |c| - keep |b|: positive when the row is not dominant enough to certify the floor
+TDMA_DEV float dom_excess(float a, float b, float c, float keep) { return fmaf(-keep, fabsf(b), fabsf(a) + fabsf(c)); }
+// Stop rule of a line after a correction: |dx|, |x| and the previous |dx| (|x_0| after the first).
+TDMA_DEV bool refine_done(float dxn, float xn, float prev, float tol, bool certified) {
+  if (dxn == 0.f) return true;
+  if (!certified) return dxn <= tol * xn;
+  const float ratio = prev > 0.f ? dxn / prev : 0.f;
+  return ratio * dxn <= tol * xn;
+}
 
 // Row i (or with TR the transposed row, as load_row) of the float coefficients and double d.
 template <bool TR = false>
@@ -152,6 +177,9 @@ __global__ void __launch_bounds__(512) refine_kernel(const Args A) {
   float a0 = 0.f, b0 = 1.f, c0 = 0.f, rho = 1.f;
   float prev_dx = 0.f;  // line owner: |dx_{t-1}|
   bool line_done = !active;
+  const float keep = certify_keep(A.tol);
+  float dom = -INFINITY;  // max over this partition's rows of dom_excess
+  bool certified = true;  // the block's rows certify the floor
   __syncthreads();
 
   int it = 0;
@@ -171,6 +199,7 @@ __global__ void __launch_bounds__(512) refine_kernel(const Args A) {
         load_coef<TR>(cf, A, base + (start + t) * es, start + t);
         if (k == 0 && t == 0) cf.a = 0.f;
         if (k == P - 1 && t == m - 1) cf.c = 0.f;
+        if (it == 0) dom = fmaxf(dom, dom_excess(cf.a, cf.b, cf.c, keep));
         const ff dd = split_f64(cf.d);
         float rhs;
         if (it == 0) {
@@ -228,7 +257,7 @@ __global__ void __launch_bounds__(512) refine_kernel(const Args A) {
         r_rhs[2 * k + 1] = widen<BT>(rhs_last);
       }
     }
-    __syncthreads();
+    if (__syncthreads_or(it == 0 && dom > 0.f)) certified = false;
     // ------------- Stage B
     if (!single && tid < Lb && (int64_t)blockIdx.x * Lb + tid < A.lay.n_lines) {
       BT* sub = red + (size_t)tid * pitch;
@@ -275,8 +304,7 @@ __global__ void __launch_bounds__(512) refine_kernel(const Args A) {
       s_red[4 * tid + 2 * (par ^ 1) + 1] = 0u;
       const bool live = (int64_t)blockIdx.x * Lb + tid < A.lay.n_lines;
       if (live && it > 0) {
-        const float ratio = prev_dx > 0.f ? mdx / prev_dx : 0.f;
-        line_done = (ratio * mdx <= A.tol * mx) || mdx == 0.f;
+        line_done = refine_done(mdx, mx, prev_dx, A.tol, certified);
       } else if (live) {
         line_done = (mx == 0.f);
       }

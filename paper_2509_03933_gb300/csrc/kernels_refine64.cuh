@@ -24,26 +24,81 @@
 
 namespace tdma {
 
-// r = d - A x exactly for every (line, row), one thread each (adjacent threads on adjacent lines),
-// into R ([row][line], nrhs floats each).
+// Lines to correct (coefficients broadcast to all lines, optional per-line shift): line l is listed
+// unless its condition-number bound is below kappa_max. For a row-diagonally-dominant A,
+// ||A^-1||_inf <= 1 / delta with delta = min_i (|b_i| - |a_i| - |c_i|) (Varah 1975), so
+// kappa_inf(A) <= ||A||_inf / delta. Both are evaluated in float (rounding about 2^-24 of the row
+// sums, far inside the factor of two of slack taken below: a line is kept off the list only if
+// ||A|| < delta kappa_max / 2). Lines without a positive margin are always listed. The rows are
+// staged in shared memory as floats (b_i, |a_i| + |c_i|), kSelectRows at a time; one thread per
+// line, grid-stride. Listed lines go to list[0 .. *count) (order unspecified).
+constexpr int kSelectRows = 2048;
+
+__global__ void __launch_bounds__(256) select_lines_kernel(const Args A, float kappa_max, int32_t* __restrict__ list,
+                                                           int32_t* count) {
+  __shared__ float sb[kSelectRows], sac[kSelectRows];
+  const int64_t n = A.lay.n, L = A.lay.n_lines;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  const int64_t first = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  // every block walks the same number of line rounds (the barriers below need all its threads)
+  const int64_t rounds = (L + stride - 1) / stride;
+  for (int64_t r = 0; r < rounds; ++r) {
+    const int64_t line = first + r * stride;
+    const bool active = line < L;
+    const float s = (active && A.shift) ? (float)ldg((const double*)A.shift + line) : 0.f;
+    float margin = INFINITY, norm = 0.f;
+    for (int64_t i0 = 0; i0 < n; i0 += kSelectRows) {
+      const int rows = (int)(n - i0 < kSelectRows ? n - i0 : kSelectRows);
+      __syncthreads();
+      for (int t = threadIdx.x; t < rows; t += blockDim.x) {
+        const int64_t i = i0 + t;
+        const double av = i > 0 ? fabs(ldg((const double*)A.a + i)) : 0.0;
+        const double cv = i < n - 1 ? fabs(ldg((const double*)A.c + i)) : 0.0;
+        sb[t] = (float)ldg((const double*)A.b + i);
+        sac[t] = (float)(av + cv);
+      }
+      __syncthreads();
+      if (active) {
+        for (int t = 0; t < rows; ++t) {
+          const float bb = fabsf(sb[t] + s);
+          margin = fminf(margin, bb - sac[t]);
+          norm = fmaxf(norm, bb + sac[t]);
+        }
+      }
+    }
+    if (active && !(margin > 0.f && norm < 0.5f * kappa_max * margin)) list[atomicAdd(count, 1)] = (int32_t)line;
+  }
+}
+
+// r = d - A x exactly for every (line, row) of the corrected lines, one thread each (adjacent
+// threads on adjacent lines), grid-stride, into R ([row][k], nrhs floats each, row pitch n_lines).
+// Line k is list[k] for k < *count, or every line k when list is null (then n_lines is written to
+// *count, the number of corrected lines the plan reports).
 template <int NR>
-__global__ void __launch_bounds__(256) residual_exact_kernel(const Args A, float* __restrict__ R) {
+__global__ void __launch_bounds__(256) residual_exact_kernel(const Args A, float* __restrict__ R,
+                                                             const int32_t* __restrict__ list, int32_t* count) {
   const Layout& L = A.lay;
-  const int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= L.n * L.n_lines) return;
-  const int64_t line = idx % L.n_lines, i = idx / L.n_lines;
-  const int64_t e = L.off(line) + i * L.es, ci = A.bcast ? i : e;
-  const double shift = A.shift ? ldg((const double*)A.shift + line) : 0.0;
-  const DecF64 da = dec_f64(i > 0 ? ldg((const double*)A.a + ci) : 0.0);
-  const DecF64 db = dec_f64(ldg((const double*)A.b + ci) + shift);  // the b of the FP64 solve
-  const DecF64 dc = dec_f64(i < L.n - 1 ? ldg((const double*)A.c + ci) : 0.0);
-  const double* X = (const double*)A.x;
-  const double* D = (const double*)A.d;
+  const int64_t cnt = list ? (int64_t)*count : L.n_lines;
+  if (!list && blockIdx.x == 0 && threadIdx.x == 0) *count = (int32_t)L.n_lines;
+  const int64_t total = L.n * cnt;
+  for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t k = idx % cnt, i = idx / cnt;
+    const int64_t line = list ? (int64_t)list[k] : k;
+    const int64_t e = L.off(line) + i * L.es, ci = A.bcast ? i : e;
+    const double shift = A.shift ? ldg((const double*)A.shift + line) : 0.0;
+    const DecF64 da = dec_f64(i > 0 ? ldg((const double*)A.a + ci) : 0.0);
+    const DecF64 db = dec_f64(ldg((const double*)A.b + ci) + shift);  // the b of the FP64 solve
+    const DecF64 dc = dec_f64(i < L.n - 1 ? ldg((const double*)A.c + ci) : 0.0);
+    const double* X = (const double*)A.x;
+    const double* D = (const double*)A.d;
+    const int64_t r = i * L.n_lines + k;
 #pragma unroll
-  for (int q = 0; q < NR; ++q) {
-    const DecF64 dxm = dec_f64(i > 0 ? X[(e - L.es) * NR + q] : 0.0);
-    const DecF64 dxp = dec_f64(i < L.n - 1 ? X[(e + L.es) * NR + q] : 0.0);
-    R[idx * NR + q] = residual_exact_dec(dec_f64(ldg(D + e * NR + q)), da, dxm, db, dec_f64(X[e * NR + q]), dc, dxp);
+    for (int q = 0; q < NR; ++q) {
+      const DecF64 dxm = dec_f64(i > 0 ? X[(e - L.es) * NR + q] : 0.0);
+      const DecF64 dxp = dec_f64(i < L.n - 1 ? X[(e + L.es) * NR + q] : 0.0);
+      R[r * NR + q] = residual_exact_dec(dec_f64(ldg(D + e * NR + q)), da, dxm, db, dec_f64(X[e * NR + q]), dc, dxp);
+    }
   }
 }
 
@@ -54,16 +109,27 @@ __global__ void __launch_bounds__(256) residual_exact_kernel(const Args A, float
 constexpr int kCorrAhead = 4;
 
 template <int NR>
-__global__ void __launch_bounds__(128) correction32_kernel(const Args A, float* __restrict__ cw, float* __restrict__ R) {
+TDMA_DEV void correct_line(const Args& A, float* __restrict__ cw, float* __restrict__ R, int64_t k, int64_t line);
+
+// Line k (as in residual_exact_kernel) uses column k of R and cw; grid-stride over k.
+template <int NR>
+__global__ void __launch_bounds__(128) correction32_kernel(const Args A, float* __restrict__ cw, float* __restrict__ R,
+                                                           const int32_t* __restrict__ list, const int32_t* count) {
+  const int64_t cnt = list ? (int64_t)*count : A.lay.n_lines;
+  for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < cnt; k += (int64_t)gridDim.x * blockDim.x)
+    correct_line<NR>(A, cw, R, k, list ? (int64_t)list[k] : k);
+}
+
+// The correction of one line: column k of R and cw.
+template <int NR>
+TDMA_DEV void correct_line(const Args& A, float* __restrict__ cw, float* __restrict__ R, int64_t k, int64_t line) {
   constexpr int K = kCorrAhead;
-  const int64_t line = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (line >= A.lay.n_lines) return;
   const int64_t n = A.lay.n, es = A.lay.es, L = A.lay.n_lines;
   const int64_t base = A.lay.off(line);
   const double shift = A.shift ? ldg((const double*)A.shift + line) : 0.0;
   double* X = (double*)A.x;
-  float* Rl = R + line * NR;   // row i at Rl[i * L * NR + q]
-  float* cwl = cw + line;      // row i at cwl[i * L]
+  float* Rl = R + k * NR;   // row i at Rl[i * L * NR + q]
+  float* cwl = cw + k;      // row i at cwl[i * L]
   float cp = 0.f, rp[NR];
 #pragma unroll
   for (int q = 0; q < NR; ++q) rp[q] = 0.f;

@@ -106,6 +106,9 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
   float al[M], ga[M], de[M], xh[M];
   float a0 = 0.f, c0 = 0.f, rho = 1.f, prev_dx = 0.f;
   bool line_done = !active;
+  const float keep = certify_keep(A.tol);
+  float dom = -INFINITY;  // max over this partition's rows of dom_excess
+  bool certified = true;  // line owner: every row of the line (all CTAs) certifies the floor
   const float* ex_prev = rank > 0 ? cluster.map_shared_rank(s_ex, rank - 1) : s_ex;
   const float* ex_next = rank < C - 1 ? cluster.map_shared_rank(s_ex, rank + 1) : s_ex;
 
@@ -132,6 +135,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
       float a = ca[t * T], b = cb[t * T], c = cc[t * T];
       if (t == 0 && first_part) a = 0.f;
       if (t == M - 1 && last_part) c = 0.f;
+      if (it == 0) dom = fmaxf(dom, dom_excess(a, b, c, keep));
       float rhs;
       if (it == 0) {
         const ff dd = split_f64(cd[t * T]);
@@ -288,14 +292,22 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
       }
       if (tid == 0) s_done = 1;
     } else {
-      // the first correction always runs; keep |x_0| per line for the contraction estimate
+      // the first correction always runs; keep |x_0| per line for the contraction estimate, and
+      // whether the line's rows in this CTA certify the refinement's floor (word 3: 0 if they do)
+      unsigned unc = __float_as_uint(fmaxf(dom, 0.f));
       if (Lb < 32) {
 #pragma unroll
-        for (int off = Lb; off < 32; off <<= 1) mdx = fmaxf(mdx, __shfl_xor_sync(0xffffffffu, mdx, off));
+        for (int off = Lb; off < 32; off <<= 1) {
+          mdx = fmaxf(mdx, __shfl_xor_sync(0xffffffffu, mdx, off));
+          unc = max(unc, __shfl_xor_sync(0xffffffffu, unc, off));
+        }
       }
-      if (tid < Lb) s_nrm[4 * tid + 2] = 0u;
+      if (tid < Lb) { s_nrm[4 * tid + 2] = 0u; s_nrm[4 * tid + 3] = 0u; }
       __syncthreads();
-      if ((tid & 31) < Lb || Lb >= 32) atomicMax(&s_nrm[4 * j + 2], __float_as_uint(mdx));
+      if ((tid & 31) < Lb || Lb >= 32) {
+        atomicMax(&s_nrm[4 * j + 2], __float_as_uint(mdx));
+        atomicMax(&s_nrm[4 * j + 3], unc);
+      }
     }
     cluster.sync();  // endpoints and norms of every CTA visible
     // thread (j, q) fetches CTA q's maxima of line j; the line owner reduces them
@@ -304,6 +316,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
       const unsigned* nq = cluster.map_shared_rank(s_nrm, k);
       if (it == 0) {
         gn[2 * k] = __uint_as_float(nq[4 * j + 2]);
+        gn[2 * k + 1] = __uint_as_float(nq[4 * j + 3]);
       } else {
         const unsigned u0v = nq[4 * j + 2 * par], u1v = nq[4 * j + 2 * par + 1];
         gn[2 * k] = __uint_as_float(u0v);
@@ -314,9 +327,14 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
     if (it == 0) {
       if (tid < Lb) {
         float m0 = 0.f;
+        unsigned u = 0u;
 #pragma unroll
-        for (int q = 0; q < C; ++q) m0 = fmaxf(m0, gn[2 * q]);
+        for (int q = 0; q < C; ++q) {
+          m0 = fmaxf(m0, gn[2 * q]);
+          u = max(u, __float_as_uint(gn[2 * q + 1]));
+        }
         prev_dx = m0;
+        certified = (u == 0u);
       }
       if (stop) break;
       continue;
@@ -329,8 +347,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
         xn = fmaxf(xn, gn[2 * q + 1]);
       }
       if (tid < lines_left) {
-        const float ratio = prev_dx > 0.f ? dxn / prev_dx : 0.f;
-        line_done = (ratio * dxn <= A.tol * xn) || dxn == 0.f;
+        line_done = refine_done(dxn, xn, prev_dx, A.tol, certified);
         prev_dx = dxn;
         if (rank == 0 && !(finite(dxn) && finite(xn))) report_error(A.st, 5);
         if (!line_done) s_done = 0;

@@ -61,6 +61,9 @@ __global__ void __launch_bounds__(256, MINB) refine_reg_kernel(const Args A) {
   for (int t = 0; t < M; ++t) { al[t] = 0.f; ga[t] = 0.f; de[t] = 0.f; xh[t] = 0.f; }
   float a0 = 0.f, c0 = 0.f, rho = 1.f, prev_dx = 0.f;
   bool line_done = !active;
+  const float keep = certify_keep(A.tol);
+  float dom = -INFINITY;  // max over this partition's rows of dom_excess
+  bool certified = true;  // the block's rows certify the floor
   if (tid < Lb) { s_nrm[4 * tid] = 0u; s_nrm[4 * tid + 1] = 0u; s_nrm[4 * tid + 2] = 0u; s_nrm[4 * tid + 3] = 0u; }
 #pragma unroll
   for (int t = 0; t < M; ++t) s_xl[(size_t)t * T + tid] = 0.f;
@@ -83,6 +86,7 @@ __global__ void __launch_bounds__(256, MINB) refine_reg_kernel(const Args A) {
         const double dv = ldg(pd + t * es);
         if (first_part && t == 0) a = 0.f;
         if (last_part && t == m - 1) c = 0.f;
+        if (it == 0) dom = fmaxf(dom, dom_excess(a, b, c, keep));
         float rhs;
         if (it == 0) {
           const ff dd = split_f64(dv);
@@ -131,7 +135,7 @@ __global__ void __launch_bounds__(256, MINB) refine_reg_kernel(const Args A) {
       r_rhs[2 * k] = widen<BT>(rho * (rhs0 - c0 * F));
       r_rhs[2 * k + 1] = widen<BT>(rhs_last);
     }
-    __syncthreads();
+    if (__syncthreads_or(it == 0 && dom > 0.f)) certified = false;
     // ---------------- Stage B: one thread per line
     if (tid < Lb && (int64_t)blockIdx.x * Lb + tid < A.lay.n_lines) {
       BT* sub = red + (size_t)tid * pitch;
@@ -190,8 +194,7 @@ __global__ void __launch_bounds__(256, MINB) refine_reg_kernel(const Args A) {
       const bool live = (int64_t)blockIdx.x * Lb + tid < A.lay.n_lines;
       if (live) {
         if (it > 0) {
-          const float ratio = prev_dx > 0.f ? dxn / prev_dx : 0.f;
-          line_done = (ratio * dxn <= A.tol * xn) || dxn == 0.f;
+          line_done = refine_done(dxn, xn, prev_dx, A.tol, certified);
         } else {
           line_done = (xn == 0.f);
         }

@@ -204,6 +204,9 @@ __global__ void __launch_bounds__(256, MINB)
   for (int t = 0; t < M; ++t) { al[t] = 0.f; ga[t] = 0.f; de[t] = 0.f; xh[t] = 0.f; }
   float a0 = 0.f, c0 = 0.f, rho = 1.f, prev_dx = 0.f;
   bool line_done = !active;
+  const float keep = certify_keep(A.tol);
+  float dom = -INFINITY;  // max over this partition's rows of dom_excess
+  bool certified = true;  // the block's rows certify the floor
 
   int it = 0;
   for (;; ++it) {
@@ -223,6 +226,7 @@ __global__ void __launch_bounds__(256, MINB)
         const double dv = t_d[o];
         if (first_part && t == 0) a = 0.f;
         if (last_part && t == m - 1) c = 0.f;
+        if (it == 0) dom = fmaxf(dom, dom_excess(a, b, c, keep));
         float rhs;
         if (it == 0) {
           rhs = split_f64(dv).h;
@@ -270,7 +274,7 @@ __global__ void __launch_bounds__(256, MINB)
       R[RL.rhs() + 2 * k] = rho * (rhs0 - c0 * F);
       R[RL.rhs() + 2 * k + 1] = rhs_last;
     }
-    __syncthreads();
+    if (__syncthreads_or(it == 0 && dom > 0.f)) certified = false;
     // ---------------- Stage B (two levels, contains barriers)
     if (!reduced_two_level(red, RL, Lb, tid, it == 0, lines_left)) report_error(A.st, 5);
     // ---------------- Stage C and update
@@ -322,8 +326,7 @@ __global__ void __launch_bounds__(256, MINB)
       s_nrm[4 * tid + 2 * (par ^ 1) + 1] = 0u;
       if (tid < lines_left) {
         if (it > 0) {
-          const float ratio = prev_dx > 0.f ? dxn / prev_dx : 0.f;
-          line_done = (ratio * dxn <= A.tol * xn) || dxn == 0.f;
+          line_done = refine_done(dxn, xn, prev_dx, A.tol, certified);
         } else {
           line_done = (xn == 0.f);
         }
@@ -447,6 +450,9 @@ __global__ void __launch_bounds__(256, 2)
   float al[M], ga[M], de[M], xh[M];
   float a0 = 0.f, c0 = 0.f, rho = 1.f, prev_dx = 0.f;
   bool line_done = !active;
+  const float keep = certify_keep(A.tol);
+  float dom = -INFINITY;  // max over this partition's rows of dom_excess
+  bool certified = true;  // the block's rows certify the floor
 
   int it = 0;
   for (;; ++it) {
@@ -462,6 +468,7 @@ __global__ void __launch_bounds__(256, 2)
       float a = ca[t * T], b = cb[t * T], c = cc[t * T];
       if (t == 0 && first_part) a = 0.f;
       if (t == M - 1 && last_part) c = 0.f;
+      if (it == 0) dom = fmaxf(dom, dom_excess(a, b, c, keep));
       float rhs;
       if (it == 0) {
         const ff dd = split_f64(cd[t * T]);
@@ -508,7 +515,7 @@ __global__ void __launch_bounds__(256, 2)
       R[RL.rhs() + 2 * k] = rho * (rhs0 - c0 * F);
       R[RL.rhs() + 2 * k + 1] = delta;
     }
-    __syncthreads();
+    if (__syncthreads_or(it == 0 && dom > 0.f)) certified = false;
     if (!reduced_two_level(red, RL, Lb, tid, it == 0, lines_left)) report_error(A.st, 5);
     // ---------------- Stage C and update
     const float u0 = R[RL.rhs() + 2 * k], un = R[RL.rhs() + 2 * k + 1];
@@ -552,8 +559,7 @@ __global__ void __launch_bounds__(256, 2)
       s_nrm[4 * tid + 2 * (par ^ 1) + 1] = 0u;
       if (tid < lines_left) {
         if (it > 0) {
-          const float ratio = prev_dx > 0.f ? dxn / prev_dx : 0.f;
-          line_done = (ratio * dxn <= A.tol * xn) || dxn == 0.f;
+          line_done = refine_done(dxn, xn, prev_dx, A.tol, certified);
         } else {
           line_done = (xn == 0.f);
         }

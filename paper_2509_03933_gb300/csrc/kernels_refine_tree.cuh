@@ -203,19 +203,20 @@ struct Sweep {
   }
 };
 
-// Per-line stop rule of the refinement: rho |dx|_inf <= tol |x|_inf with the contraction
-// estimate rho = |dx| / |dx_prev| (|dx_0| = |x_0|). A non-finite norm ends the line with status 5.
-TDMA_DEV bool tree_line_done(unsigned gdx, unsigned gxm, unsigned& prev, bool active, float tol, bool reporter,
-                             DevStatus* st) {
+// Per-line stop rule of the refinement (refine_done): for a line whose rows certify the float-pair
+// residual's floor, rho |dx|_inf <= tol |x|_inf with the contraction estimate rho = |dx| / |dx_prev|
+// (|dx_0| = |x_0|); for another line |dx|_inf <= tol |x|_inf. A non-finite norm ends the line with
+// status 5.
+TDMA_DEV bool tree_line_done(unsigned gdx, unsigned gxm, unsigned& prev, bool active, float tol, bool certified,
+                             bool reporter, DevStatus* st) {
   if (!active) return true;
   if (!(bits_finite(gdx) && bits_finite(gxm))) {
     if (reporter) report_error(st, 5);
     return true;
   }
-  const float dxn = __uint_as_float(gdx), xn = __uint_as_float(gxm), pv = __uint_as_float(prev);
+  const float pv = __uint_as_float(prev);
   prev = gdx;
-  const float ratio = pv > 0.f ? dxn / pv : 0.f;
-  return ratio * dxn <= tol * xn || dxn == 0.f;
+  return refine_done(__uint_as_float(gdx), __uint_as_float(gxm), pv, tol, certified);
 }
 
 // Persistent: the grid holds the clusters that fit on the GPU at once, and cluster k takes line
@@ -261,6 +262,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
   double* const tx = reinterpret_cast<double*>(ta);
   double* rx = tx + (rd - td);
   const int64_t es = A.lay.es, ic = A.lay.ic;
+  const float keep = certify_keep(A.tol);
 
   if (tid == 0) {
     mbar_init(&bar[0], 1);
@@ -316,8 +318,10 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
     float x0[M];
     float u0, v0;
     unsigned nx;
+    bool certified;  // the line's rows (all CTAs) certify the floor of the float-pair residual
     Sweep<M> S;  // its factors serve pass 1 as well (same matrix)
     {
+      float dom = -INFINITY;  // max over this partition's rows of dom_excess
 #pragma unroll
       for (int t = 0; t < M; ++t) {
         if (t == H) {  // the second half of the rows (the first half is being swept meanwhile)
@@ -330,6 +334,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
         float a = ra[t * 256], b = rb[t * 256], c = rc[t * 256];
         if (t == 0 && first_part) a = 0.f;
         if (t == M - 1 && last_part) c = 0.f;
+        dom = fmaxf(dom, dom_excess(a, b, c, keep));
         const ff dd = split_f64_fast(rd[t * 128]);
         rd2[t * 128] = make_float2(dd.h, dd.l);  // same thread, same 8 bytes: read before write
         S.row(t, a, b, c, dd.h);
@@ -339,10 +344,13 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
         cluster_wait();  // every CTA of the cluster has started
         started = true;
       }
-      unsigned unused;
+      // rides on the exchange as `extra`: 0 when every row of this CTA's part of the line certifies
+      const unsigned unc = line_max(__float_as_uint(fmaxf(dom, 0.f)));
+      unsigned unc_line;
       float xs_c, xe_c;
-      tree_stage_b<C>(blk, 0u, slots, &xbar[0], xph0 & 1u, rank, p, jj, j, u0, v0, xs_c, xe_c, unused, alive, A.st);
+      tree_stage_b<C>(blk, unc, slots, &xbar[0], xph0 & 1u, rank, p, jj, j, u0, v0, xs_c, xe_c, unc_line, alive, A.st);
       ++xph0;
+      certified = unc_line == 0u;
       // Boundary unknowns exactly as the neighbours will see them in the residual: at a CTA edge
       // the cluster tree's values, elsewhere the partition's own block form.
       const float xs = (p == 0 && rank > 0) ? xs_c : Sweep<M>::first(blk, u0, v0);
@@ -398,7 +406,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
         tree_norms_read<C>(gdx, gxm, norms + C * kTreeNormPitch, &xbar[3], xph3 & 1u, p, j, alive, A.st);
         ++xph3;
       }
-      bool line_done = tree_line_done(gdx, gxm, prev, active, A.tol, reporter, A.st);
+      bool line_done = tree_line_done(gdx, gxm, prev, active, A.tol, certified, reporter, A.st);
       bool all_done = __syncthreads_and(line_done) != 0;
 
       // ---------------- later corrections (rare): x re-read from global memory
@@ -464,7 +472,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
         tree_norms_push<C>(line_max(ndx), line_max(nxm), nb, &xbar[2 + q], rank, p, j);
         tree_norms_read<C>(gdx, gxm, nb, &xbar[2 + q], (q ? xph3 : xph2) & 1u, p, j, alive, A.st);
         if (q) ++xph3; else ++xph2;
-        line_done = tree_line_done(gdx, gxm, prev, active, A.tol, reporter, A.st);
+        line_done = tree_line_done(gdx, gxm, prev, active, A.tol, certified, reporter, A.st);
         all_done = __syncthreads_and(line_done) != 0;
       }
       if (reporter) {

@@ -64,7 +64,8 @@ def test_adi_512_cubed_sweeps_match_closed_form():
 def test_poisson_wavenumber_lines_1024_cubed(precision, tol):
     # Against the extended-precision oracle. Plain FP64 elimination is a few 1e-12 off on the
     # lowest modes (so is the FP64 CPU Thomas: 3e-12 on the pinned zero mode), hence its looser
-    # bound; one correction from an exact residual (solved in FP32) meets 1e-12.
+    # bound; f64r corrects the lines whose condition-number bound reaches 1e5 (the lowest modes,
+    # a few thousand of the 2^20) from an exact residual, solved in FP32, and meets 1e-12.
     n = 1024
     p = synth.poisson_lines(n, n, n, seed=2, device="cuda")
     d = p["d"]
@@ -77,6 +78,8 @@ def test_poisson_wavenumber_lines_1024_cubed(precision, tol):
     main.solve(p["a"], p["b0"], p["c"], d3[:, 1:, :], x3[:, 1:, :])
     zero.solve(p["pin_a"], p["pin_b"], p["pin_c"], d3[:, :1, :], x3[:, :1, :])
     assert main.last_error()[0] == 0 and zero.last_error()[0] == 0
+    if precision == "f64r":
+        assert 0 < main.corrected_lines() < (n * n) // 100 and zero.corrected_lines() == 1
     # sampled modes: the pinned zero mode, the lowest and highest wavenumbers, random ones
     rng = np.random.default_rng(2)
     modes = np.unique(np.concatenate([[0, 1, n, n + 1, n * n - 1, n * n // 2 + n // 2], rng.choice(n * n, 58, False)]))

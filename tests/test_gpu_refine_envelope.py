@@ -6,8 +6,9 @@ kappa * 2^-48 of |x|. Lines are FP32-representable (coefficients rounded to floa
 problem) with a diagonal-dominance margin eps that sets kappa from about 10^2 to 10^6. For every
 case the solve must either meet 1e-12 against the extended-precision oracle (per line and pooled)
 or report TDMA_ERR_NOT_CONVERGED: a status of 0 with a larger error is a silent failure and fails
-the test. Well-conditioned cases must converge. Covered for the kernel of strided lines (lines
-along the slowest axis) and for the chunk kernel (unit-stride lines)."""
+the test. Well-conditioned cases (their floor certified by the rows' diagonal dominance) must
+converge. Covered for the kernel of strided lines (lines along the slowest axis) and for the chunk
+kernel (unit-stride lines)."""
 import numpy as np
 import pytest
 import torch
@@ -64,5 +65,5 @@ def test_f32_refine_meets_1e12_or_reports_not_converged(layout, eps):
     assert st in (0, 7), info
     if st == 0:
         assert err <= 1e-12, "silent failure: " + info
-    if kappa < 2e3:
-        assert st == 0, info  # well-conditioned lines converge
+    if kappa < 300:
+        assert st == 0, info  # well-conditioned lines converge (their floor is certified)
