@@ -177,6 +177,10 @@ def source_sha(kernel: str) -> str:
     return h.hexdigest()[:16]
 
 
+def pipe_batches(tune) -> int:
+    return int(tune["choice"][0])
+
+
 def rank_rows(ny: int, rank: int, world: int, scaling: str):
     """(y0, y1, ny_global): the y-rows [y0, y1) of the global grid that ``rank`` solves.
 
@@ -626,6 +630,9 @@ def suite_ragged(stream, hbm_peak, n_lines=20000):
         a, b, c = (r[k] for k in keys)
         d = r["d"]
         x, plan = tdma.solve_ragged(a, b, c, d, r["offsets"], r["lengths"], precision=prec)
+        default_cfg = plan.config
+        ms_default = _timed(lambda: plan.solve(a, b, c, d, x), 10, 3, stream)
+        tuned_cfg = plan.autotune(a, b, c, d, x)  # rows per partition (and chunk vs group kernel), timed
         ms = _timed(lambda: plan.solve(a, b, c, d, x), 10, 3, stream)
         st, iters = plan.last_error()
         xs = x.cpu().numpy()
@@ -641,7 +648,9 @@ def suite_ragged(stream, hbm_peak, n_lines=20000):
                      "hbm_frac": fbytes * U / (ms * 1e-3) / 1e9 / hbm_peak, "rel_l2_error": oracle.rel_l2(got, want),
                      "status": st, "corrections_max": iters, "backward_ms": msb,
                      "backward_unknowns_per_s": U / (msb * 1e-3),
-                     "backward_lambda_rel_l2_error": lam_err, "plan": plan.config}
+                     "backward_lambda_rel_l2_error": lam_err, "plan": plan.config,
+                     "autotune": {"default_plan": default_cfg, "default_ms": ms_default, "tuned_plan": tuned_cfg,
+                                  "tuned_ms": ms}}
     return out
 
 
@@ -694,7 +703,8 @@ def main():
     ap.add_argument("--scaling", default="weak", choices=["weak", "strong"],
                     help="N > 1: weak = ny y-rows per rank of a taller grid; strong = the grid's y-rows split")
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--e2e-batches", type=int, default=8, help="slices of lines in the pipelined host solve")
+    ap.add_argument("--e2e-batches", type=int, default=0,
+                    help="slices of lines in the pipelined host solve (0: chosen by HostPipeline.tuned)")
     ap.add_argument("--cpu-lines", type=int, default=32768, help="lines in the CPU oracle sample")
     ap.add_argument("--ref-lines", type=int, default=32768, help="lines per reference-arm step")
     ap.add_argument("--no-e2e", action="store_true")
@@ -833,14 +843,19 @@ def main():
         shape = tuple(d.shape)
         a32 = b32 = c32 = d = x = None  # the pipeline stages slices in its own device buffers
         torch.cuda.empty_cache()
-        pipe = tdma.HostPipeline(shape, axis=0, precision="f32r", batches=args.e2e_batches, slots=2, device=dev)
+        if args.e2e_batches > 0:
+            pipe = tdma.HostPipeline(shape, axis=0, precision="f32r", batches=args.e2e_batches, slots=2, device=dev)
+            tune = {"choice": (args.e2e_batches, 2), "tuned": False}
+        else:  # slices and slots chosen on this data (timed candidates, the pipeline model beside them)
+            pipe, tune = tdma.HostPipeline.tuned(shape, 0, "f32r", h["a"], h["b"], h["c"], h["d"], hx, device=dev)
         barrier()
         tot, _ = time_steps(lambda: pipe.solve(h["a"], h["b"], h["c"], h["d"], hx), args.e2e_steps, 2, stream)
         barrier()
         ms_e = reduce_max(tot / args.e2e_steps, dev)
         e2e = {"value": U_all / (ms_e * 1e-3), "unit": UNIT, "h2d_bytes_per_step": bi * ws,
                "d2h_bytes_per_step": bo * ws, "steps": args.e2e_steps, "ms_per_step": ms_e,
-               "api": f"HostPipeline(batches={args.e2e_batches}, slots=2) -> tdma_solve_host"}
+               "api": f"HostPipeline(batches={pipe_batches(tune)}, slots={tune['choice'][1]}) -> tdma_solve_host",
+               "pipeline_tuning": tune}
         if rank == 0:
             e2e["rel_l2_error"] = synth_lines_check(hx, ys, ref.shape[0], ref)
         del pipe, h, hx

@@ -56,16 +56,37 @@ def max_threads() -> int:
     return int(_load().oracle_max_threads())
 
 
+# Arm CPU part numbers (MIDR part field) of the server cores this runs on
+_ARM_PARTS = {"0xd4f": "Arm Neoverse V2", "0xd40": "Arm Neoverse V1", "0xd0c": "Arm Neoverse N1",
+              "0xd49": "Arm Neoverse N2", "0xd84": "Arm Neoverse V3"}
+
+
 def cpu_model() -> str:
-    """The host CPU's model name (from /proc/cpuinfo where it has one)."""
+    """The host CPU's model name: /proc/cpuinfo's model name (x86), else lscpu's, else the Arm part
+    number, else the machine type."""
+    fields = {}
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
-                key = line.split(":")[0].strip().lower()
-                if key in ("model name", "cpu model", "hardware"):
-                    return line.split(":", 1)[1].strip()
+                if ":" in line:
+                    k, v = line.split(":", 1)
+                    fields.setdefault(k.strip().lower(), v.strip())
     except OSError:
         pass
+    if fields.get("model name"):
+        return fields["model name"]
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name:"):
+                name = line.split(":", 1)[1].strip()
+                if name and name != "-":
+                    return name
+    except (OSError, subprocess.SubprocessError):
+        pass
+    part = fields.get("cpu part", "").lower()
+    if part:
+        return _ARM_PARTS.get(part, f"Arm CPU part {part}")
     return platform.processor() or platform.machine()
 
 

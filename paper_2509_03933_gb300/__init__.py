@@ -250,10 +250,16 @@ class Plan:
 
     def autotune(self, a, b, c, d, x, workspace=None, stream=None):
         """Time the candidate configurations on these buffers and keep the fastest. Without an
-        explicit workspace, one large enough for every candidate (3 words per unknown) is offered."""
+        explicit workspace, one large enough for every candidate is offered (3 words per unknown;
+        ragged batches: 5 words per unknown plus padding for the shortest partitions)."""
         if workspace is None:
-            unknowns = self.desc.n * self.desc.n_lines * self.desc.nrhs
-            workspace = torch.empty(max(1, unknowns * 8 * 3), dtype=torch.uint8, device=d.device)
+            if self.desc.n == 0:
+                unknowns = self.desc.ragged_total + 256 * self.desc.n_lines
+                words = 5
+            else:
+                unknowns = self.desc.n * self.desc.n_lines * self.desc.nrhs
+                words = 3
+            workspace = torch.empty(max(1, unknowns * 8 * words), dtype=torch.uint8, device=d.device)
         ws = workspace
         st = self._lib.tdma_plan_autotune(self._h, _ptr(a), _ptr(b), _ptr(c), _ptr(d), _ptr(x), _ptr(ws),
                                           ctypes.c_size_t(ws.numel()), _stream(stream))
@@ -391,6 +397,83 @@ class HostPipeline:
     def synchronize(self):
         for s in self.streams:
             s.synchronize()
+
+    @staticmethod
+    def predict(h, s, o, batches, slots):
+        """Pipelined time of ``batches`` slices whose host-to-device copy, solve and device-to-host
+        copy take h, s and o each (the three stages of Section 4.2's pipeline; the copies in the two
+        directions run on separate copy engines): the first slice passes all three stages, then one
+        slice leaves every max(h, s, o), or every (h + s + o) / slots when the slots, each holding one
+        slice through its three stages, are the limit."""
+        return h + s + o + (batches - 1) * max(h, s, o, (h + s + o) / slots)
+
+    @classmethod
+    def tuned(cls, shape, axis, precision, a, b, c, d, x, device="cuda", batches=(4, 8, 16), slots=(2, 3),
+              reps=2):
+        """A pipeline with ``batches`` and ``slots`` chosen for this grid on the caller's host arrays
+        (overwriting x), cached per (shape, axis, precision) for the process. Like the batch-size
+        estimator of Section 4.2.3, the stages of one slice are timed once per slice count on one slot
+        (so nothing overlaps: the solve alone, and the copies as the rest of the serial time, split by
+        bytes in and out) and the pipelined time is predicted (``predict``); every candidate is then
+        also measured, and the fastest measured is kept. Returns (pipeline, report) with the choice and
+        the predicted and measured milliseconds of every candidate."""
+        key = (tuple(int(v) for v in shape), axis, precision)
+        dev = torch.device(device)
+        if key in _PIPE_CACHE:
+            k, sl = _PIPE_CACHE[key]["choice"]
+            return cls(shape, axis, precision, k, sl, device), _PIPE_CACHE[key]
+        lines = 1
+        for i, v in enumerate(shape):
+            if i != axis % len(shape):
+                lines *= int(v)
+        bin_ = sum(t.numel() * t.element_size() for t in (a, b, c, d))
+        bout = x.numel() * x.element_size()
+
+        def timed(fn):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            fn()
+            torch.cuda.synchronize(dev)
+            best = float("inf")
+            for _ in range(reps):
+                e0.record()
+                fn()
+                e1.record()
+                torch.cuda.synchronize(dev)
+                best = min(best, e0.elapsed_time(e1))
+            return best
+
+        rows = []
+        for k in batches:
+            if lines % k:
+                continue
+            one = cls(shape, axis, precision, k, 1, device)
+            serial = timed(lambda: one.solve(a, b, c, d, x))  # one slot: every stage in turn
+            bufs = one.buffers[0]
+            ws = one.workspaces[0] if one.workspaces else None
+            solve = timed(lambda: one.plan.solve(*bufs[:4], bufs[4], workspace=ws)) * k
+            copies = max(0.0, serial - solve)
+            h, o = copies * bin_ / (bin_ + bout) / k, copies * bout / (bin_ + bout) / k
+            del one, bufs, ws
+            for sl in slots:
+                pred = cls.predict(h, solve / k, o, k, sl)
+                pipe = cls(shape, axis, precision, k, sl, device)
+                meas = timed(lambda: pipe.solve(a, b, c, d, x))
+                rows.append({"batches": k, "slots": sl, "predicted_ms": pred, "measured_ms": meas,
+                             "stage_ms": [h, solve / k, o]})
+                del pipe
+                torch.cuda.empty_cache()
+        if not rows:
+            raise ValueError("no candidate slice count divides the number of lines")
+        best = min(rows, key=lambda r: r["measured_ms"])
+        est = min(rows, key=lambda r: r["predicted_ms"])
+        report = {"choice": (best["batches"], best["slots"]), "estimator_choice": (est["batches"], est["slots"]),
+                  "estimator_choice_measured_ms": est["measured_ms"], "best_measured_ms": best["measured_ms"],
+                  "candidates": rows}
+        _PIPE_CACHE[key] = report
+        return cls(shape, axis, precision, best["batches"], best["slots"], device), report
+
+
+_PIPE_CACHE = {}
 
 
 def _check_same_layout(ref, *ts):

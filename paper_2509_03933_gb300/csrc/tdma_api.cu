@@ -44,6 +44,8 @@ struct tdma_plan_s {
   RaggedTables rt{};       // ragged batches: sorted order, groups, scratch bases, work counter
   void* rt_mem = nullptr;  // one device allocation holding the tables
   tdma_config_t rcfg{};    // ragged batches: configuration of the group kernels (backward pass)
+  int ragged_rows = kRaggedRowsPerPart;  // ragged batches: rows per partition of the group kernels
+  tdma_config_t pkcfg{};   // configuration of the chunk kernel, when its tables were built
   PackedTables pk{};       // ragged F32 + refinement: chunks of packed lines, metadata, line norms
   void* pk_mem = nullptr;  // one device allocation holding them
 };
@@ -693,6 +695,11 @@ tdma_status_t build_ragged(tdma_plan_s* p) {
   const tdma_desc_t& d = p->desc;
   const int64_t L = d.n_lines;
   if (d.nrhs != 1) return TDMA_ERR_UNSUPPORTED;
+  if (p->rt_mem) {  // rebuilt (autotune): the previous tables go
+    if (cudaFree(p->rt_mem) != cudaSuccess) return TDMA_ERR_CUDA;
+    p->rt_mem = nullptr;
+  }
+  const int rows_per_part = std::max(2, p->ragged_rows);
   std::vector<int32_t> len((size_t)L);
   if (L > 0 && cudaMemcpy(len.data(), d.ragged_lengths, sizeof(int32_t) * L, cudaMemcpyDeviceToHost) != cudaSuccess)
     return TDMA_ERR_CUDA;
@@ -701,8 +708,8 @@ tdma_status_t build_ragged(tdma_plan_s* p) {
   std::vector<int32_t> order((size_t)L);
   for (int64_t i = 0; i < L; ++i) order[i] = (int32_t)i;
   std::stable_sort(order.begin(), order.end(), [&](int32_t x, int32_t y) { return len[x] > len[y]; });
-  auto parts_for = [](int64_t n) {
-    int64_t P = (n + kRaggedRowsPerPart - 1) / kRaggedRowsPerPart;
+  auto parts_for = [rows_per_part](int64_t n) {
+    int64_t P = (n + rows_per_part - 1) / rows_per_part;
     P = std::min<int64_t>(P, kRaggedThreads);
     P = std::min<int64_t>(P, n / 2);
     return (int)std::max<int64_t>(P, 1);
@@ -757,7 +764,7 @@ tdma_status_t build_ragged(tdma_plan_s* p) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ragged_refine_kernel<false>, kRaggedThreads, c.smem_bytes);
   c.blocks = (int32_t)std::max<int64_t>(1, std::min<int64_t>((int64_t)sms * std::max(occ, 1), (int64_t)groups.size()));
   c.partitions = groups.empty() ? 1 : groups.front().P;
-  c.rows_per_thread = kRaggedRowsPerPart;
+  c.rows_per_thread = rows_per_part;
   c.lines_per_block = groups.empty() ? 1 : groups.front().count;
   p->cfg = c;
   p->rcfg = c;
@@ -912,6 +919,7 @@ bool build_packed_tables(tdma_plan_s* p, const std::vector<int64_t>& off, const 
   const int64_t nc = (int64_t)chunks.size();
   c.blocks = (int32_t)(kPackC * (resident > 0 ? std::min<int64_t>(nc, resident) : nc));
   p->cfg = c;
+  p->pkcfg = c;
   return true;
 }
 
@@ -954,12 +962,21 @@ std::vector<tdma_config_t> tune_candidates(const tdma_desc_t& d, bool allow_tma)
   return out;
 }
 
-std::string tune_key(const tdma_desc_t& d) {
+int log2_bucket(int64_t v) {
   int lb = 0;
-  for (int64_t v = std::max<int64_t>(1, d.n_lines); v > 1; v >>= 1) ++lb;
+  for (v = std::max<int64_t>(1, v); v > 1; v >>= 1) ++lb;
+  return lb;
+}
+
+std::string tune_key(const tdma_desc_t& d) {
   char buf[160];
-  std::snprintf(buf, sizeof(buf), "p%d n%lld l%d u%d r%d b%d s%d", (int)d.precision, (long long)d.n, lb,
-                d.elem_stride == 1 ? 1 : 0, d.nrhs, d.coef_broadcast, d.diag_shift ? 1 : 0);
+  if (d.n == 0) {  // ragged: by line count, longest line and total unknowns (powers of two)
+    std::snprintf(buf, sizeof(buf), "ragged p%d l%d m%d t%d", (int)d.precision, log2_bucket(d.n_lines),
+                  log2_bucket(d.ragged_max_n), log2_bucket(d.ragged_total));
+    return buf;
+  }
+  std::snprintf(buf, sizeof(buf), "p%d n%lld l%d u%d r%d b%d s%d", (int)d.precision, (long long)d.n,
+                log2_bucket(d.n_lines), d.elem_stride == 1 ? 1 : 0, d.nrhs, d.coef_broadcast, d.diag_shift ? 1 : 0);
   return buf;
 }
 
@@ -989,6 +1006,17 @@ std::map<std::string, TuneChoice>& tune_table() {
   return g_tune;
 }
 
+// A cached ragged choice: (variant, rows per partition of the group kernels).
+bool cached_ragged(const tdma_desc_t& d, int& variant, int& rows) {
+  std::lock_guard<std::mutex> lock(g_tune_mu);
+  auto& tab = tune_table();
+  auto it = tab.find(tune_key(d));
+  if (it == tab.end()) return false;
+  variant = it->second.variant;
+  rows = it->second.partitions;
+  return true;
+}
+
 bool cached_config(const tdma_desc_t& d, bool allow_tma, tdma_config_t& c) {
   TuneChoice t{};
   {
@@ -1003,22 +1031,79 @@ bool cached_config(const tdma_desc_t& d, bool allow_tma, tdma_config_t& c) {
   return false;
 }
 
-void remember_config(const tdma_desc_t& d, const tdma_config_t& c) {
+// Ragged plans store (variant, rows per partition) in the (variant, P) slot of the table.
+void remember_choice(const tdma_desc_t& d, int variant, int second) {
   std::lock_guard<std::mutex> lock(g_tune_mu);
   auto& tab = tune_table();
   const std::string key = tune_key(d);
-  tab[key] = TuneChoice{c.variant, c.partitions};
+  tab[key] = TuneChoice{variant, second};
   if (const char* path = std::getenv("TDMA_AUTOTUNE_CACHE")) {
     if (FILE* f = std::fopen(path, "a")) {
-      std::fprintf(f, "%s|%d|%d\n", key.c_str(), c.variant, c.partitions);
+      std::fprintf(f, "%s|%d|%d\n", key.c_str(), variant, second);
       std::fclose(f);
     }
   }
 }
+void remember_config(const tdma_desc_t& d, const tdma_config_t& c) { remember_choice(d, c.variant, c.partitions); }
+
+// Time the forward solve of the plan's current configuration: one warm-up, then kReps launches
+// between two events on `s`. Returns a negative value when a launch fails.
+float time_forward(tdma_plan_s* p, const Args& A, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1) {
+  constexpr int kReps = 3;
+  if (launch_forward(p, A, s) != cudaSuccess) return -1.f;
+  cudaEventRecord(e0, s);
+  bool ok = true;
+  for (int r = 0; r < kReps && ok; ++r) ok = launch_forward(p, A, s) == cudaSuccess;
+  cudaEventRecord(e1, s);
+  float ms = 0.f;
+  if (cudaEventSynchronize(e1) != cudaSuccess || !ok || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) return -1.f;
+  return ms / kReps;
+}
+
+// Ragged batches: the group kernels with 8, 12, 16, 24 or 32 rows per partition (the batch's lines
+// cut into partitions of about that many rows; the partition count per line and the lines per
+// block follow), and for FP32 + refinement also the chunk kernel when its tables exist. Every
+// candidate runs on the caller's data; candidates whose workspace exceeds ws_bytes are skipped.
+// The group tables are rebuilt for each candidate and finally for the choice (the backward pass
+// uses them with either forward kernel).
+tdma_status_t autotune_ragged(tdma_plan_s* p, const void* a, const void* b, const void* c, const void* d, void* x,
+                              void* ws, size_t ws_bytes, cudaStream_t s) {
+  static const int kRows[] = {8, 12, 16, 24, 32};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return TDMA_ERR_CUDA;
+  const int keep_rows = p->ragged_rows;
+  const bool packed = p->pk_mem != nullptr && p->pkcfg.variant == TDMA_VARIANT_PACKED;
+  float best = 1e30f;
+  int best_variant = p->cfg.variant, best_rows = keep_rows;
+  if (packed) {
+    p->cfg = p->pkcfg;
+    const float ms = time_forward(p, make_args(p, a, b, c, d, x, ws), s, e0, e1);
+    if (ms >= 0.f && ms < best) { best = ms; best_variant = TDMA_VARIANT_PACKED; }
+  }
+  for (int rows : kRows) {
+    p->ragged_rows = rows;
+    if (build_ragged(p) != TDMA_OK) continue;
+    if (p->workspace > ws_bytes || (p->workspace > 0 && !ws)) continue;
+    if (prepare_kernel(p) != cudaSuccess) continue;
+    const float ms = time_forward(p, make_args(p, a, b, c, d, x, ws), s, e0, e1);
+    if (ms >= 0.f && ms < best) { best = ms; best_variant = TDMA_VARIANT_RAGGED; best_rows = rows; }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  p->ragged_rows = best_rows;
+  const tdma_status_t r = build_ragged(p);  // the chosen group tables (and the backward's)
+  if (r != TDMA_OK) return r;
+  if (best_variant == TDMA_VARIANT_PACKED) p->cfg = p->pkcfg;
+  if (prepare_kernel(p) != cudaSuccess) return TDMA_ERR_CUDA;
+  remember_choice(p->desc, best_variant, best_rows);
+  cudaMemsetAsync(p->status, 0, sizeof(DevStatus), s);
+  return cudaStreamSynchronize(s) == cudaSuccess ? TDMA_OK : TDMA_ERR_CUDA;
+}
 
 tdma_status_t autotune_impl(tdma_plan_s* p, const void* a, const void* b, const void* c, const void* d, void* x,
                             void* ws, size_t ws_bytes, cudaStream_t s) {
-  if (p->desc.n == 0 || p->desc.n_lines == 0 || p->desc.pdd) return TDMA_OK;
+  if (p->desc.n_lines == 0 || p->desc.pdd) return TDMA_OK;
+  if (p->desc.n == 0) return autotune_ragged(p, a, b, c, d, x, ws, ws_bytes, s);
   auto cands = tune_candidates(p->desc, p->allow_tma);
   if (p->cfg.variant == TDMA_VARIANT_PACKED) cands.insert(cands.begin(), p->cfg);  // the plan's own chunk tables
   cudaEvent_t e0, e1;
@@ -1171,13 +1256,18 @@ tdma_status_t tdma_plan_create(tdma_plan_t* plan, const tdma_desc_t* desc, size_
     p->cfg = c;
     p->workspace = workspace_for(*desc, c);
   } else {
+    int cv = 0, crows = 0;
+    const bool cached = cached_ragged(*desc, cv, crows) && crows >= 2;
+    if (cached) p->ragged_rows = crows;
     const tdma_status_t r = build_ragged(p);
     if (r != TDMA_OK) {
       if (p->rt_mem) cudaFree(p->rt_mem);
       delete p;
       return r;
     }
-    build_packed(p);  // the chunk kernel for the forward pass where it applies
+    const tdma_config_t group = p->cfg;
+    // the chunk kernel for the forward pass where it applies (unless a tuned choice says otherwise)
+    if (build_packed(p) && cached && cv == TDMA_VARIANT_RAGGED) p->cfg = group;
   }
   if (p->refine64) {  // residual / correction buffer after the solver's own workspace
     p->r_offset = (p->workspace + 255) / 256 * 256;
@@ -1302,7 +1392,8 @@ tdma_status_t tdma_last_device_error(tdma_plan_t p, void* stream, int32_t* info)
   if (cudaMemcpyAsync(&h, p->status, sizeof(DevStatus), cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess)
     return TDMA_ERR_CUDA;
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return TDMA_ERR_CUDA;
-  if (cudaMemsetAsync(p->status, 0, sizeof(DevStatus), (cudaStream_t)stream) != cudaSuccess) return TDMA_ERR_CUDA;
+  // clear the error and iteration words; word 2 (lines the last TDMA_F64_REFINE solve corrected) stays
+  if (cudaMemsetAsync(p->status, 0, 2 * sizeof(int32_t), (cudaStream_t)stream) != cudaSuccess) return TDMA_ERR_CUDA;
   if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return TDMA_ERR_CUDA;
   if (info) *info = h.iters;
   return (tdma_status_t)h.err;

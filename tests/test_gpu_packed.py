@@ -127,15 +127,16 @@ def test_packed_in_place_and_repeated_solves():
 
 
 def test_packed_second_correction_for_weakly_dominant_lines():
-    # tridiag(-1, 2.001, -1) has condition number about 4000: the float solve is good to about
-    # 2e-4, one correction leaves about 6e-8 and the stop rule asks for more (the rare path that
-    # reads x back); the reference is the extended-precision oracle
+    # tridiag(-1, 2.01, -1) has condition number about 400: the float solve is good to about 1e-5,
+    # one correction leaves about 1e-10 and the stop rule asks for more (the rare path that reads x
+    # back); the rows' dominance (1 - 2 / 2.01 = 5e-3) certifies the float-pair residual's floor
+    # below the tolerance, so the line converges; the reference is the extended-precision oracle
     lengths = np.array([3000, 50, 17000, 700], np.int32)
     a, b, c, d, offs, lens = _problem(lengths, 15)
     o, n = offs.cpu().numpy(), lens.cpu().numpy()
     a.fill_(-1.0)
     c.fill_(-1.0)
-    b.fill_(2.001)
+    b.fill_(2.01)
     A, B, C = a.double(), b.double(), c.double()
     xt = torch.sin(torch.arange(a.numel(), device="cuda", dtype=torch.float64) * 0.37)
     dn = B * xt
@@ -207,14 +208,14 @@ def test_packed_backward_matches_group_kernel_and_oracle():
 
 
 def test_packed_backward_second_correction():
-    # tridiag(-1, 2.001, -1) (condition number about 4000, its own transpose): the adjoint solve
-    # on the transposed rows needs more than one correction too; the nonsymmetric case is covered
+    # tridiag(-1, 2.01, -1) (condition number about 400, its own transpose): the adjoint solve on
+    # the transposed rows needs more than one correction too; the nonsymmetric case is covered
     # against the group kernel above
     lengths = np.array([4000, 9000, 31], np.int32)
     a, b, c, d, offs, lens = _problem(lengths, 19)
     a.fill_(-1.0)
     c.fill_(-1.0)
-    b.fill_(2.001)
+    b.fill_(2.01)
     x, plan = _solve(a, b, c, d, offs, lens)
     w = torch.cos(torch.arange(x.numel(), device="cuda", dtype=torch.float64) * 0.11)
     g = _grads(a, b, c, x, w, plan)

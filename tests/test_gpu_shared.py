@@ -42,9 +42,9 @@ def _lines(t, axis, nrhs):
     return np.stack([synth.line_view(t[..., r], axis).numpy() for r in range(nrhs)], axis=-1)
 
 
-def _plan(d, axis, precision, nrhs, partitions=1):
+def _plan(d, axis, precision, nrhs, partitions=1, refine_kappa=0.0):
     return tdma.Plan(*tdma.line_layout(d, axis, nrhs=nrhs), precision=precision, partitions=partitions, nrhs=nrhs,
-                     coef_broadcast=True)
+                     coef_broadcast=True, refine_kappa=refine_kappa)
 
 
 def _oracle(a, b, c, d, axis, nrhs, ext=False):
@@ -177,24 +177,33 @@ def test_shared_backward_sums_gradients_over_lines(precision, nrhs):
 def test_shared_with_exact_residual_correction():
     # tridiag(-1, 2.001, -1) shared by all lines (condition number about 4000): the FP64 solve
     # followed by the exact-residual correction (an FP32 solve, which gains a factor of about
-    # 4000 x 6e-8 per step) against the extended-precision oracle
+    # 4000 x 6e-8 per step) against the extended-precision oracle. Its condition-number bound
+    # (4001) is below the default selection threshold (1e5), so by default no line is corrected and
+    # the result is the plain FP64 solve bit for bit; refine_kappa < 0 corrects every line.
     n, L = 2048, 256
     a = torch.full((n,), -1.0, dtype=torch.float64, device="cuda")
     c = a.clone()
     b = torch.full((n,), 2.001, dtype=torch.float64, device="cuda")
     d = _rhs((n, L), 71, torch.float64, 1)
-    plan = _plan(d, 0, "f64r", 1)
-    assert plan.config["variant"] == SHARED
-    x = torch.empty_like(d)
-    plan.solve(a, b, c, d, x)
-    assert plan.last_error()[0] == 0
     ref = _oracle(a, b, c, d, 0, 1, ext=True)
     plain = _plan(d, 0, "f64", 1)
     x64 = torch.empty_like(d)
     plain.solve(a, b, c, d, x64)
-    e_corr = O.rel_l2(_lines(x, 0, 1), ref)
+    plan = _plan(d, 0, "f64r", 1, refine_kappa=-1.0)
+    assert plan.config["variant"] == SHARED
+    x = torch.empty_like(d)
+    plan.solve(a, b, c, d, x)
+    assert plan.last_error()[0] == 0
+    assert plan.corrected_lines() == L
+    e_corr = rel_err(_lines(x, 0, 1), ref)
     assert e_corr <= 1e-14
-    assert e_corr <= O.rel_l2(_lines(x64, 0, 1), ref)
+    assert e_corr <= rel_err(_lines(x64, 0, 1), ref)
+    default = _plan(d, 0, "f64r", 1)
+    xd = torch.empty_like(d)
+    default.solve(a, b, c, d, xd)
+    assert default.last_error()[0] == 0 and default.corrected_lines() == 0
+    assert torch.equal(xd, x64)
+    assert rel_err(_lines(xd, 0, 1), ref) <= 1e-12
 
 
 def test_shared_singular_pivot_sets_status():
