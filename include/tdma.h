@@ -362,6 +362,15 @@ tdma_status_t tdma_slab_finish(const tdma_slab_desc_t* desc, int64_t line0, int6
 tdma_status_t tdma_probe_fp64_fma(int32_t blocks, int32_t threads, int64_t iters, double* out, int64_t* fma_count,
                                   void* stream);
 
+/* Failure detection without a fault (the paper has no counterpart): every wait of the solver kernels
+ * on an mbarrier (TMA tile arrivals, cluster exchanges) polls a bounded number of times and then gives
+ * up with TDMA_ERR_TIMEOUT in the plan's status block instead of hanging. This launches one warp that
+ * runs that same bounded wait, `polls` polls (1 .. 2^20; about 64 ns each after the first 64), on an
+ * mbarrier nothing arrives on and nothing is in flight for, then writes TDMA_ERR_TIMEOUT into *status
+ * (a device int32 the caller zeroes first; written only if still 0). The GPU context stays usable.
+ * TDMA_ERR_INVALID_ARG for a NULL status or polls out of range. */
+tdma_status_t tdma_probe_bounded_wait(uint32_t polls, int32_t* status, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -109,6 +109,8 @@ def load_library(build: bool = True) -> ctypes.CDLL:
     lib.tdma_probe_fp64_fma.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int64, _VP,
                                         ctypes.POINTER(ctypes.c_int64), _VP]
     lib.tdma_probe_fp64_fma.restype = st
+    lib.tdma_probe_bounded_wait.argtypes = [ctypes.c_uint32, _VP, _VP]
+    lib.tdma_probe_bounded_wait.restype = st
     lib.tdma_plan_corrected_lines.argtypes = [_VP, _VP, ctypes.POINTER(ctypes.c_int64)]
     lib.tdma_plan_corrected_lines.restype = st
     _LIB = lib

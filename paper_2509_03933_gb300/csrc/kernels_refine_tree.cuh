@@ -220,8 +220,14 @@ TDMA_DEV bool tree_line_done(unsigned gdx, unsigned gxm, unsigned& prev, bool ac
 }
 
 // Persistent: the grid holds the clusters that fit on the GPU at once, and cluster k takes line
-// groups k, k + K, k + 2K, ... (K clusters). While it works on one group it prefetches the next
-// group's tile into L2, so the TMA load of the next tile finds its data there.
+// groups k, k + K, k + 2K, ... (K clusters). The next group's a, b and c tiles are loaded while the
+// current group is still in its second half (after the pass-1 exchange: Stage C, the x store, the
+// norm exchange and the verdict), so that only the d tile's load is waited for at the top of a
+// group: x leaves through the d tile, whose float pairs are dead once pass 1 has formed its
+// residual, and the rare later corrections read their operands from global memory. A solve in
+// place (x is d) cannot read d back from global memory after x went out, so it keeps the tiles for
+// the later corrections: x leaves through the a and b tiles, the next group's tiles all load at
+// its top, and a later correction reloads a and b and takes c and the d pairs from the tiles.
 template <int M, int C>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
     refine_tree_kernel(const Args A, const __grid_constant__ TmaMaps maps) {
@@ -257,10 +263,11 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
   const float* rc = tc + fo;
   double* rd = td + (w >> 2) * (M * 128) + p * 16 + ((((w & 3) * 2 + (jj >> 1)) ^ p) << 1) + (jj & 1);
   float2* rd2 = reinterpret_cast<float2*>(rd);  // d as a float pair, written in place by pass 0
-  // x leaves through the a and b tiles (32 KB, the layout of the d tile) by TMA store once pass 1
-  // no longer reads them
-  double* const tx = reinterpret_cast<double*>(ta);
-  double* rx = tx + (rd - td);
+  // x leaves by TMA store through the d tile (each thread writes x where it read its d), or in
+  // place through the a and b tiles (32 KB, the layout of the d tile)
+  const bool inplace = A.x == A.d;
+  double* const tx = inplace ? reinterpret_cast<double*>(ta) : td;
+  double* const rx = tx + (rd - td);
   const int64_t es = A.lay.es, ic = A.lay.ic;
   const float keep = certify_keep(A.tol);
 
@@ -282,30 +289,23 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
     const int64_t line0 = g * kTreeLines;
     const bool active = line0 + j < A.lay.n_lines;
     const bool reporter = rank == 0 && p == 0 && active;  // one thread per line reports
-    double* px = (double*)A.x + A.lay.off(active ? line0 + j : 0) + (int64_t)kg * M * es;
+    const int64_t eoff = A.lay.off(active ? line0 + j : 0) + (int64_t)kg * M * es;  // this partition's row 0
+    double* px = (double*)A.x + eoff;
     const int c_in = (int)(line0 % ic), c_out = (int)(line0 / ic), c_p = rank * kTreeParts;
     if (tid == 0) {
-      bulk_wait_read_all();  // the previous tile's x store has read the a and b tiles
+      bulk_wait_read_all();  // the previous tile's x store has read the d tile
+      // a, b and c of every group after the cluster's first came in during the previous group
+      const bool abc_early = !inplace && g > (int64_t)(blockIdx.x / C);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {  // row half h: rows [h H, (h + 1) H), 1 KB per row
-        mbar_arrive_expect_tx(&bar[h], 5u * H * 1024u);
-        tma_load_4d(ta + h * H * 256, &maps.a, &bar[h], c_in, c_out, c_p, h * H);
-        tma_load_4d(tb + h * H * 256, &maps.b, &bar[h], c_in, c_out, c_p, h * H);
-        tma_load_4d(tc + h * H * 256, &maps.c, &bar[h], c_in, c_out, c_p, h * H);
+        mbar_arrive_expect_tx(&bar[h], (abc_early ? 2u : 5u) * H * 1024u);
+        if (!abc_early) {
+          tma_load_4d(ta + h * H * 256, &maps.a, &bar[h], c_in, c_out, c_p, h * H);
+          tma_load_4d(tb + h * H * 256, &maps.b, &bar[h], c_in, c_out, c_p, h * H);
+          tma_load_4d(tc + h * H * 256, &maps.c, &bar[h], c_in, c_out, c_p, h * H);
+        }
         tma_load_4d(td + h * H * 128, &maps.d, &bar[h], c_in, c_out, c_p, h * H);
         tma_load_4d(td + M * 128 + h * H * 128, &maps.d, &bar[h], c_in + 16, c_out, c_p, h * H);
-      }
-      if (g + n_clusters < n_groups) {  // the next group of this cluster, into L2
-        const int64_t l1 = (g + n_clusters) * kTreeLines;
-        const int n_in = (int)(l1 % ic), n_out = (int)(l1 / ic);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          tma_prefetch_4d(&maps.a, n_in, n_out, c_p, h * H);
-          tma_prefetch_4d(&maps.b, n_in, n_out, c_p, h * H);
-          tma_prefetch_4d(&maps.c, n_in, n_out, c_p, h * H);
-          tma_prefetch_4d(&maps.d, n_in, n_out, c_p, h * H);
-          tma_prefetch_4d(&maps.d, n_in + 16, n_out, c_p, h * H);
-        }
       }
     }
     if (!mbar_wait_bounded(&bar[0], tph0, kTmaWaitPolls) && alive) {
@@ -386,14 +386,29 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
         tree_stage_b<C>(blk, nx, slots + C * kTreeSlotPitch, &xbar[1], xph1 & 1u, rank, p, jj, j, u, v, xs_c, xe_c,
                         prev, alive, A.st);  // prev: line max |x_0|
         ++xph1;
+        // Every thread has finished its pass-1 sweep, the last read of the a, b and c tiles: the
+        // next group's rows of a, b and c may come in (their phase's arrival follows at its top).
+        __syncthreads();
+        if (tid == 0 && !inplace && g + n_clusters < n_groups) {
+          const int64_t l1 = (g + n_clusters) * kTreeLines;
+          const int n_in = (int)(l1 % ic), n_out = (int)(l1 / ic);
+          fence_proxy_async_smem();
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            mbar_expect_tx(&bar[h], 3u * H * 1024u);
+            tma_load_4d(ta + h * H * 256, &maps.a, &bar[h], n_in, n_out, c_p, h * H);
+            tma_load_4d(tb + h * H * 256, &maps.b, &bar[h], n_in, n_out, c_p, h * H);
+            tma_load_4d(tc + h * H * 256, &maps.c, &bar[h], n_in, n_out, c_p, h * H);
+          }
+        }
         float dx[M];
         S.solve(Sweep<M>::first(blk, u, v), Sweep<M>::last(blk, u, v), dx);
         unsigned ndx = 0u;
 #pragma unroll
         for (int t = 0; t < M; ++t) ndx = max(ndx, abs_bits(dx[t]));
         tree_norms_push<C>(line_max(ndx), nx, norms + C * kTreeNormPitch, &xbar[3], rank, p, j);
-        // Every thread of the CTA has sent its block (the exchange wait above needed all of
-        // them), so all reads of the a and b tiles in this pass are done: x goes there.
+        // x over this thread's own d pairs (read by its pass-1 sweep, before the barrier above), or
+        // in place over the a and b tiles (every thread's pass-1 sweep is done: the barrier above)
 #pragma unroll
         for (int t = 0; t < M; ++t) rx[t * 128] = f2d_fast(x0[t]) + f2d_fast(dx[t]);  // exact widenings, one FP64 add
         fence_proxy_async_smem();
@@ -409,25 +424,35 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
       bool line_done = tree_line_done(gdx, gxm, prev, active, A.tol, certified, reporter, A.st);
       bool all_done = __syncthreads_and(line_done) != 0;
 
-      // ---------------- later corrections (rare): x re-read from global memory
+      // ---------------- later corrections (rare): operands from global memory (the tiles hold the
+      // next group's rows and this group's outgoing x); in place, a and b reloaded into their tiles
+      // and c and the d pairs from the tiles
       int it = 1;
+      const float* ga = (const float*)A.a + eoff;
+      const float* gb = (const float*)A.b + eoff;
+      const float* gc = (const float*)A.c + eoff;
+      const double* gd = (const double*)A.d + eoff;
       while (!all_done && it < A.max_iters) {
         ++it;
         if (tid == 0) {
           bulk_wait_all();  // x of pass 1 is in global memory
           fence_proxy_async_global();
-          mbar_arrive_expect_tx(&bar[0], 2u * M * 1024u);  // a and b again (x went through their tiles)
+          if (inplace) {
+            mbar_arrive_expect_tx(&bar[0], 2u * M * 1024u);  // a and b again (x went through their tiles)
 #pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            tma_load_4d(ta + h * H * 256, &maps.a, &bar[0], c_in, c_out, c_p, h * H);
-            tma_load_4d(tb + h * H * 256, &maps.b, &bar[0], c_in, c_out, c_p, h * H);
+            for (int h = 0; h < 2; ++h) {
+              tma_load_4d(ta + h * H * 256, &maps.a, &bar[0], c_in, c_out, c_p, h * H);
+              tma_load_4d(tb + h * H * 256, &maps.b, &bar[0], c_in, c_out, c_p, h * H);
+            }
           }
         }
-        if (!mbar_wait_bounded(&bar[0], tph0, kTmaWaitPolls) && alive) {
-          alive = false;
-          report_error(A.st, 6);
+        if (inplace) {
+          if (!mbar_wait_bounded(&bar[0], tph0, kTmaWaitPolls) && alive) {
+            alive = false;
+            report_error(A.st, 6);
+          }
+          tph0 ^= 1u;
         }
-        tph0 ^= 1u;
         cluster_arrive();  // x of the previous pass, written by every CTA, visible to all
         cluster_wait();
         Sweep<M> S;  // a fresh solve (the first pass's factors are not kept past pass 1)
@@ -439,12 +464,24 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
         }
 #pragma unroll
         for (int t = 0; t < M; ++t) {
-          float a = ra[t * 256], b = rb[t * 256], c = rc[t * 256];
+          float a = 0.f, b = 1.f, c = 0.f;
+          ff dd{0.f, 0.f};
+          if (inplace) {
+            a = ra[t * 256];
+            b = rb[t * 256];
+            c = rc[t * 256];
+            const float2 dp = rd2[t * 128];
+            dd = ff{dp.x, dp.y};
+          } else if (active) {
+            a = ga[t * es];
+            b = gb[t * es];
+            c = gc[t * es];
+            dd = split_f64(gd[t * es]);
+          }
           if (t == 0 && first_part) a = 0.f;
           if (t == M - 1 && last_part) c = 0.f;
-          const float2 dd = rd2[t * 128];
           const ff xn = t == M - 1 ? xe : (active ? split_f64(px[(t + 1) * es]) : ff{0.f, 0.f});
-          S.row(t, a, b, c, residual_ff(a, b, c, ff{dd.x, dd.y}, xm, xc, xn));
+          S.row(t, a, b, c, residual_ff(a, b, c, dd, xm, xc, xn));
           xm = xc;
           xc = xn;
         }

@@ -1,9 +1,11 @@
-// Measurement probe: FP64 fused multiply-add throughput of the current GPU, the second roofline
-// of the FP64 solve paths (their sweeps are chains of FP64 fused multiply-adds, multiplies and
-// reciprocal refinements, all on the FP64 pipe).
+// Measurement and diagnostic probes: FP64 fused multiply-add throughput of the current GPU (the
+// second roofline of the FP64 solve paths, whose sweeps are chains of FP64 fused multiply-adds,
+// multiplies and reciprocal refinements, all on the FP64 pipe), and the bounded wait of the solver
+// kernels made to run out.
 #include <cuda_runtime.h>
 #include <cstdint>
 #include "tdma.h"
+#include "tma.cuh"
 
 namespace {
 
@@ -26,7 +28,27 @@ __global__ void fp64_fma_kernel(double* out, int64_t iters, double y, double z, 
   if (s == sentinel) out[blockIdx.x] = s;
 }
 
+// The bounded mbarrier wait every TMA and cluster exchange of the solver kernels uses
+// (mbar_wait_bounded), on a barrier that expects one arrival which never comes: no copy and no peer
+// store is pending on it, so giving up leaves nothing in flight. Each thread polls `polls` times,
+// gives up, and records TDMA_ERR_TIMEOUT in *status as the solver kernels do.
+__global__ void bounded_wait_kernel(uint32_t polls, int32_t* status) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    tdma::mbar_init(&bar, 1);
+    tdma::mbar_fence_init();
+  }
+  __syncthreads();
+  if (!tdma::mbar_wait_bounded(&bar, 0, polls)) atomicCAS(status, 0, (int32_t)TDMA_ERR_TIMEOUT);
+}
+
 }  // namespace
+
+extern "C" tdma_status_t tdma_probe_bounded_wait(uint32_t polls, int32_t* status, void* stream) {
+  if (status == nullptr || polls < 1 || polls > (1u << 20)) return TDMA_ERR_INVALID_ARG;
+  bounded_wait_kernel<<<1, 32, 0, static_cast<cudaStream_t>(stream)>>>(polls, status);
+  return cudaGetLastError() == cudaSuccess ? TDMA_OK : TDMA_ERR_CUDA;
+}
 
 extern "C" tdma_status_t tdma_probe_fp64_fma(int32_t blocks, int32_t threads, int64_t iters, double* out,
                                              int64_t* fma_count, void* stream) {

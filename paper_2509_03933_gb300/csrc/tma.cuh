@@ -16,6 +16,11 @@ TDMA_DEV void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.clus
 TDMA_DEV void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
+// Raise the transaction count of the barrier's current phase by `bytes` without arriving: copies
+// issued now complete on a phase whose arrival comes later (mbar_arrive_expect_tx).
+TDMA_DEV void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.expect_tx.relaxed.cta.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
 TDMA_DEV bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t done;
   asm volatile(
