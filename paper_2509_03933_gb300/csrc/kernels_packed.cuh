@@ -503,7 +503,7 @@ TDMA_DEV void load_ac(float* sa, float* sc, const float* fa, const float* fc, in
 }
 
 // Copies of chunk g's segment for this CTA into shared memory, transposed; rows past the chunk's
-// end become identity rows. Compute threads only.
+// end become identity rows. Every thread of the CTA (the coordinator warp too).
 template <int C, bool TR>
 TDMA_DEV void packed_issue_loads(const PackedTables& PT, const Args& A, int g, int rank, int tid, float* ta, float* tb,
                                  float* tc, double* td) {
@@ -517,11 +517,11 @@ TDMA_DEV void packed_issue_loads(const PackedTables& PT, const Args& A, int g, i
   const float* fb = (const float*)A.b;
   const float* fc = (const float*)A.c;
   const double* gd = (const double*)A.d;
-  // row i = tid + kPackT j of the segment is row t of partition k; both advance by fixed steps
+  // row i = tid + kPackThreads j of the segment is row t of partition k; both advance by fixed steps
   int k, t;
   seg_row(tid, M, inv, k, t);
-  const int dk = kPackT / M, dt = kPackT - dk * M;
-  for (int i = tid; i < kPackT * M; i += kPackT) {
+  const int dk = kPackThreads / M, dt = kPackThreads - dk * M;
+  for (int i = tid; i < kPackT * M; i += kPackThreads) {
     const int pos = t * kPackPitch + k;
     if (i < segn) {
       load_ac<TR>(ta + pos, tc + pos, fa, fc, gbase + i, seg0 + i, ch.rows);
@@ -602,8 +602,8 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
   const int n_clusters = (int)(gridDim.x / C);
   const int g0 = (int)(blockIdx.x / C);
   if (g0 < PT.n_chunks) {
-    if (!coord) packed_issue_loads<C, TR>(PT, A, g0, rank, tid, ta, tb, tc, td);
-    else if (lane == 0 && g0 + n_clusters < PT.n_chunks) packed_prefetch(PT, A, g0 + n_clusters, rank);
+    packed_issue_loads<C, TR>(PT, A, g0, rank, tid, ta, tb, tc, td);
+    if (coord && lane == 0 && g0 + n_clusters < PT.n_chunks) packed_prefetch(PT, A, g0 + n_clusters, rank);
   }
 
   for (int g = g0; g < PT.n_chunks; g += n_clusters) {
@@ -665,20 +665,19 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
     // x has gone out and the next chunk's copies are on their way.
     ++epoch;
     cluster_arrive();
-    // x = x_0 + dx in FP64 (exact widenings, one FP64 add), coalesced out of shared memory
-    if (!coord) {
-      for (int i = tid; i < segn; i += kPackT) {
-        int k, t;
-        seg_row(i, M, inv, k, t);
-        const float2 v = tx[t * kPackPitch + k];
-        gx[gbase + i] = f2d_fast(v.x) + f2d_fast(v.y);
-      }
+    // x = x_0 + dx in FP64 (exact widenings, one FP64 add), coalesced out of shared memory, by
+    // every warp of the CTA
+    for (int i = tid; i < segn; i += kPackThreads) {
+      int k, t;
+      seg_row(i, M, inv, k, t);
+      const float2 v = tx[t * kPackPitch + k];
+      gx[gbase + i] = f2d_fast(v.x) + f2d_fast(v.y);
     }
     if (overlap) {
       __syncthreads();  // the pairs have left shared memory: the next chunk may come in
       if (has_next) {
-        if (!coord) packed_issue_loads<C, TR>(PT, A, g + n_clusters, rank, tid, ta, tb, tc, td);
-        else if (lane == 0 && g + 2 * n_clusters < PT.n_chunks) packed_prefetch(PT, A, g + 2 * n_clusters, rank);
+        packed_issue_loads<C, TR>(PT, A, g + n_clusters, rank, tid, ta, tb, tc, td);
+        if (coord && lane == 0 && g + 2 * n_clusters < PT.n_chunks) packed_prefetch(PT, A, g + 2 * n_clusters, rank);
       }
     }
     cluster_wait();  // the atomics of every CTA are complete and visible
@@ -716,8 +715,8 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
     }
     if (rank == 0 && tid == 0) report_iters(A.st, it);
     if (!overlap && has_next) {  // every use of this chunk's shared memory is over (cluster barriers)
-      if (!coord) packed_issue_loads<C, TR>(PT, A, g + n_clusters, rank, tid, ta, tb, tc, td);
-      else if (lane == 0 && g + 2 * n_clusters < PT.n_chunks) packed_prefetch(PT, A, g + 2 * n_clusters, rank);
+      packed_issue_loads<C, TR>(PT, A, g + n_clusters, rank, tid, ta, tb, tc, td);
+      if (coord && lane == 0 && g + 2 * n_clusters < PT.n_chunks) packed_prefetch(PT, A, g + 2 * n_clusters, rank);
     }
   }
   if (!started) cluster_wait();  // a cluster without a chunk still completes the start-up barrier
