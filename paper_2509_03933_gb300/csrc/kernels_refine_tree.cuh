@@ -219,15 +219,32 @@ TDMA_DEV bool tree_line_done(unsigned gdx, unsigned gxm, unsigned& prev, bool ac
   return refine_done(__uint_as_float(gdx), __uint_as_float(gxm), pv, tol, certified);
 }
 
+// One thread loads a group's tile: rows [h M/2, (h + 1) M/2) of a, b, c (float) and d (double,
+// two boxes of 16 lines) arrive on bar[h], 5 KB per row.
+template <int M>
+TDMA_DEV void tree_load_tiles(const TmaMaps& maps, float* ta, float* tb, float* tc, double* td, uint64_t* bar, int c_in,
+                              int c_out, int c_p) {
+  constexpr int H = M / 2;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    mbar_arrive_expect_tx(&bar[h], 5u * H * 1024u);
+    tma_load_4d(ta + h * H * 256, &maps.a, &bar[h], c_in, c_out, c_p, h * H);
+    tma_load_4d(tb + h * H * 256, &maps.b, &bar[h], c_in, c_out, c_p, h * H);
+    tma_load_4d(tc + h * H * 256, &maps.c, &bar[h], c_in, c_out, c_p, h * H);
+    tma_load_4d(td + h * H * 128, &maps.d, &bar[h], c_in, c_out, c_p, h * H);
+    tma_load_4d(td + M * 128 + h * H * 128, &maps.d, &bar[h], c_in + 16, c_out, c_p, h * H);
+  }
+}
+
 // Persistent: the grid holds the clusters that fit on the GPU at once, and cluster k takes line
-// groups k, k + K, k + 2K, ... (K clusters). The next group's a, b and c tiles are loaded while the
-// current group is still in its second half (after the pass-1 exchange: Stage C, the x store, the
-// norm exchange and the verdict), so that only the d tile's load is waited for at the top of a
-// group: x leaves through the d tile, whose float pairs are dead once pass 1 has formed its
-// residual, and the rare later corrections read their operands from global memory. A solve in
-// place (x is d) cannot read d back from global memory after x went out, so it keeps the tiles for
-// the later corrections: x leaves through the a and b tiles, the next group's tiles all load at
-// its top, and a later correction reloads a and b and takes c and the d pairs from the tiles.
+// groups k, k + K, k + 2K, ... (K clusters). The next group's tiles are loaded while the current
+// group is still in its second half (after the pass-1 exchange: Stage C, the x store, the norm
+// exchange and the verdict): x goes from registers to global memory, so the tiles are dead once
+// pass 1 has formed its residual, and the rare later corrections read their operands from global
+// memory. A solve in place (x is d) cannot read d back from global memory after x went out, so it
+// keeps the tiles for the later corrections: x leaves through the a and b tiles by TMA store, the
+// next group's tiles load at its top, and a later correction reloads a and b and takes c and the
+// d pairs from the tiles.
 template <int M, int C>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
     refine_tree_kernel(const Args A, const __grid_constant__ TmaMaps maps) {
@@ -263,10 +280,10 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
   const float* rc = tc + fo;
   double* rd = td + (w >> 2) * (M * 128) + p * 16 + ((((w & 3) * 2 + (jj >> 1)) ^ p) << 1) + (jj & 1);
   float2* rd2 = reinterpret_cast<float2*>(rd);  // d as a float pair, written in place by pass 0
-  // x leaves by TMA store through the d tile (each thread writes x where it read its d), or in
-  // place through the a and b tiles (32 KB, the layout of the d tile)
+  // x leaves from registers to global memory, or, in place, by TMA store through the a and b
+  // tiles (32 KB, the layout of the d tile)
   const bool inplace = A.x == A.d;
-  double* const tx = inplace ? reinterpret_cast<double*>(ta) : td;
+  double* const tx = reinterpret_cast<double*>(ta);
   double* const rx = tx + (rd - td);
   const int64_t es = A.lay.es, ic = A.lay.ic;
   const float keep = certify_keep(A.tol);
@@ -292,21 +309,10 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
     const int64_t eoff = A.lay.off(active ? line0 + j : 0) + (int64_t)kg * M * es;  // this partition's row 0
     double* px = (double*)A.x + eoff;
     const int c_in = (int)(line0 % ic), c_out = (int)(line0 / ic), c_p = rank * kTreeParts;
-    if (tid == 0) {
-      bulk_wait_read_all();  // the previous tile's x store has read the d tile
-      // a, b and c of every group after the cluster's first came in during the previous group
-      const bool abc_early = !inplace && g > (int64_t)(blockIdx.x / C);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {  // row half h: rows [h H, (h + 1) H), 1 KB per row
-        mbar_arrive_expect_tx(&bar[h], (abc_early ? 2u : 5u) * H * 1024u);
-        if (!abc_early) {
-          tma_load_4d(ta + h * H * 256, &maps.a, &bar[h], c_in, c_out, c_p, h * H);
-          tma_load_4d(tb + h * H * 256, &maps.b, &bar[h], c_in, c_out, c_p, h * H);
-          tma_load_4d(tc + h * H * 256, &maps.c, &bar[h], c_in, c_out, c_p, h * H);
-        }
-        tma_load_4d(td + h * H * 128, &maps.d, &bar[h], c_in, c_out, c_p, h * H);
-        tma_load_4d(td + M * 128 + h * H * 128, &maps.d, &bar[h], c_in + 16, c_out, c_p, h * H);
-      }
+    // every group after the cluster's first came in during the previous group, unless in place
+    if (tid == 0 && (inplace || g == (int64_t)(blockIdx.x / C))) {
+      bulk_wait_read_all();  // in place: the previous tile's x store has read the a and b tiles
+      tree_load_tiles<M>(maps, ta, tb, tc, td, bar, c_in, c_out, c_p);
     }
     if (!mbar_wait_bounded(&bar[0], tph0, kTmaWaitPolls) && alive) {
       alive = false;
@@ -386,19 +392,15 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
         tree_stage_b<C>(blk, nx, slots + C * kTreeSlotPitch, &xbar[1], xph1 & 1u, rank, p, jj, j, u, v, xs_c, xe_c,
                         prev, alive, A.st);  // prev: line max |x_0|
         ++xph1;
-        // Every thread has finished its pass-1 sweep, the last read of the a, b and c tiles: the
-        // next group's rows of a, b and c may come in (their phase's arrival follows at its top).
-        __syncthreads();
-        if (tid == 0 && !inplace && g + n_clusters < n_groups) {
-          const int64_t l1 = (g + n_clusters) * kTreeLines;
-          const int n_in = (int)(l1 % ic), n_out = (int)(l1 / ic);
+        // Every thread has finished its pass-1 sweep, the last read of the tiles (x does not pass
+        // through them unless in place): the next group's rows may come in. The d pairs written
+        // in place by pass 0 are ordered before the copies' writes by each writer's proxy fence.
+        if (!inplace) {
           fence_proxy_async_smem();
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            mbar_expect_tx(&bar[h], 3u * H * 1024u);
-            tma_load_4d(ta + h * H * 256, &maps.a, &bar[h], n_in, n_out, c_p, h * H);
-            tma_load_4d(tb + h * H * 256, &maps.b, &bar[h], n_in, n_out, c_p, h * H);
-            tma_load_4d(tc + h * H * 256, &maps.c, &bar[h], n_in, n_out, c_p, h * H);
+          __syncthreads();
+          if (tid == 0 && g + n_clusters < n_groups) {
+            const int64_t l1 = (g + n_clusters) * kTreeLines;
+            tree_load_tiles<M>(maps, ta, tb, tc, td, bar, (int)(l1 % ic), (int)(l1 / ic), c_p);
           }
         }
         float dx[M];
@@ -407,16 +409,25 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
 #pragma unroll
         for (int t = 0; t < M; ++t) ndx = max(ndx, abs_bits(dx[t]));
         tree_norms_push<C>(line_max(ndx), nx, norms + C * kTreeNormPitch, &xbar[3], rank, p, j);
-        // x over this thread's own d pairs (read by its pass-1 sweep, before the barrier above), or
-        // in place over the a and b tiles (every thread's pass-1 sweep is done: the barrier above)
+        // x = x_0 + dx (exact widenings, one FP64 add): straight to global memory (for a fixed
+        // row the four lines of a lane quad are 32 contiguous bytes), or in place through the a
+        // and b tiles by TMA store (every thread's pass-1 sweep is done: the barrier below)
+        if (!inplace) {
+          if (active) {
 #pragma unroll
-        for (int t = 0; t < M; ++t) rx[t * 128] = f2d_fast(x0[t]) + f2d_fast(dx[t]);  // exact widenings, one FP64 add
-        fence_proxy_async_smem();
-        __syncthreads();
-        if (tid == 0) {  // out-of-range lines of a partial group are not written
-          tma_store_4d(&maps.x, tx, c_in, c_out, c_p, 0);
-          tma_store_4d(&maps.x, tx + M * 128, c_in + 16, c_out, c_p, 0);
-          bulk_commit();
+            for (int t = 0; t < M; ++t) px[t * es] = f2d_fast(x0[t]) + f2d_fast(dx[t]);
+          }
+        } else {
+          __syncthreads();
+#pragma unroll
+          for (int t = 0; t < M; ++t) rx[t * 128] = f2d_fast(x0[t]) + f2d_fast(dx[t]);
+          fence_proxy_async_smem();
+          __syncthreads();
+          if (tid == 0) {  // out-of-range lines of a partial group are not written
+            tma_store_4d(&maps.x, tx, c_in, c_out, c_p, 0);
+            tma_store_4d(&maps.x, tx + M * 128, c_in + 16, c_out, c_p, 0);
+            bulk_commit();
+          }
         }
         tree_norms_read<C>(gdx, gxm, norms + C * kTreeNormPitch, &xbar[3], xph3 & 1u, p, j, alive, A.st);
         ++xph3;
@@ -425,7 +436,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
       bool all_done = __syncthreads_and(line_done) != 0;
 
       // ---------------- later corrections (rare): operands from global memory (the tiles hold the
-      // next group's rows and this group's outgoing x); in place, a and b reloaded into their tiles
+      // next group's rows); in place, a and b reloaded into their tiles (which held the outgoing x)
       // and c and the d pairs from the tiles
       int it = 1;
       const float* ga = (const float*)A.a + eoff;
@@ -434,10 +445,10 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
       const double* gd = (const double*)A.d + eoff;
       while (!all_done && it < A.max_iters) {
         ++it;
-        if (tid == 0) {
-          bulk_wait_all();  // x of pass 1 is in global memory
-          fence_proxy_async_global();
-          if (inplace) {
+        if (inplace) {
+          if (tid == 0) {
+            bulk_wait_all();  // x of pass 1 is in global memory
+            fence_proxy_async_global();
             mbar_arrive_expect_tx(&bar[0], 2u * M * 1024u);  // a and b again (x went through their tiles)
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
@@ -445,8 +456,6 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
               tma_load_4d(tb + h * H * 256, &maps.b, &bar[0], c_in, c_out, c_p, h * H);
             }
           }
-        }
-        if (inplace) {
           if (!mbar_wait_bounded(&bar[0], tph0, kTmaWaitPolls) && alive) {
             alive = false;
             report_error(A.st, 6);
@@ -517,8 +526,9 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
         if (!line_done) report_error(A.st, 7);
       }
     }
-    // The next TMA load rewrites the tile. The generic-proxy writes to it (d split in place, x)
-    // were fenced before the x store; the last __syncthreads_and above ordered every read.
+    // In place, the next TMA load (at the top) rewrites the tiles: the generic-proxy writes to them
+    // (d split in place, x) were fenced before the x store, and the last __syncthreads_and above
+    // ordered every read.
   }
   if (!started) cluster_wait();  // a CTA without a group still completes the start-up barrier
   if (tid == 0) bulk_wait_all();  // the last x store has been written
