@@ -45,7 +45,7 @@ FP64_OPS_NOMINAL = 152 * 2 * 2.07e9  # FP64 pipe, nominal: 152 SMs x 2 ops/clk x
 KERNEL_OF_VARIANT = {0: "dc_kernel", 1: "thomas_kernel", 2: "refine_kernel", 3: "ragged_refine_kernel",
                      4: "refine_reg_kernel", 5: "refine_tma_fixed_kernel", 6: "refine_cluster_kernel",
                      7: "dc_kernel", 8: "refine_tree_kernel", 9: "packed_refine_kernel",
-                     10: "shared_stream_kernel"}
+                     10: "shared_stream_kernel", 11: "refine_tree_kernel"}
 
 
 def dist_env():

@@ -146,7 +146,8 @@ enum {
   TDMA_VARIANT_DC_GLOBAL = 7, /* fused Stage A/B/C, Stage A scratch in the workspace        */
   TDMA_VARIANT_REFINE_TREE = 8, /* refinement over a CTA cluster, Stage B as a merge tree    */
   TDMA_VARIANT_PACKED = 9,    /* ragged refinement: chunks of packed lines per CTA cluster */
-  TDMA_VARIANT_SHARED = 10    /* shared coefficients (broadcast, no shift): factorised once  */
+  TDMA_VARIANT_SHARED = 10,   /* shared coefficients (broadcast, no shift): factorised once  */
+  TDMA_VARIANT_REFINE_TREE_X = 11 /* the merge-tree cluster refinement on unit-stride lines  */
 };
 
 /* Validate `desc`, choose a launch configuration and report the workspace it needs.

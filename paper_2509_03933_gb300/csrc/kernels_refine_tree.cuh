@@ -219,20 +219,43 @@ TDMA_DEV bool tree_line_done(unsigned gdx, unsigned gxm, unsigned& prev, bool ac
   return refine_done(__uint_as_float(gdx), __uint_as_float(gxm), pv, tol, certified);
 }
 
-// One thread loads a group's tile: rows [h M/2, (h + 1) M/2) of a, b, c (float) and d (double,
-// two boxes of 16 lines) arrive on bar[h], 5 KB per row.
-template <int M>
+// One thread loads a group's tile. Lines along a strided axis: rows [h M/2, (h + 1) M/2) of a, b,
+// c (float) and d (double, two boxes of 16 lines) arrive on bar[h], 5 KB per row. Unit-stride
+// lines (XL): the CTA's 8 M rows of the 32 lines, a, b and c in boxes of 32 rows and d in boxes of
+// 16 rows (each box 128 bytes of every line, 4 KB), all on bar[0]; `parts` selects a, b and c (1),
+// d (2) or both (3), and `arrive` whether this call also arrives on bar[0] (without it, the copies
+// count towards a phase whose arrival comes later).
+template <int M, bool XL>
 TDMA_DEV void tree_load_tiles(const TmaMaps& maps, float* ta, float* tb, float* tc, double* td, uint64_t* bar, int c_in,
-                              int c_out, int c_p) {
-  constexpr int H = M / 2;
+                              int c_out, int c_p, int parts = 3, bool arrive = true) {
+  if constexpr (!XL) {
+    constexpr int H = M / 2;
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {
-    mbar_arrive_expect_tx(&bar[h], 5u * H * 1024u);
-    tma_load_4d(ta + h * H * 256, &maps.a, &bar[h], c_in, c_out, c_p, h * H);
-    tma_load_4d(tb + h * H * 256, &maps.b, &bar[h], c_in, c_out, c_p, h * H);
-    tma_load_4d(tc + h * H * 256, &maps.c, &bar[h], c_in, c_out, c_p, h * H);
-    tma_load_4d(td + h * H * 128, &maps.d, &bar[h], c_in, c_out, c_p, h * H);
-    tma_load_4d(td + M * 128 + h * H * 128, &maps.d, &bar[h], c_in + 16, c_out, c_p, h * H);
+    for (int h = 0; h < 2; ++h) {
+      mbar_arrive_expect_tx(&bar[h], 5u * H * 1024u);
+      tma_load_4d(ta + h * H * 256, &maps.a, &bar[h], c_in, c_out, c_p, h * H);
+      tma_load_4d(tb + h * H * 256, &maps.b, &bar[h], c_in, c_out, c_p, h * H);
+      tma_load_4d(tc + h * H * 256, &maps.c, &bar[h], c_in, c_out, c_p, h * H);
+      tma_load_4d(td + h * H * 128, &maps.d, &bar[h], c_in, c_out, c_p, h * H);
+      tma_load_4d(td + M * 128 + h * H * 128, &maps.d, &bar[h], c_in + 16, c_out, c_p, h * H);
+    }
+  } else {
+    const int r0 = c_p * M;  // the CTA's first row (c_p = rank x 8 partitions)
+    const uint32_t bytes = ((parts & 1) ? 3u * M * 1024u : 0u) + ((parts & 2) ? 2u * M * 1024u : 0u);
+    if (arrive) mbar_arrive_expect_tx(&bar[0], bytes);
+    else mbar_expect_tx(&bar[0], bytes);
+    if (parts & 1) {
+#pragma unroll
+      for (int i = 0; i < M / 4; ++i) {
+        tma_load_3d(ta + i * 1024, &maps.a, &bar[0], r0 + 32 * i, c_in, c_out);
+        tma_load_3d(tb + i * 1024, &maps.b, &bar[0], r0 + 32 * i, c_in, c_out);
+        tma_load_3d(tc + i * 1024, &maps.c, &bar[0], r0 + 32 * i, c_in, c_out);
+      }
+    }
+    if (parts & 2) {
+#pragma unroll
+      for (int i = 0; i < M / 2; ++i) tma_load_3d(td + i * 512, &maps.d, &bar[0], r0 + 16 * i, c_in, c_out);
+    }
   }
 }
 
@@ -245,14 +268,25 @@ TDMA_DEV void tree_load_tiles(const TmaMaps& maps, float* ta, float* tb, float* 
 // keeps the tiles for the later corrections: x leaves through the a and b tiles by TMA store, the
 // next group's tiles load at its top, and a later correction reloads a and b and takes c and the
 // d pairs from the tiles.
-template <int M, int C>
+//
+// XL: lines with unit element stride (rows contiguous in memory). The CTA's rows of the 32 lines
+// arrive as boxes of 128 bytes per line with the 128-byte swizzle (a, b, c: 32 rows; d: 16 rows),
+// so that partition p of line j reads rows 4q..4q+3 of a, b and c as one 16-byte word at chunk
+// (4 (p mod 2) + q) XOR (j mod 8) of box p / 2, and rows 2q, 2q + 1 of d at chunk q XOR (j mod 8)
+// of box p: the 8 lanes of each quarter-warp access of a, b and c then cover the 32 banks, and d
+// costs two wavefronts per quarter. A thread's x rows are contiguous in memory but 8 KB apart from
+// its lane neighbours', so x goes out through the d tile (the thread's own d slots) by TMA store;
+// the next group's a, b and c tiles load early, its d tile at the top once the store has read it.
+template <int M, int C, bool XL>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
     refine_tree_kernel(const Args A, const __grid_constant__ TmaMaps maps) {
   static_assert(C == 2 || C == 4 || C == 8, "cluster size");
   static_assert(M >= 4 && M % 2 == 0, "rows per partition");
+  static_assert(!XL || M == 16, "unit-stride tiles: a partition is half of a 32-row box");
   constexpr int H = M / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];  // aligned to 1 KB below
-  // tile mbarriers: rows [0, M/2) and [M/2, M) of every array arrive on bar[0] and bar[1]
+  // tile mbarriers: rows [0, M/2) and [M/2, M) of every array arrive on bar[0] and bar[1] (XL:
+  // the whole tile on bar[0])
   __shared__ __align__(8) uint64_t bar[2];
   // exchange mbarriers: [0], [1] block slots of even / odd passes, [2], [3] norm slots
   __shared__ __align__(8) uint64_t xbar[4];
@@ -272,19 +306,21 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
   double* td = reinterpret_cast<double*>(tc + M * 256);
   float* slots = reinterpret_cast<float*>(td + M * 256);
   unsigned* norms = reinterpret_cast<unsigned*>(slots + 2 * C * kTreeSlotPitch);
-  // This thread's element of row 0 in each tile under the 128-byte swizzle (16-byte chunk index
-  // XOR 128-byte row index mod 8; the row index mod 8 is the partition p). Row t is 1 KB further.
-  const int fo = p * 32 + (((w ^ p) & 7) << 2) + jj;
-  const float* ra = ta + fo;
-  const float* rb = tb + fo;
-  const float* rc = tc + fo;
-  double* rd = td + (w >> 2) * (M * 128) + p * 16 + ((((w & 3) * 2 + (jj >> 1)) ^ p) << 1) + (jj & 1);
-  float2* rd2 = reinterpret_cast<float2*>(rd);  // d as a float pair, written in place by pass 0
-  // x leaves from registers to global memory, or, in place, by TMA store through the a and b
-  // tiles (32 KB, the layout of the d tile)
+  float2* td2 = reinterpret_cast<float2*>(td);  // d as float pairs, written in place by pass 0
+  // Element of row t of this thread's partition in the a, b, c tiles (fidx) and in the d tile
+  // (didx). Strided lines: the 128-byte swizzle (16-byte chunk index XOR 128-byte row index mod
+  // 8, the row index mod 8 being the partition p), row t 1 KB further. XL: see the kernel header.
+  const int j7 = j & 7;
+  const int fo = XL ? ((p >> 1) << 10) + (j << 5) : p * 32 + (((w ^ p) & 7) << 2) + jj;
+  const int fx = ((p & 1) << 2) ^ j7;  // XL: rows 4q..4q+3 of a, b, c are in chunk fx ^ q
+  const int dof = XL ? (p << 9) + (j << 4)
+                     : (w >> 2) * (M * 128) + p * 16 + ((((w & 3) * 2 + (jj >> 1)) ^ p) << 1) + (jj & 1);
+  auto fidx = [&](int t) { return XL ? fo + ((fx ^ (t >> 2)) << 2) + (t & 3) : fo + t * 256; };
+  auto didx = [&](int t) { return XL ? dof + (((t >> 1) ^ j7) << 1) + (t & 1) : dof + t * 128; };
+  // x leaves from registers to global memory, or by TMA store from the thread's d slots (XL) or,
+  // in place, from the a and b tiles (32 KB, the layout of the d tile)
   const bool inplace = A.x == A.d;
-  double* const tx = reinterpret_cast<double*>(ta);
-  double* const rx = tx + (rd - td);
+  double* const tx = (XL && !inplace) ? td : reinterpret_cast<double*>(ta);
   const int64_t es = A.lay.es, ic = A.lay.ic;
   const float keep = certify_keep(A.tol);
 
@@ -309,10 +345,12 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
     const int64_t eoff = A.lay.off(active ? line0 + j : 0) + (int64_t)kg * M * es;  // this partition's row 0
     double* px = (double*)A.x + eoff;
     const int c_in = (int)(line0 % ic), c_out = (int)(line0 / ic), c_p = rank * kTreeParts;
-    // every group after the cluster's first came in during the previous group, unless in place
-    if (tid == 0 && (inplace || g == (int64_t)(blockIdx.x / C))) {
-      bulk_wait_read_all();  // in place: the previous tile's x store has read the a and b tiles
-      tree_load_tiles<M>(maps, ta, tb, tc, td, bar, c_in, c_out, c_p);
+    // every group after the cluster's first came in during the previous group (XL: its a, b and
+    // c), unless in place
+    const bool first_group = g == (int64_t)(blockIdx.x / C);
+    if (tid == 0 && (XL || inplace || first_group)) {
+      bulk_wait_read_all();  // the previous group's x store has read the tile it went through
+      tree_load_tiles<M, XL>(maps, ta, tb, tc, td, bar, c_in, c_out, c_p, (inplace || first_group) ? 3 : 2);
     }
     if (!mbar_wait_bounded(&bar[0], tph0, kTmaWaitPolls) && alive) {
       alive = false;
@@ -328,22 +366,51 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
     Sweep<M> S;  // its factors serve pass 1 as well (same matrix)
     {
       float dom = -INFINITY;  // max over this partition's rows of dom_excess
+      if constexpr (XL) {
 #pragma unroll
-      for (int t = 0; t < M; ++t) {
-        if (t == H) {  // the second half of the rows (the first half is being swept meanwhile)
-          if (!mbar_wait_bounded(&bar[1], tph1, kTmaWaitPolls) && alive) {
-            alive = false;
-            report_error(A.st, 6);
+        for (int q = 0; q < M / 4; ++q) {  // rows 4q..4q+3
+          const int f4 = fo + ((fx ^ q) << 2), d0 = dof + (((2 * q) ^ j7) << 1), d1 = dof + (((2 * q + 1) ^ j7) << 1);
+          const float4 a4 = *reinterpret_cast<const float4*>(ta + f4);
+          const float4 b4 = *reinterpret_cast<const float4*>(tb + f4);
+          const float4 c4 = *reinterpret_cast<const float4*>(tc + f4);
+          const double2 e0 = *reinterpret_cast<const double2*>(td + d0);
+          const double2 e1 = *reinterpret_cast<const double2*>(td + d1);
+          const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
+          const float cv[4] = {c4.x, c4.y, c4.z, c4.w};
+          const double dv[4] = {e0.x, e0.y, e1.x, e1.y};
+          ff sp[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int t = 4 * q + u;
+            float a = av[u], c = cv[u];
+            if (t == 0 && first_part) a = 0.f;
+            if (t == M - 1 && last_part) c = 0.f;
+            dom = fmaxf(dom, dom_excess(a, bv[u], c, keep));
+            sp[u] = split_f64_fast(dv[u]);
+            S.row(t, a, bv[u], c, sp[u].h);
           }
-          tph1 ^= 1u;
+          // same thread, same 16 bytes: read before write
+          *reinterpret_cast<float4*>(td + d0) = make_float4(sp[0].h, sp[0].l, sp[1].h, sp[1].l);
+          *reinterpret_cast<float4*>(td + d1) = make_float4(sp[2].h, sp[2].l, sp[3].h, sp[3].l);
         }
-        float a = ra[t * 256], b = rb[t * 256], c = rc[t * 256];
-        if (t == 0 && first_part) a = 0.f;
-        if (t == M - 1 && last_part) c = 0.f;
-        dom = fmaxf(dom, dom_excess(a, b, c, keep));
-        const ff dd = split_f64_fast(rd[t * 128]);
-        rd2[t * 128] = make_float2(dd.h, dd.l);  // same thread, same 8 bytes: read before write
-        S.row(t, a, b, c, dd.h);
+      } else {
+#pragma unroll
+        for (int t = 0; t < M; ++t) {
+          if (t == H) {  // the second half of the rows (the first half is being swept meanwhile)
+            if (!mbar_wait_bounded(&bar[1], tph1, kTmaWaitPolls) && alive) {
+              alive = false;
+              report_error(A.st, 6);
+            }
+            tph1 ^= 1u;
+          }
+          float a = ta[fidx(t)], b = tb[fidx(t)], c = tc[fidx(t)];
+          if (t == 0 && first_part) a = 0.f;
+          if (t == M - 1 && last_part) c = 0.f;
+          dom = fmaxf(dom, dom_excess(a, b, c, keep));
+          const ff dd = split_f64_fast(td[didx(t)]);
+          td2[didx(t)] = make_float2(dd.h, dd.l);  // same thread, same 8 bytes: read before write
+          S.row(t, a, b, c, dd.h);
+        }
       }
       const Blk blk = S.block();
       if (!started) {
@@ -377,30 +444,49 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
       // ---------------- pass 1: correction for r = d - A x_0, x = x_0 + dx
       unsigned prev, gdx, gxm;
       {
-#pragma unroll
-        for (int t = 0; t < M; ++t) {
-          float a = ra[t * 256], b = rb[t * 256], c = rc[t * 256];
+        auto row1 = [&](int t, float a, float b, float c, float dh, float dl) {
           if (t == 0 && first_part) a = 0.f;
           if (t == M - 1 && last_part) c = 0.f;
-          const float2 dd = rd2[t * 128];
           const float xm = t == 0 ? u0 : x0[t > 0 ? t - 1 : 0];
           const float xp = t == M - 1 ? v0 : x0[t < M - 1 ? t + 1 : 0];
-          S.row_rhs(t, a, b, residual_f(a, b, c, dd.x, dd.y, xm, x0[t], xp));
+          S.row_rhs(t, a, b, residual_f(a, b, c, dh, dl, xm, x0[t], xp));
+        };
+        if constexpr (XL) {
+#pragma unroll
+          for (int q = 0; q < M / 4; ++q) {
+            const int f4 = fo + ((fx ^ q) << 2);
+            const float4 a4 = *reinterpret_cast<const float4*>(ta + f4);
+            const float4 b4 = *reinterpret_cast<const float4*>(tb + f4);
+            const float4 c4 = *reinterpret_cast<const float4*>(tc + f4);
+            const float4 e0 = *reinterpret_cast<const float4*>(td + dof + (((2 * q) ^ j7) << 1));
+            const float4 e1 = *reinterpret_cast<const float4*>(td + dof + (((2 * q + 1) ^ j7) << 1));
+            row1(4 * q, a4.x, b4.x, c4.x, e0.x, e0.y);
+            row1(4 * q + 1, a4.y, b4.y, c4.y, e0.z, e0.w);
+            row1(4 * q + 2, a4.z, b4.z, c4.z, e1.x, e1.y);
+            row1(4 * q + 3, a4.w, b4.w, c4.w, e1.z, e1.w);
+          }
+        } else {
+#pragma unroll
+          for (int t = 0; t < M; ++t) {
+            const float2 dd = td2[didx(t)];
+            row1(t, ta[fidx(t)], tb[fidx(t)], tc[fidx(t)], dd.x, dd.y);
+          }
         }
         const Blk blk = S.block();
         float u, v, xs_c, xe_c;
         tree_stage_b<C>(blk, nx, slots + C * kTreeSlotPitch, &xbar[1], xph1 & 1u, rank, p, jj, j, u, v, xs_c, xe_c,
                         prev, alive, A.st);  // prev: line max |x_0|
         ++xph1;
-        // Every thread has finished its pass-1 sweep, the last read of the tiles (x does not pass
-        // through them unless in place): the next group's rows may come in. The d pairs written
-        // in place by pass 0 are ordered before the copies' writes by each writer's proxy fence.
+        // Every thread has finished its pass-1 sweep, the last read of the a, b and c tiles (and,
+        // unless x goes through it, of the d tile): the next group's rows may come in. The d pairs
+        // written in place by pass 0 are ordered before the copies' writes by each writer's proxy
+        // fence.
         if (!inplace) {
           fence_proxy_async_smem();
           __syncthreads();
           if (tid == 0 && g + n_clusters < n_groups) {
             const int64_t l1 = (g + n_clusters) * kTreeLines;
-            tree_load_tiles<M>(maps, ta, tb, tc, td, bar, (int)(l1 % ic), (int)(l1 / ic), c_p);
+            tree_load_tiles<M, XL>(maps, ta, tb, tc, td, bar, (int)(l1 % ic), (int)(l1 / ic), c_p, XL ? 1 : 3, !XL);
           }
         }
         float dx[M];
@@ -410,22 +496,35 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
         for (int t = 0; t < M; ++t) ndx = max(ndx, abs_bits(dx[t]));
         tree_norms_push<C>(line_max(ndx), nx, norms + C * kTreeNormPitch, &xbar[3], rank, p, j);
         // x = x_0 + dx (exact widenings, one FP64 add): straight to global memory (for a fixed
-        // row the four lines of a lane quad are 32 contiguous bytes), or in place through the a
-        // and b tiles by TMA store (every thread's pass-1 sweep is done: the barrier below)
-        if (!inplace) {
+        // row the four lines of a lane quad are 32 contiguous bytes), or by TMA store through the
+        // thread's own d slots (XL) or, in place, through the a and b tiles (every thread's pass-1
+        // sweep is done: the barrier below)
+        if (!XL && !inplace) {
           if (active) {
 #pragma unroll
             for (int t = 0; t < M; ++t) px[t * es] = f2d_fast(x0[t]) + f2d_fast(dx[t]);
           }
         } else {
-          __syncthreads();
+          if (inplace) __syncthreads();
+          if constexpr (XL) {
 #pragma unroll
-          for (int t = 0; t < M; ++t) rx[t * 128] = f2d_fast(x0[t]) + f2d_fast(dx[t]);
+            for (int q = 0; q < M / 2; ++q)
+              *reinterpret_cast<double2*>(tx + dof + ((q ^ j7) << 1)) =
+                  make_double2(f2d_fast(x0[2 * q]) + f2d_fast(dx[2 * q]), f2d_fast(x0[2 * q + 1]) + f2d_fast(dx[2 * q + 1]));
+          } else {
+#pragma unroll
+            for (int t = 0; t < M; ++t) tx[didx(t)] = f2d_fast(x0[t]) + f2d_fast(dx[t]);
+          }
           fence_proxy_async_smem();
           __syncthreads();
           if (tid == 0) {  // out-of-range lines of a partial group are not written
-            tma_store_4d(&maps.x, tx, c_in, c_out, c_p, 0);
-            tma_store_4d(&maps.x, tx + M * 128, c_in + 16, c_out, c_p, 0);
+            if constexpr (XL) {
+#pragma unroll
+              for (int i = 0; i < M / 2; ++i) tma_store_3d(&maps.x, tx + i * 512, c_p * M + 16 * i, c_in, c_out);
+            } else {
+              tma_store_4d(&maps.x, tx, c_in, c_out, c_p, 0);
+              tma_store_4d(&maps.x, tx + M * 128, c_in + 16, c_out, c_p, 0);
+            }
             bulk_commit();
           }
         }
@@ -445,15 +544,25 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
       const double* gd = (const double*)A.d + eoff;
       while (!all_done && it < A.max_iters) {
         ++it;
+        if (tid == 0 && (XL || inplace)) {
+          bulk_wait_all();  // x of pass 1 is in global memory
+          fence_proxy_async_global();
+        }
         if (inplace) {
           if (tid == 0) {
-            bulk_wait_all();  // x of pass 1 is in global memory
-            fence_proxy_async_global();
             mbar_arrive_expect_tx(&bar[0], 2u * M * 1024u);  // a and b again (x went through their tiles)
+            if constexpr (XL) {
 #pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              tma_load_4d(ta + h * H * 256, &maps.a, &bar[0], c_in, c_out, c_p, h * H);
-              tma_load_4d(tb + h * H * 256, &maps.b, &bar[0], c_in, c_out, c_p, h * H);
+              for (int i = 0; i < M / 4; ++i) {
+                tma_load_3d(ta + i * 1024, &maps.a, &bar[0], c_p * M + 32 * i, c_in, c_out);
+                tma_load_3d(tb + i * 1024, &maps.b, &bar[0], c_p * M + 32 * i, c_in, c_out);
+              }
+            } else {
+#pragma unroll
+              for (int h = 0; h < 2; ++h) {
+                tma_load_4d(ta + h * H * 256, &maps.a, &bar[0], c_in, c_out, c_p, h * H);
+                tma_load_4d(tb + h * H * 256, &maps.b, &bar[0], c_in, c_out, c_p, h * H);
+              }
             }
           }
           if (!mbar_wait_bounded(&bar[0], tph0, kTmaWaitPolls) && alive) {
@@ -476,10 +585,10 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
           float a = 0.f, b = 1.f, c = 0.f;
           ff dd{0.f, 0.f};
           if (inplace) {
-            a = ra[t * 256];
-            b = rb[t * 256];
-            c = rc[t * 256];
-            const float2 dp = rd2[t * 128];
+            a = ta[fidx(t)];
+            b = tb[fidx(t)];
+            c = tc[fidx(t)];
+            const float2 dp = td2[didx(t)];
             dd = ff{dp.x, dp.y};
           } else if (active) {
             a = ga[t * es];
@@ -526,9 +635,9 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
         if (!line_done) report_error(A.st, 7);
       }
     }
-    // In place, the next TMA load (at the top) rewrites the tiles: the generic-proxy writes to them
-    // (d split in place, x) were fenced before the x store, and the last __syncthreads_and above
-    // ordered every read.
+    // Where x went through the tiles by TMA store, the next TMA load into them waits for the store's
+    // read (at the top); the generic-proxy writes to them (d split in place, x) were fenced before
+    // the store, and the last __syncthreads_and above ordered every read.
   }
   if (!started) cluster_wait();  // a CTA without a group still completes the start-up barrier
   if (tid == 0) bulk_wait_all();  // the last x store has been written

@@ -280,6 +280,35 @@ bool encode_map(CUtensorMap* map, const void* ptr, bool f64, const tdma_desc_t& 
   return r == CUDA_SUCCESS;
 }
 
+// Unit-stride lines (the merge-tree kernel's XL tiles): a 3D map {row, inner line, outer line} with
+// boxes of `box_rows` rows (128 bytes) of 32 lines and the 128-byte swizzle.
+bool tma_layout_ok_x(const tdma_desc_t& d) {
+  if (d.n <= 0 || d.elem_stride != 1 || d.n_lines < 32 || d.inner_stride < d.n || d.inner_stride % 4) return false;
+  if (d.n_lines > d.inner_count) {
+    if (d.inner_count % 32 || d.n_lines % d.inner_count) return false;
+    if (d.outer_stride % 4 || d.outer_stride < d.inner_count * d.inner_stride) return false;
+  }
+  return d.inner_count < (1ll << 31) && d.n_lines / std::max<int64_t>(1, d.inner_count) < (1ll << 31) &&
+         d.inner_stride * 8 < (1ll << 40) && d.outer_stride * 8 < (1ll << 40);
+}
+bool encode_map_x(CUtensorMap* map, const void* ptr, bool f64, const tdma_desc_t& d) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn || !aligned(ptr, 16)) return false;
+  const cuuint64_t eb = f64 ? 8 : 4;
+  const int64_t outer = d.n_lines > d.inner_count ? d.n_lines / d.inner_count : 1;
+  const int64_t inner = d.n_lines > d.inner_count ? d.inner_count : d.n_lines;
+  cuuint64_t dims[3] = {(cuuint64_t)d.n, (cuuint64_t)inner, (cuuint64_t)outer};
+  const cuuint64_t os = outer > 1 ? (cuuint64_t)d.outer_stride * eb : (cuuint64_t)inner * d.inner_stride * eb;
+  cuuint64_t strides[2] = {(cuuint64_t)d.inner_stride * eb, (os + 15) / 16 * 16};
+  cuuint32_t box[3] = {f64 ? 16u : 32u, 32u, 1u};
+  cuuint32_t estr[3] = {1, 1, 1};
+  const CUresult r = fn(map, f64 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                        const_cast<void*>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 int reduced_groups(int P) {
   int G = 1;
   while (2 * G <= P && (2 * P) % (2 * G) == 0 && (2 * P) / (2 * G) >= 2 * (2 * G)) G *= 2;
@@ -342,9 +371,12 @@ size_t tree_smem(int M, int C) {
 #undef TDMA_TR_SMEM
   return 0;
 }
-int64_t tree_resident_clusters(int M, int C, size_t smem);
-bool refine_tree_config(const tdma_desc_t& d, int P_req, tdma_config_t& c) {
-  // TDMA_DISABLE_TREE=1 leaves these shapes to the cluster kernel with serial Stage B
+int64_t tree_resident_clusters(int M, int C, bool xl, size_t smem);
+// Lines along a strided axis (lines adjacent in memory), or with `xl` unit-stride lines (rows
+// adjacent in memory): the same kernel with the tiles cut along the other axis.
+bool refine_tree_config(const tdma_desc_t& d, int P_req, tdma_config_t& c, bool xl = false) {
+  // TDMA_DISABLE_TREE=1 leaves these shapes to the cluster kernel with serial Stage B (strided
+  // lines) or the chunk kernel (unit-stride lines)
   if (const char* e = std::getenv("TDMA_DISABLE_TREE")) if (e[0] == '1') return false;
   int M, C;
   if (!tree_shape(d.n, M, C)) return false;
@@ -355,13 +387,13 @@ bool refine_tree_config(const tdma_desc_t& d, int P_req, tdma_config_t& c) {
   t.lines_per_block = kTreeLines;
   t.threads_per_block = 256;
   t.smem_bytes = (int64_t)tree_smem(M, C);
+  t.variant = xl ? TDMA_VARIANT_REFINE_TREE_X : TDMA_VARIANT_REFINE_TREE;
+  if (xl ? !tma_layout_ok_x(d) : !tma_layout_ok(d, t)) return false;
+  if (d.n_lines < kTreeLines) return false;  // a cluster needs a full line group
   // persistent grid: the clusters that fit on the GPU at once, at most one per line group
   const int64_t groups = (d.n_lines + kTreeLines - 1) / kTreeLines;
-  const int64_t resident = tree_resident_clusters(M, C, (size_t)t.smem_bytes);
+  const int64_t resident = tree_resident_clusters(M, C, xl, (size_t)t.smem_bytes);
   t.blocks = (int32_t)(C * (resident > 0 ? std::min(groups, resident) : groups));
-  t.variant = TDMA_VARIANT_REFINE_TREE;
-  if (!tma_layout_ok(d, t)) return false;
-  if (d.n_lines < kTreeLines) return false;  // a cluster needs a full line group
   c = t;
   return true;
 }
@@ -395,12 +427,12 @@ template <class K> cudaError_t set_smem(K kernel, size_t bytes) {
 }
 
 // Clusters of the merge-tree kernel that fit on the current device at once (0 if unknown).
-int64_t tree_resident_clusters(int M, int C, size_t smem) {
+int64_t tree_resident_clusters(int M, int C, bool xl, size_t smem) {
   static std::mutex mu;
-  static std::map<std::tuple<int, int, int>, int64_t> cache;
+  static std::map<std::tuple<int, int, int, int>, int64_t> cache;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-  const auto key = std::make_tuple(dev, M, C);
+  const auto key = std::make_tuple(dev, M, C, xl ? 1 : 0);
   {
     std::lock_guard<std::mutex> lock(mu);
     auto it = cache.find(key);
@@ -411,9 +443,11 @@ int64_t tree_resident_clusters(int M, int C, size_t smem) {
   cfg.blockDim = dim3(256);
   cfg.dynamicSmemBytes = smem;
   int n = 0;
-#define TDMA_OCC_TR(MM, CC)                                                         \
-  if (M == MM && C == CC && set_smem(refine_tree_kernel<MM, CC>, smem) == cudaSuccess) \
-    if (cudaOccupancyMaxActiveClusters(&n, refine_tree_kernel<MM, CC>, &cfg) != cudaSuccess) n = 0;
+#define TDMA_OCC_TR(MM, CC)                                                                                  \
+  if (M == MM && C == CC && !xl && set_smem(refine_tree_kernel<MM, CC, false>, smem) == cudaSuccess)          \
+    if (cudaOccupancyMaxActiveClusters(&n, refine_tree_kernel<MM, CC, false>, &cfg) != cudaSuccess) n = 0;   \
+  if (M == MM && C == CC && xl && set_smem(refine_tree_kernel<MM, CC, true>, smem) == cudaSuccess)            \
+    if (cudaOccupancyMaxActiveClusters(&n, refine_tree_kernel<MM, CC, true>, &cfg) != cudaSuccess) n = 0;
   TDMA_REFINE_TREE_SHAPES(TDMA_OCC_TR)
 #undef TDMA_OCC_TR
   (void)cudaGetLastError();
@@ -492,13 +526,30 @@ cudaError_t launch_forward(const tdma_plan_s* p, const Args& A, cudaStream_t s) 
                       encode_map(&maps.d, A.d, true, p->desc, c, kTreeParts, 16, true, H) &&
                       encode_map(&maps.x, A.x, true, p->desc, c, kTreeParts, 16, true);
       if (!ok) return cudaErrorInvalidValue;
-#define TDMA_LAUNCH_TR(MM, CC)                                        \
-  if (c.rows_per_thread == MM && C == CC) {                            \
-    refine_tree_kernel<MM, CC><<<grid, block, sm, s>>>(A, maps);       \
-    return cudaGetLastError();                                          \
+#define TDMA_LAUNCH_TR(MM, CC)                                              \
+  if (c.rows_per_thread == MM && C == CC) {                                  \
+    refine_tree_kernel<MM, CC, false><<<grid, block, sm, s>>>(A, maps);      \
+    return cudaGetLastError();                                                \
   }
       TDMA_REFINE_TREE_SHAPES(TDMA_LAUNCH_TR)
 #undef TDMA_LAUNCH_TR
+      return cudaErrorInvalidValue;
+    }
+    case TDMA_VARIANT_REFINE_TREE_X: {
+      TmaMaps maps;
+      std::memset(&maps, 0, sizeof(maps));
+      const int C = c.partitions / kTreeParts;
+      const bool ok = encode_map_x(&maps.a, A.a, false, p->desc) && encode_map_x(&maps.b, A.b, false, p->desc) &&
+                      encode_map_x(&maps.c, A.c, false, p->desc) && encode_map_x(&maps.d, A.d, true, p->desc) &&
+                      encode_map_x(&maps.x, A.x, true, p->desc);
+      if (!ok) return cudaErrorInvalidValue;
+#define TDMA_LAUNCH_TRX(MM, CC)                                             \
+  if (c.rows_per_thread == MM && C == CC) {                                  \
+    refine_tree_kernel<MM, CC, true><<<grid, block, sm, s>>>(A, maps);       \
+    return cudaGetLastError();                                                \
+  }
+      TDMA_REFINE_TREE_SHAPES(TDMA_LAUNCH_TRX)
+#undef TDMA_LAUNCH_TRX
       return cudaErrorInvalidValue;
     }
     case TDMA_VARIANT_REFINE_CLUSTER: {
@@ -573,10 +624,13 @@ cudaError_t prepare_kernel(const tdma_plan_s* p) {
         case 16: return set_smem(refine_tma_kernel<16, 2>, sm);
         default: return set_smem(refine_tma_kernel<32, 1>, sm);
       }
-    case TDMA_VARIANT_REFINE_TREE: {
+    case TDMA_VARIANT_REFINE_TREE:
+    case TDMA_VARIANT_REFINE_TREE_X: {
       const int C = p->cfg.partitions / kTreeParts;
-#define TDMA_PREP_TR(MM, CC) \
-  if (p->cfg.rows_per_thread == MM && C == CC) return set_smem(refine_tree_kernel<MM, CC>, sm);
+      const bool xl = p->cfg.variant == TDMA_VARIANT_REFINE_TREE_X;
+#define TDMA_PREP_TR(MM, CC)                                                              \
+  if (p->cfg.rows_per_thread == MM && C == CC)                                            \
+    return xl ? set_smem(refine_tree_kernel<MM, CC, true>, sm) : set_smem(refine_tree_kernel<MM, CC, false>, sm);
       TDMA_REFINE_TREE_SHAPES(TDMA_PREP_TR)
 #undef TDMA_PREP_TR
       return cudaErrorInvalidValue;
@@ -933,6 +987,7 @@ std::vector<tdma_config_t> tune_candidates(const tdma_desc_t& d, bool allow_tma)
   tdma_config_t c{};
   if (d.precision == TDMA_F32_REFINE) {
     if (allow_tma && refine_tree_config(d, 0, c)) out.push_back(c);
+    if (allow_tma && refine_tree_config(d, 0, c, true)) out.push_back(c);
     if (allow_tma && refine_cluster_config(d, 0, c)) out.push_back(c);
     for (int P : Ps) {
       tdma_config_t r{};
@@ -1230,8 +1285,10 @@ tdma_status_t tdma_plan_create(tdma_plan_t* plan, const tdma_desc_t* desc, size_
     p->workspace = workspace_for(*desc, c);
   } else if (is_uniform(*desc)) {
     bool ok = false;
-    if (desc->precision == TDMA_F32_REFINE && build_packed_uniform(p)) {
-      c = p->cfg;  // unit-stride lines: the chunk kernel over whole contiguous lines
+    if (desc->precision == TDMA_F32_REFINE && p->allow_tma && refine_tree_config(*desc, desc->partitions, c, true)) {
+      ok = true;  // unit-stride lines of n = 8 C M: the merge-tree kernel with tiles along the lines
+    } else if (desc->precision == TDMA_F32_REFINE && build_packed_uniform(p)) {
+      c = p->cfg;  // other unit-stride lines: the chunk kernel over whole contiguous lines
       ok = true;
     } else if (desc->precision == TDMA_F32_REFINE) {
       ok = p->allow_tma && (refine_tree_config(*desc, desc->partitions, c) ||

@@ -229,10 +229,11 @@ def test_packed_backward_second_correction():
         assert O.rel_l2(h(g[3])[s], O.thomas_ext(at, bt, ct, h(w)[s])) <= 1e-12
 
 
-@pytest.mark.parametrize("n,L,gap", [(1024, 300, 0), (CHUNK_ROWS, 3, 0), (5000, 40, 16), (37, 2000, 0), (2, 9, 3)])
+@pytest.mark.parametrize("n,L,gap", [(1000, 300, 0), (CHUNK_ROWS, 3, 0), (5000, 40, 16), (37, 2000, 0), (2, 9, 3)])
 def test_uniform_unit_stride_lines_use_the_chunk_kernel(n, L, gap):
-    # uniform lines along the contiguous axis in FP32 + refinement: whole contiguous lines form
-    # the chunks (a gap between lines ends a chunk); x between the lines stays untouched
+    # uniform lines along the contiguous axis in FP32 + refinement whose length is not one the
+    # merge-tree kernel takes (n = 256, 512, 1024): whole contiguous lines form the chunks (a gap
+    # between lines ends a chunk); x between the lines stays untouched
     g = synth.grid_general((L, n + gap), 1, 20 + n, device="cuda", fp32_coefficients=True)
     a, b, c = (g[k][:, :n] for k in ("a32", "b32", "c32"))
     d = g["d"][:, :n]

@@ -7,8 +7,8 @@ problem) with a diagonal-dominance margin eps that sets kappa from about 10^2 to
 case the solve must either meet 1e-12 against the extended-precision oracle (per line and pooled)
 or report TDMA_ERR_NOT_CONVERGED: a status of 0 with a larger error is a silent failure and fails
 the test. Well-conditioned cases (their floor certified by the rows' diagonal dominance) must
-converge. Covered for the kernel of strided lines (lines along the slowest axis) and for the chunk
-kernel (unit-stride lines)."""
+converge. Covered for the merge-tree kernel on strided lines (lines along the slowest axis) and
+on unit-stride lines of n = 1024, and for the chunk kernel (unit-stride lines of n = 1000)."""
 import numpy as np
 import pytest
 import torch
@@ -40,11 +40,13 @@ def _kappa(a, b, c):
 EPS = [3e-2, 3e-3, 3e-4, 3e-5, 0.0]  # kappa about 1e2 .. 1e6
 
 
-@pytest.mark.parametrize("layout", ["strided", "unit_stride"])
+@pytest.mark.parametrize("layout", ["strided", "unit_stride", "unit_stride_chunk"])
 @pytest.mark.parametrize("eps", EPS)
 def test_f32_refine_meets_1e12_or_reports_not_converged(layout, eps):
     lines = 256
     a, b, c, d = _lines(eps, lines, 1000 + int(eps * 1e6))
+    if layout == "unit_stride_chunk":  # lines of 1000: not a length of the merge-tree kernel
+        a, b, c, d = (np.ascontiguousarray(t[:, :1000]) for t in (a, b, c, d))
     kappa = _kappa(a[0], b[0], c[0])
     ref = O.thomas_ext(a, b, c, d)
     if layout == "strided":  # [N][lines]: lines along the slowest axis
