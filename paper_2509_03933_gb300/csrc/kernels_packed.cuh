@@ -7,22 +7,26 @@
 // two blocks meets a line boundary, the terms that couple them vanish and the merge only copies.
 // At plan time the lines, in memory order, are cut into chunks of whole, contiguous lines of at
 // most kPackChunk rows; chunk g is solved by one cluster of kPackC CTAs with 224 partitions each
-// of M rows (M even, the smallest with 896 M >= rows), the rows past the chunk's end being
+// of M rows (M odd, the smallest with 896 M >= rows), the rows past the chunk's end being
 // identity rows (a = c = d = 0, b = 1: decoupled unknowns equal to 0), so that every partition is
-// full and the row loops are straight-line code compiled for each M. The paper batches lines of one direction into
-// composite systems (Section 4.2.1); here the batch is a chunk and the composite system is the
-// chunk's rows.
+// full and the row loops are straight-line code compiled for each M. The paper batches lines of
+// one direction into composite systems (Section 4.2.1); here the batch is a chunk and the
+// composite system is the chunk's rows.
 //
-// Data path per chunk: every CTA copies its segment of a, b, c (float) and d (double) into
-// shared memory with coalesced asynchronous copies, transposed to [row in partition][partition]
-// (pitch 257) so that the 32 lanes of a warp read 32 consecutive words; the next chunk is
-// prefetched into L2 meanwhile. Pass 0 solves with the float part of d; pass 1 solves for the
-// extra-precise residual (float pairs) and corrects; x = x_0 + dx leaves in FP64 through the
-// shared-memory space of a and b, copied out coalesced. Per-line maxima of |x_0| and |dx| go to
-// a per-line table by atomics; after a cluster barrier the thread holding each line's first row
-// applies the stop rule of the other refinement kernels, and a second barrier shares the
-// verdict. Lines that need more corrections (rare) take further passes that read x back from
-// global memory.
+// Data path per chunk: every CTA's segment of a, b, c (float) and d (double) is one contiguous
+// run of rows in memory and lands in shared memory in the same order, partition k's rows at
+// [k M, (k + 1) M): the 16-byte-aligned interior of each array by one bulk copy (cp.async.bulk,
+// completing on the CTA's tile mbarrier), the few elements before and after it by plain loads.
+// With M odd the 32 lanes of a warp, k M + t apart, read 32 distinct banks (4-byte words) or the
+// 32 banks in each half-warp (8-byte words), with no padding. Pass 0 solves with the float part of
+// d; pass 1 solves for the extra-precise residual (float pairs) and corrects; x = x_0 + dx in FP64
+// goes over the thread's own d slots (with x over d, into the space of a and b), and each warp
+// copies its own 32 M contiguous rows out, coalesced. The next chunk's a, b and c copies go out
+// as soon as pass 1's Stage B has passed its last read of them, its d copies once every warp's x
+// has left. Per-line maxima of |x_0| and |dx| go to a per-line table by atomics; after a cluster
+// barrier every CTA applies the stop rule of the other refinement kernels to the chunk's lines.
+// Lines that need more corrections (rare) take further passes that read x back from global
+// memory.
 #pragma once
 #include <cooperative_groups.h>
 #include "layout.cuh"
@@ -38,9 +42,10 @@ constexpr int kPackC = 4;                    // CTAs per cluster
 constexpr int kPackW = 7;                    // compute warps per CTA
 constexpr int kPackT = 32 * kPackW;          // compute threads (partitions) per CTA
 constexpr int kPackThreads = kPackT + 32;    // + one coordinator warp
-constexpr int kPackM = 20;                   // rows per partition at most
-constexpr int kPackPitch = kPackT + 1;       // shared-memory pitch of one row position
-constexpr int kPackChunk = kPackC * kPackT * kPackM;  // rows per chunk at most (17920)
+constexpr int kPackM = 21;                   // rows per partition at most (odd)
+constexpr int kPackRowBits = 21;             // metadata bits of the row starts (bit 21: line end after)
+constexpr int kPackTile = kPackT * kPackM + 8;  // tile elements: a segment and its alignment shift
+constexpr int kPackChunk = kPackC * kPackT * kPackM;  // rows per chunk at most (18816)
 constexpr uint32_t kPackWaitPolls = 1u << 16;
 // Per-line words of the norm table (float bits of non-negative values): [0] max |dx| and [1] max
 // |x_0| of the first correction (zero at launch, written once); [2] max |dx|, [3] max |x| of a
@@ -58,8 +63,8 @@ struct PackedChunk {
 };
 
 // Partition metadata (one pair of words per partition of every distinct chunk structure):
-//   x bits 0..19  bit t: row t of the partition starts a line
-//   x bit 20      the row after the partition's last row starts a line or lies past the chunk
+//   x bits 0..20  bit t: row t of the partition starts a line
+//   x bit 21      the row after the partition's last row starts a line or lies past the chunk
 //   y             line of the partition's first row, counted from the chunk's first line
 struct PackedTables {
   const PackedChunk* chunks;
@@ -68,13 +73,6 @@ struct PackedTables {
   int32_t n_chunks;
 };
 
-TDMA_DEV void cp_async4(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-TDMA_DEV void cp_async8(void* dst, const void* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
-}
-TDMA_DEV void cp_async_wait_all() { asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory"); }
 // L2 prefetch of the 16-byte-aligned part of [p, p + bytes)
 TDMA_DEV void prefetch_l2_range(const void* p, int64_t bytes) {
   const uint64_t s = ((uint64_t)p + 15) & ~(uint64_t)15, e = ((uint64_t)p + bytes) & ~(uint64_t)15;
@@ -88,14 +86,6 @@ TDMA_DEV uint32_t ld_relaxed_u32(const uint32_t* p) {
 }
 TDMA_DEV void st_cluster_u32(uint32_t addr, uint32_t v) {
   asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
-}
-
-// Row index i of a CTA segment -> (partition k, row t within it) for M <= 20 and i < 4480:
-// k = floor(i / M) from a 20-bit reciprocal (exact there: i (2^20 / M rounded up) / 2^20
-// overshoots i / M by less than 4480 / 2^20 < 1 / 20).
-TDMA_DEV void seg_row(int i, int M, uint32_t inv, int& k, int& t) {
-  k = (int)(((uint32_t)i * inv) >> 20);
-  t = i - k * M;
 }
 
 // Stage A of one partition of m <= MM rows (runtime m, rows unrolled): the modified Thomas sweep
@@ -371,7 +361,7 @@ TDMA_DEV bool packed_later_verdict(uint32_t mask, int m, int line, uint32_t* nor
 
 // One further correction of a partition (rare): the coefficients read from global memory (with
 // TR those of the transposed rows), d from the shared-memory float pairs when they are still there
-// (sd != nullptr) or from global memory, x of the partition and its neighbours read back from
+// (sd: the partition's first row, else null) or from global memory, x of the partition and its neighbours read back from
 // global memory; residual in float pairs, Stage A/B/C, x += dx written back. Kept out of line so
 // that its registers do not weigh on the two main passes.
 template <bool TR>
@@ -395,7 +385,7 @@ __device__ __noinline__ void packed_later_pass(const PackedTables& PT, const flo
       const float b = fb[gi];
       ff dd;
       if (sd) {
-        const float2 v = sd[t * kPackPitch];
+        const float2 v = sd[t];
         dd = ff{v.x, v.y};
       } else {
         dd = split_f64(gd[gi]);
@@ -424,14 +414,16 @@ __device__ __noinline__ void packed_later_pass(const PackedTables& PT, const flo
 }
 
 // Passes 0 and 1 of one compute thread for chunks of MM rows per partition (every partition
-// full; a and c already zero where lines start and end). Pass 0 solves with the float part of d
-// (split in place into float pairs), pass 1 solves for the extra-precise residual with the same
-// factors, and the pair (x_0, dx) goes to rx (the a and b space: named barrier 2 of pass 1
-// completes only after every compute warp has arrived on barrier 1, after its last read of a and
-// b), with the per-line maxima of |dx| and |x_0| to the line table. The copy-out forms x in FP64.
+// full; a and c already zero where lines start and end); ra, rb, rc, rd: the partition's first row
+// in the tiles. Pass 0 solves with the float part of d (split in place into float pairs), pass 1
+// solves for the extra-precise residual with the same factors, and x = x_0 + dx (exact widenings,
+// one FP64 add) goes to rx: over the thread's own d pairs (read by its pass-1 sweep), or, when x is
+// written over d, into the a and b space (named barrier 2 of pass 1 completes only after every
+// compute warp has arrived on barrier 1, after its last read of the tiles). The per-line maxima of
+// |dx| and |x_0| go to the line table.
 template <int MM>
 TDMA_DEV void packed_passes(const float* ra, const float* rb, const float* rc, const double* rd, float2* rd2,
-                            float2* rx, float* wsl0, const float4* dsl0, float* wsl1, const float4* dsl1, int w,
+                            double* rx, float* wsl0, const float4* dsl0, float* wsl1, const float4* dsl1, int w,
                             int lane, bool edge_s, bool edge_e, uint32_t mask, int line, uint32_t* norms,
                             float keep) {
   Sweep<MM> S;
@@ -441,9 +433,9 @@ TDMA_DEV void packed_passes(const float* ra, const float* rb, const float* rc, c
   {
 #pragma unroll
     for (int t = 0; t < MM; ++t) {
-      const ff dd = split_f64_fast(rd[t * kPackPitch]);
-      rd2[t * kPackPitch] = make_float2(dd.h, dd.l);  // same thread, same 8 bytes
-      const float a = ra[t * kPackPitch], b = rb[t * kPackPitch], c = rc[t * kPackPitch];
+      const ff dd = split_f64_fast(rd[t]);
+      rd2[t] = make_float2(dd.h, dd.l);  // same thread, same 8 bytes
+      const float a = ra[t], b = rb[t], c = rc[t];
       dom = fmaxf(dom, dom_excess(a, b, c, keep));
       S.row(t, a, b, c, dd.h);
     }
@@ -461,8 +453,8 @@ TDMA_DEV void packed_passes(const float* ra, const float* rb, const float* rc, c
   {
 #pragma unroll
     for (int t = 0; t < MM; ++t) {
-      const float a = ra[t * kPackPitch], b = rb[t * kPackPitch], c = rc[t * kPackPitch];
-      const float2 dd = rd2[t * kPackPitch];
+      const float a = ra[t], b = rb[t], c = rc[t];
+      const float2 dd = rd2[t];
       const float xm = t == 0 ? u0 : x0[t > 0 ? t - 1 : 0];
       const float xp = t == MM - 1 ? v0 : x0[t < MM - 1 ? t + 1 : 0];
       S.row_rhs(t, a, b, residual_f(a, b, c, dd.x, dd.y, xm, x0[t], xp));
@@ -475,7 +467,7 @@ TDMA_DEV void packed_passes(const float* ra, const float* rb, const float* rc, c
     LineMax nm;
     nm.init(mask, MM, line, 0, __float_as_uint(fmaxf(dom, 0.f)));
     S.solve_visit(xs, xe, [&](int t, float dxv) {
-      rx[t * kPackPitch] = make_float2(x0[t], dxv);
+      rx[t] = f2d_fast(x0[t]) + f2d_fast(dxv);
       nm.add(t, mask, dxv, x0[t], norms);
     });
     nm.finish(mask, MM, lane, norms);
@@ -483,64 +475,118 @@ TDMA_DEV void packed_passes(const float* ra, const float* rb, const float* rc, c
 }
 
 // compiled rows per partition (the plan rounds M up to one of these)
-#define TDMA_PACKED_M(X) X(2) X(4) X(6) X(8) X(10) X(12) X(14) X(16) X(18) X(20)
+#define TDMA_PACKED_M(X) X(3) X(5) X(7) X(9) X(11) X(13) X(15) X(17) X(19) X(21)
 
-// Persistent: the grid holds the clusters that fit on the GPU at once; cluster q takes chunks
-// q, q + Q, q + 2Q, ... (Q clusters, chunks sorted longest first at plan time). Warps 0..6 of a
-// CTA compute (one partition per thread), warp 7 coordinates Stage B.
-// Coefficients of row i of the chunk, copied into shared memory: (a_i, c_i), or with TR the
-// transposed system's (c_{i-1}, a_{i+1}) (the adjoint solve of the backward pass). Entries that
-// would come from outside the chunk lie on a line boundary, where they are zero.
-template <bool TR>
-TDMA_DEV void load_ac(float* sa, float* sc, const float* fa, const float* fc, int64_t gi, int ci, int rows) {
-  if (!TR) {
-    cp_async4(sa, fa + gi);
-    cp_async4(sc, fc + gi);
-  } else {
-    if (ci > 0) cp_async4(sa, fc + gi - 1); else *sa = 0.f;
-    if (ci + 1 < rows) cp_async4(sc, fa + gi + 1); else *sc = 0.f;
-  }
-}
-
-// Copies of chunk g's segment for this CTA into shared memory, transposed; rows past the chunk's
-// end become identity rows. Every thread of the CTA (the coordinator warp too).
-template <int C, bool TR>
-TDMA_DEV void packed_issue_loads(const PackedTables& PT, const Args& A, int g, int rank, int tid, float* ta, float* tb,
-                                 float* tc, double* td) {
+// Chunk g's segment for this CTA: rows [seg0, seg0 + segn) of the chunk, starting at element gbase.
+struct PackedSeg {
+  int64_t gbase;
+  int M, seg0, segn, rows;
+};
+TDMA_DEV PackedSeg packed_seg(const PackedTables& PT, int g, int rank) {
   const PackedChunk ch = PT.chunks[g];
-  const int M = ch.M;
-  const uint32_t inv = ((1u << 20) + (uint32_t)M - 1u) / (uint32_t)M;
-  const int seg0 = rank * kPackT * M;
-  const int segn = max(0, min(ch.rows - seg0, kPackT * M));
-  const int64_t gbase = ch.base + seg0;
-  const float* fa = (const float*)A.a;
-  const float* fb = (const float*)A.b;
-  const float* fc = (const float*)A.c;
-  const double* gd = (const double*)A.d;
-  // row i = tid + kPackThreads j of the segment is row t of partition k; both advance by fixed steps
-  int k, t;
-  seg_row(tid, M, inv, k, t);
-  const int dk = kPackThreads / M, dt = kPackThreads - dk * M;
-  for (int i = tid; i < kPackT * M; i += kPackThreads) {
-    const int pos = t * kPackPitch + k;
-    if (i < segn) {
-      load_ac<TR>(ta + pos, tc + pos, fa, fc, gbase + i, seg0 + i, ch.rows);
-      cp_async4(tb + pos, fb + gbase + i);
-      cp_async8(td + pos, gd + gbase + i);
-    } else {  // identity row past the chunk's end
-      ta[pos] = 0.f;
-      tb[pos] = 1.f;
-      tc[pos] = 0.f;
-      td[pos] = 0.0;
-    }
-    k += dk;
-    t += dt;
-    if (t >= M) {
-      t -= M;
-      ++k;
-    }
+  PackedSeg q;
+  q.M = ch.M;
+  q.seg0 = rank * kPackT * ch.M;
+  q.segn = max(0, min(ch.rows - q.seg0, kPackT * ch.M));
+  q.gbase = ch.base + q.seg0;
+  q.rows = ch.rows;
+  return q;
+}
+
+// One array's copy into its tile. Tile element sh + i holds segment row i, read from src[i]
+// (src: the global element of segment row 0; for the transposed rows of TR shifted by one) for
+// the rows i in [lo, hi); sh is src's position within its 16-byte word (0..3 floats, 0..1
+// doubles), so that the bulk copy of the interior [a0, a1), 16-byte aligned at both ends in global
+// memory, lands 16-byte aligned in the tile too. Rows outside [lo, hi) lie past a line's end
+// (zero) or past the chunk (identity rows).
+struct PackedArr {
+  const char* src;  // global address of segment row 0 (one before the array when lo >= 1)
+  char* tile;       // tile base (16-byte aligned)
+  int es, sh, lo, hi, a0, a1;
+};
+TDMA_DEV PackedArr packed_arr(const void* base, int64_t s, void* tile, int es, int lo, int hi) {
+  PackedArr r;
+  r.es = es;
+  r.src = reinterpret_cast<const char*>(base) + s * es;
+  r.tile = reinterpret_cast<char*>(tile);
+  const int k = 16 / es;
+  r.sh = (int)((reinterpret_cast<uintptr_t>(r.src) / (uintptr_t)es) & (uintptr_t)(k - 1));
+  r.lo = lo;
+  r.hi = max(lo, hi);
+  r.a0 = min(r.hi, lo + ((k - ((r.sh + lo) & (k - 1))) & (k - 1)));
+  r.a1 = max(r.a0, r.hi - ((r.sh + r.hi) & (k - 1)));
+  return r;
+}
+// The four tiles' copies of segment q: (a, b, c, d), or with TR the transposed rows
+// (c_{i-1}, b, a_{i+1}, d), whose first and last elements would come from outside the chunk and
+// are not read (they fall on a line start and a line end, where they are zero).
+template <bool TR>
+TDMA_DEV void packed_arrs(const Args& A, const PackedSeg& q, float* ta, float* tb, float* tc, double* td,
+                          PackedArr (&r)[4]) {
+  if (!TR) {
+    r[0] = packed_arr(A.a, q.gbase, ta, 4, 0, q.segn);
+    r[2] = packed_arr(A.c, q.gbase, tc, 4, 0, q.segn);
+  } else {
+    r[0] = packed_arr(A.c, q.gbase - 1, ta, 4, q.seg0 == 0 ? 1 : 0, q.segn);
+    r[2] = packed_arr(A.a, q.gbase + 1, tc, 4, 0, min(q.segn, q.rows - q.seg0 - 1));
+  }
+  r[1] = packed_arr(A.b, q.gbase, tb, 4, 0, q.segn);
+  r[3] = packed_arr(A.d, q.gbase, td, 8, 0, q.segn);
+}
+// One thread: the bulk copies of the tiles in `parts` (bit j: tile j of a, b, c, d) of segment q,
+// counted on the tile mbarrier (with `arrive` this call also arrives on it; without, the copies
+// count towards a phase whose arrival comes later).
+template <bool TR>
+TDMA_DEV void packed_bulk(const Args& A, const PackedSeg& q, float* ta, float* tb, float* tc, double* td,
+                          uint64_t* bar, int parts, bool arrive) {
+  PackedArr r[4];
+  packed_arrs<TR>(A, q, ta, tb, tc, td, r);
+  uint32_t bytes = 0;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if ((parts >> j) & 1) bytes += (uint32_t)(r[j].a1 - r[j].a0) * (uint32_t)r[j].es;
+  if (arrive) mbar_arrive_expect_tx(bar, bytes);
+  else mbar_expect_tx(bar, bytes);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (!((parts >> j) & 1) || r[j].a1 <= r[j].a0) continue;
+    const int es = r[j].es;
+    bulk_load_1d(r[j].tile + (size_t)(r[j].sh + r[j].a0) * es, r[j].src + (size_t)r[j].a0 * es,
+                 (uint32_t)(r[j].a1 - r[j].a0) * (uint32_t)es, bar);
   }
 }
+// Every thread of the CTA: the tile elements of segment q that the bulk copies do not bring: rows
+// [lo, a0) and [a1, hi) by plain loads (at most three of each per array), zeros at [0, lo) and
+// [hi, segn), and identity rows past the chunk's end.
+template <bool TR>
+TDMA_DEV void packed_fill(const Args& A, const PackedSeg& q, float* ta, float* tb, float* tc, double* td, int tid) {
+  PackedArr r[4];
+  packed_arrs<TR>(A, q, ta, tb, tc, td, r);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const PackedArr& x = r[j];
+    const int head = x.a0, tail = x.hi - x.a1;  // rows [0, a0) then [a1, hi), then [hi, segn)
+    for (int i = tid; i < head + tail + (q.segn - x.hi); i += kPackThreads) {
+      const int row = i < head ? i : (i < head + tail ? x.a1 + (i - head) : x.hi + (i - head - tail));
+      const bool load = row >= x.lo && row < x.hi;
+      if (x.es == 4) {
+        const float v = load ? __ldg(reinterpret_cast<const float*>(x.src) + row) : 0.f;
+        reinterpret_cast<float*>(x.tile)[x.sh + row] = v;
+      } else {
+        const double v = load ? __ldg(reinterpret_cast<const double*>(x.src) + row) : 0.0;
+        reinterpret_cast<double*>(x.tile)[x.sh + row] = v;
+      }
+    }
+  }
+  // identity rows past the chunk's end: a = c = d = 0, b = 1
+  for (int i = q.segn + tid; i < kPackT * q.M; i += kPackThreads) {
+    ta[r[0].sh + i] = 0.f;
+    tb[r[1].sh + i] = 1.f;
+    tc[r[2].sh + i] = 0.f;
+    td[r[3].sh + i] = 0.0;
+  }
+}
+
 // L2 prefetch of chunk g's segment for this CTA (one thread)
 TDMA_DEV void packed_prefetch(const PackedTables& PT, const Args& A, int g, int rank) {
   const PackedChunk nx = PT.chunks[g];
@@ -557,14 +603,17 @@ TDMA_DEV void packed_prefetch(const PackedTables& PT, const Args& A, int g, int 
 // Persistent: the grid holds the clusters that fit on the GPU at once; cluster q takes chunks
 // q, q + Q, q + 2Q, ... (Q clusters, chunks sorted longest first at plan time). Warps 0..6 of a
 // CTA compute (one partition per thread), warp 7 coordinates Stage B. Unless x is written over d,
-// the next chunk's copies go out as soon as x has left shared memory, so that they overlap the
-// per-line stop rule and its two cluster barriers; the rare further corrections then read the
-// coefficients and d from global memory.
+// the next chunk's a, b and c copies go out (from the coordinator) as soon as pass 1's Stage B has
+// passed the compute warps' last read of them, and its d copies once every warp's x has left the
+// d tile, so that they overlap Stage C, the x copy-out and the per-line stop rule; the rare further
+// corrections then read the coefficients and d from global memory. With x over d, d stays in
+// shared memory until its chunk is done, and every copy of the next chunk goes out after it.
 template <int C, bool TR>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
     packed_refine_kernel(const Args A, const PackedTables PT) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ __align__(8) uint64_t xbar[2];      // exchange mbarriers, by pass parity
+  __shared__ __align__(8) uint64_t tbar;         // tile copies of a chunk
   __shared__ __align__(16) float wsl[2][8 * 8];  // warp blocks (slot 7 unused), by pass parity
   __shared__ __align__(16) float4 dsl[2][8];     // per warp: u, v, first and last unknowns
   __shared__ __align__(16) float csl[2][C * 8];  // CTA blocks of the cluster, by pass parity
@@ -575,11 +624,11 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
   const int rank = (int)cluster_rank();
   const int kp = rank * kPackT + tid;  // partition index within the chunk (compute threads)
   float* ta = reinterpret_cast<float*>(smem_raw);
-  float* tb = ta + kPackM * kPackPitch;
-  float* tc = tb + kPackM * kPackPitch;
-  double* td = reinterpret_cast<double*>(tc + kPackM * kPackPitch);
+  float* tb = ta + kPackTile;
+  float* tc = tb + kPackTile;
+  double* td = reinterpret_cast<double*>(tc + kPackTile);
   float2* td2 = reinterpret_cast<float2*>(td);
-  float2* tx = reinterpret_cast<float2*>(ta);  // (x_0, dx) pairs leave through the a and b space
+  double* tx_ab = reinterpret_cast<double*>(ta);  // with x over d, x leaves through the a and b space
   const float* fa = (const float*)A.a;
   const float* fb = (const float*)A.b;
   const float* fc = (const float*)A.c;
@@ -590,6 +639,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
   if (tid == 0) {
     mbar_init(&xbar[0], 1);
     mbar_init(&xbar[1], 1);
+    mbar_init(&tbar, 1);
     s_more = 0u;
     for (int i = 0; i < 8; ++i) wsl[i / 4][7 * 8 + (i & 3)] = 0.f;  // the empty slot 7
     mbar_fence_init();
@@ -597,39 +647,47 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
   __syncthreads();
   cluster_arrive();  // barriers initialised; the matching wait precedes the first remote store
   bool started = false, alive = true;
-  uint32_t xph[2] = {0u, 0u};
+  uint32_t xph[2] = {0u, 0u}, tph = 0u;
   uint32_t epoch = 0u;
   const int n_clusters = (int)(gridDim.x / C);
   const int g0 = (int)(blockIdx.x / C);
   if (g0 < PT.n_chunks) {
-    packed_issue_loads<C, TR>(PT, A, g0, rank, tid, ta, tb, tc, td);
+    if (tid == 0) packed_bulk<TR>(A, packed_seg(PT, g0, rank), ta, tb, tc, td, &tbar, 15, true);
     if (coord && lane == 0 && g0 + n_clusters < PT.n_chunks) packed_prefetch(PT, A, g0 + n_clusters, rank);
   }
 
   for (int g = g0; g < PT.n_chunks; g += n_clusters) {
     const PackedChunk ch = PT.chunks[g];
-    const int M = ch.M;
-    const uint32_t inv = ((1u << 20) + (uint32_t)M - 1u) / (uint32_t)M;
-    const int seg0 = rank * kPackT * M;
-    const int segn = max(0, min(ch.rows - seg0, kPackT * M));
-    const int m = coord ? 0 : max(0, min(M, segn - tid * M));
+    const PackedSeg q = packed_seg(PT, g, rank);
+    const int M = q.M;
+    const int m = coord ? 0 : max(0, min(M, q.segn - tid * M));
     const uint2 meta = coord ? make_uint2(0u, 0u) : PT.meta[(int64_t)ch.meta * (C * kPackT) + kp];
-    const uint32_t mask = meta.x & 0xFFFFFu;
+    const uint32_t mask = meta.x & ((1u << kPackRowBits) - 1u);
     const int line = ch.line0 + (int)meta.y;
     // c = 0 on rows that end a line: row t ends one when row t + 1 starts one
-    const uint32_t endmask = m > 0 ? ((mask >> 1) | (((meta.x >> 20) & 1u) << (m - 1))) : 0u;
-    const int64_t gbase = ch.base + seg0;
+    const uint32_t endmask = m > 0 ? ((mask >> 1) | (((meta.x >> kPackRowBits) & 1u) << (m - 1))) : 0u;
     const bool has_next = g + n_clusters < PT.n_chunks;
+    PackedArr r[4];
+    packed_arrs<TR>(A, q, ta, tb, tc, td, r);
 
-    cp_async_wait_all();  // this chunk's copies (issued during the previous chunk or before the loop)
+    // with x over d, this chunk's copies go out now (the previous chunk is done with the tiles)
+    if (!overlap && g != g0 && tid == 0) packed_bulk<TR>(A, q, ta, tb, tc, td, &tbar, 15, true);
+    packed_fill<TR>(A, q, ta, tb, tc, td, tid);
+    if (!mbar_wait_bounded(&tbar, tph, kPackWaitPolls) && alive) {
+      alive = false;
+      report_error(A.st, 6);
+    }
+    tph ^= 1u;
     __syncthreads();
     if (!started) {
       cluster_wait();  // every CTA of the cluster has started: remote stores may begin
       started = true;
     }
     // a = 0 where a line starts, c = 0 where one ends (each thread its own rows)
-    for (uint32_t bm = mask; bm; bm &= bm - 1u) ta[(__ffs(bm) - 1) * kPackPitch + tid] = 0.f;
-    for (uint32_t bm = endmask; bm; bm &= bm - 1u) tc[(__ffs(bm) - 1) * kPackPitch + tid] = 0.f;
+    for (uint32_t bm = mask; bm; bm &= bm - 1u) ta[r[0].sh + tid * M + (__ffs(bm) - 1)] = 0.f;
+    for (uint32_t bm = endmask; bm; bm &= bm - 1u) tc[r[2].sh + tid * M + (__ffs(bm) - 1)] = 0.f;
+    // this chunk's generic-proxy writes to the tiles come before the next chunk's copies into them
+    fence_proxy_async_smem();
     const bool edge_s = lane == 0 && kp > 0, edge_e = lane == 31 && kp + 1 < C * kPackT;
 
     if (coord) {
@@ -637,18 +695,19 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
       packed_coord_b<C>(wsl[1], dsl[1], csl[1], &xbar[1], xph[1] & 1u, rank, lane, alive, A.st);
       ++xph[0];
       ++xph[1];
-      __syncthreads();  // x staged by the compute warps
+      // pass 1's barrier 1 is behind: every compute warp has made its last read of a, b and c
+      if (overlap && has_next && lane == 0) {
+        packed_bulk<TR>(A, packed_seg(PT, g + n_clusters, rank), ta, tb, tc, td, &tbar, 7, false);
+        if (g + 2 * n_clusters < PT.n_chunks) packed_prefetch(PT, A, g + 2 * n_clusters, rank);
+      }
     } else {
-      const float* ra = ta + tid;
-      const float* rb = tb + tid;
-      const float* rc = tc + tid;
-      const double* rd = td + tid;
-      float2* rd2 = td2 + tid;
+      const int o = tid * M;
+      double* rx = overlap ? td + r[3].sh + o : tx_ab + o;
       switch (M) {
-#define TDMA_PASSES(MM)                                                                             \
-  case MM:                                                                                           \
-    packed_passes<MM>(ra, rb, rc, rd, rd2, tx + tid, wsl[0], dsl[0], wsl[1], dsl[1], w, lane, edge_s, edge_e, \
-                      mask, line, PT.norms, keep);                                                   \
+#define TDMA_PASSES(MM)                                                                                      \
+  case MM:                                                                                                    \
+    packed_passes<MM>(ta + r[0].sh + o, tb + r[1].sh + o, tc + r[2].sh + o, td + r[3].sh + o, td2 + r[3].sh + o, \
+                      rx, wsl[0], dsl[0], wsl[1], dsl[1], w, lane, edge_s, edge_e, mask, line, PT.norms, keep);  \
     break;
         TDMA_PACKED_M(TDMA_PASSES)
 #undef TDMA_PASSES
@@ -659,47 +718,39 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
           packed_compute_b(Blk{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, wsl[1], dsl[1], w, lane, du, dv);
         }
       }
-      __syncthreads();
+      fence_proxy_async_smem();  // the d pairs and x come before the next chunk's copies
+      // x in FP64: the warp's own 32 M rows, contiguous in memory, coalesced
+      __syncwarp();
+      const double* xs = overlap ? td + r[3].sh : tx_ab;
+      const int w0 = w * 32 * M, w1 = min(w0 + 32 * M, q.segn);
+      for (int i = w0 + lane; i < w1; i += 32) gx[q.gbase + i] = xs[i];
     }
-    // The line maxima of every CTA are in: arrive on the cluster barrier now and wait only after
-    // x has gone out and the next chunk's copies are on their way.
+    __syncthreads();  // every warp's x has left the d tile; the line maxima of this CTA are in
+    // arrive on the cluster barrier now and wait only after the next chunk's d copies are out
     ++epoch;
     cluster_arrive();
-    // x = x_0 + dx in FP64 (exact widenings, one FP64 add), coalesced out of shared memory, by
-    // every warp of the CTA
-    for (int i = tid; i < segn; i += kPackThreads) {
-      int k, t;
-      seg_row(i, M, inv, k, t);
-      const float2 v = tx[t * kPackPitch + k];
-      gx[gbase + i] = f2d_fast(v.x) + f2d_fast(v.y);
-    }
-    if (overlap) {
-      __syncthreads();  // the pairs have left shared memory: the next chunk may come in
-      if (has_next) {
-        packed_issue_loads<C, TR>(PT, A, g + n_clusters, rank, tid, ta, tb, tc, td);
-        if (coord && lane == 0 && g + 2 * n_clusters < PT.n_chunks) packed_prefetch(PT, A, g + 2 * n_clusters, rank);
-      }
-    }
+    if (overlap && has_next && tid == 0)
+      packed_bulk<TR>(A, packed_seg(PT, g + n_clusters, rank), ta, tb, tc, td, &tbar, 8, true);
     cluster_wait();  // the atomics of every CTA are complete and visible
     // ---------------- stop rule per line: every CTA evaluates all lines of the chunk
     bool again = __syncthreads_or(packed_first_verdict(ch, PT.norms, A.tol, A.max_iters <= 1, rank == 0, A.st)) != 0;
     int it = 1;
 
     // ---------------- further corrections (rare): coefficients and x from global memory
-    if (again && it < A.max_iters) {  // x of every CTA went out after its first arrival: wait for it
+    if (again && it < A.max_iters) {  // x of every CTA went out before its first arrival: wait for it
       cluster_arrive();
       cluster_wait();
     }
     while (again && it < A.max_iters) {
       ++it;
-      const int q = it & 1;
+      const int qp = it & 1;
       if (coord) {
-        packed_coord_b<C>(wsl[q], dsl[q], csl[q], &xbar[q], xph[q] & 1u, rank, lane, alive, A.st);
-        ++xph[q];
+        packed_coord_b<C>(wsl[qp], dsl[qp], csl[qp], &xbar[qp], xph[qp] & 1u, rank, lane, alive, A.st);
+        ++xph[qp];
         __syncthreads();
       } else {
-        packed_later_pass<TR>(PT, fa, fb, fc, gd, overlap ? nullptr : td2 + tid, wsl[q], dsl[q], gx,
-                              gbase + (int64_t)tid * M, w, lane, kp, m, mask, endmask, line, seg0 + tid * M,
+        packed_later_pass<TR>(PT, fa, fb, fc, gd, overlap ? nullptr : td2 + r[3].sh + tid * M, wsl[qp], dsl[qp],
+                              gx, q.gbase + (int64_t)tid * M, w, lane, kp, m, mask, endmask, line, q.seg0 + tid * M,
                               ch.rows);
         __syncthreads();
       }
@@ -714,10 +765,6 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
       again = s_more == epoch;
     }
     if (rank == 0 && tid == 0) report_iters(A.st, it);
-    if (!overlap && has_next) {  // every use of this chunk's shared memory is over (cluster barriers)
-      packed_issue_loads<C, TR>(PT, A, g + n_clusters, rank, tid, ta, tb, tc, td);
-      if (coord && lane == 0 && g + 2 * n_clusters < PT.n_chunks) packed_prefetch(PT, A, g + 2 * n_clusters, rank);
-    }
   }
   if (!started) cluster_wait();  // a cluster without a chunk still completes the start-up barrier
 }

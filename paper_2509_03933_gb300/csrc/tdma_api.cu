@@ -895,7 +895,7 @@ bool build_packed_tables(tdma_plan_s* p, const std::vector<int64_t>& off, const 
   std::vector<int32_t> starts, key;
   for (size_t g = 0; g < spans.size(); ++g) {
     const Span& sp = spans[g];
-    // rows per partition: the smallest compiled M with 896 M >= rows (identity rows fill the rest)
+    // rows per partition: the smallest compiled (odd) M with 896 M >= rows (identity rows fill the rest)
     const int rows = (int)sp.rows, need = (rows + PPC - 1) / PPC;
     int M = 0;
 #define TDMA_PICK_M(MM) if (M == 0 && MM >= need) M = MM;
@@ -925,7 +925,7 @@ bool build_packed_tables(tdma_plan_s* p, const std::vector<int64_t>& off, const 
         for (size_t q = li; q < starts.size() && starts[q] < r1; ++q)
           if (starts[q] >= r0) w |= 1u << (starts[q] - r0);
         const bool ends = r1 >= rows || std::binary_search(starts.begin(), starts.end(), r1);
-        if (ends) w |= 1u << 20;
+        if (ends) w |= 1u << kPackRowBits;
       } else {
         li = starts.size() - 1;
       }
@@ -945,7 +945,7 @@ bool build_packed_tables(tdma_plan_s* p, const std::vector<int64_t>& off, const 
     cudaFree(mem);
     return false;
   }
-  const size_t sm = (size_t)kPackM * kPackPitch * (3 * sizeof(float) + sizeof(double));
+  const size_t sm = (size_t)kPackTile * (3 * sizeof(float) + sizeof(double));
   if (set_smem(packed_refine_kernel<kPackC, false>, sm) != cudaSuccess ||
       set_smem(packed_refine_kernel<kPackC, true>, sm) != cudaSuccess) {
     cudaFree(mem);

@@ -64,6 +64,14 @@ TDMA_DEV void tma_store_3d(const CUtensorMap* map, const void* src, int c0, int 
                "r"(smem_u32(src)), "r"(c0), "r"(c1), "r"(c2)
                : "memory");
 }
+// 1D bulk copy of `bytes` (a multiple of 16) from global to shared memory, both addresses 16-byte
+// aligned, completion counted on `bar` (bytes).
+TDMA_DEV void bulk_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
 // Prefetch a 4D tile into L2 (no shared-memory destination, no completion to wait for).
 TDMA_DEV void tma_prefetch_4d(const CUtensorMap* map, int c0, int c1, int c2, int c3) {
   asm volatile("cp.async.bulk.prefetch.tensor.4d.L2.global.tile [%0, {%1, %2, %3, %4}];" ::"l"(

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 PACKED = 9        # TDMA_VARIANT_PACKED
 RAGGED = 3        # TDMA_VARIANT_RAGGED
-CHUNK_ROWS = 17920  # longest line the chunk kernel takes (4 CTAs x 224 partitions x 20 rows)
+CHUNK_ROWS = 18816  # longest line the chunk kernel takes (4 CTAs x 224 partitions x 21 rows)
 
 
 def _oracle(a, b, c, d, offs, lens, lines=None, dtype=np.float64):
@@ -150,6 +150,30 @@ def test_packed_second_correction_for_weakly_dominant_lines():
     assert st == 0
     assert iters >= 2
     assert _err(x, _oracle(a, b, c, dn, o, n, dtype=np.longdouble), o, n) <= 1e-12
+
+
+def test_packed_stop_rule_run_out_and_nonfinite_values():
+    # Chunks whose lines fail the local stop test go to the rule on the line maxima after the last
+    # chunk: an unreachable tolerance runs max_refine_iters corrections and reports
+    # TDMA_ERR_NOT_CONVERGED (7), with x still as good as the corrections make it; a NaN in d
+    # reports TDMA_ERR_NONFINITE (5); the plan's next launch, on clean data, reports 0 again.
+    lengths = synth.ragged_lengths(300, 16, 16384, seed=9)
+    a, b, c, d, offs, lens = _problem(lengths, 21)
+    o, n = offs.cpu().numpy(), lens.cpu().numpy()
+    ref = _oracle(a, b, c, d, o, n)
+    x, plan = _solve(a, b, c, d, offs, lens, check=False, max_refine_iters=3, refine_tol=1e-30)
+    assert plan.config["variant"] == PACKED
+    assert plan.last_error() == (7, 3)
+    assert _err(x, ref, o, n) <= 1e-12
+    x, plan = _solve(a, b, c, d, offs, lens, check=False, max_refine_iters=1, refine_tol=1e-30)
+    assert plan.last_error() == (7, 1)
+    bad = d.clone()
+    bad[int(o[5]) + int(n[5]) // 2] = float("nan")
+    x, plan = _solve(a, b, c, bad, offs, lens, check=False)
+    assert plan.last_error()[0] == 5
+    x, _ = _solve(a, b, c, d, offs, lens, check=False, plan=plan)
+    assert plan.last_error()[0] == 0
+    assert _err(x, ref, o, n) <= 1e-12
 
 
 def test_packed_agrees_with_group_kernel():
