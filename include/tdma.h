@@ -160,7 +160,10 @@ tdma_status_t tdma_plan_create(tdma_plan_t* plan, const tdma_desc_t* desc, size_
 tdma_status_t tdma_plan_destroy(tdma_plan_t plan);
 
 /* Solve A x = d for every line (forward pass). x may alias d. Enqueues kernels on `stream`
- * and returns without waiting; allocates nothing. */
+ * and returns without waiting; allocates nothing. Arrays must be aligned to their element size
+ * (both values of a pair with nrhs = 2); the cluster variants (TDMA_VARIANT_REFINE_CLUSTER,
+ * _REFINE_TREE, _REFINE_TREE_X) move tiles by TMA and need every array 16-byte aligned.
+ * Otherwise TDMA_ERR_UNSUPPORTED, before anything is enqueued. */
 tdma_status_t tdma_solve(tdma_plan_t plan, const void* a, const void* b, const void* c,
                          const void* d, void* x, void* workspace, size_t workspace_bytes,
                          void* stream);

@@ -1369,6 +1369,11 @@ static tdma_status_t check_ptrs(const tdma_plan_s* p, const void* a, const void*
   if (!aligned(a, ce) || !aligned(b, ce) || !aligned(c, ce)) return TDMA_ERR_UNSUPPORTED;
   if (!aligned(d, de) || !aligned(x, de)) return TDMA_ERR_UNSUPPORTED;
   if (p->desc.diag_shift && !aligned(p->desc.diag_shift, ce)) return TDMA_ERR_UNSUPPORTED;
+  // the cluster kernels move their tiles by TMA: every array 16-byte aligned
+  const int v = p->cfg.variant;
+  if ((v == TDMA_VARIANT_REFINE_TREE || v == TDMA_VARIANT_REFINE_TREE_X || v == TDMA_VARIANT_REFINE_CLUSTER) &&
+      !(aligned(a, 16) && aligned(b, 16) && aligned(c, 16) && aligned(d, 16) && aligned(x, 16)))
+    return TDMA_ERR_UNSUPPORTED;
   return TDMA_OK;
 }
 

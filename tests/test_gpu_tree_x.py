@@ -104,3 +104,25 @@ def test_more_corrections_not_converged_and_in_place():
     st, iters = stiff.last_error()
     assert st == 7 and iters == 3
     assert rel_err(_lines(x), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_cluster_variants_refuse_arrays_off_16_bytes(axis):
+    # the tiles travel by TMA: an array one element off a 16-byte boundary is refused before
+    # anything runs (TDMA_ERR_UNSUPPORTED); the aligned solve still works afterwards
+    n, L = 256, 64
+    shape = (n, L) if axis == 0 else (L, n)
+    g = synth.grid_general(shape, axis, 71, device="cuda", fp32_coefficients=True)
+    a, b, c, d = g["a32"], g["b32"], g["c32"], g["d"]
+    plan = tdma.Plan(*tdma.line_layout(d, axis), precision="f32r")
+    assert plan.config["variant"] == (8 if axis == 0 else TREE_X)
+    big = torch.empty(d.numel() + 1, dtype=torch.float64, device="cuda")
+    xs = big[1:].view(shape)  # 8 bytes past a 16-byte boundary
+    with pytest.raises(tdma.TDMAError) as e:
+        plan.solve(a, b, c, d, xs)
+    assert e.value.status == 2
+    x = torch.empty_like(d)
+    plan.solve(a, b, c, d, x)
+    assert plan.last_error()[0] == 0
+    ref = O.thomas(*(_lines(t if axis == 1 else t.T) for t in (a, b, c, d)))
+    assert rel_err(_lines(x if axis == 1 else x.T), ref) <= 1e-12
