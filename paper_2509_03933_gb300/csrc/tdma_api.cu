@@ -19,6 +19,7 @@
 #include "kernels_refine_cluster.cuh"
 #include "kernels_refine_tree.cuh"
 #include "kernels_thomas.cuh"
+#include "kernels_thomas_short.cuh"
 #include "kernels_ragged.cuh"
 #include "kernels_packed.cuh"
 #include "kernels_shared.cuh"
@@ -426,6 +427,28 @@ template <class K> cudaError_t set_smem(K kernel, size_t bytes) {
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// The staged Thomas kernel for short lines: its shared-memory limit, and its launch (one warp per
+// 32 lines).
+template <class CT, int NR> size_t short_smem(const tdma_desc_t& d) { return thomas_short_smem(d.n, NR, sizeof(CT)); }
+cudaError_t prepare_thomas_short(const tdma_desc_t& d) {
+  if (d.precision == TDMA_F64)
+    return d.nrhs == 1 ? set_smem(thomas_short_kernel<double, 1>, short_smem<double, 1>(d))
+                       : set_smem(thomas_short_kernel<double, 2>, short_smem<double, 2>(d));
+  return d.nrhs == 1 ? set_smem(thomas_short_kernel<float, 1>, short_smem<float, 1>(d))
+                     : set_smem(thomas_short_kernel<float, 2>, short_smem<float, 2>(d));
+}
+cudaError_t launch_thomas_short(const tdma_desc_t& d, const Args& A, cudaStream_t s) {
+  const dim3 grid((unsigned)((d.n_lines + 31) / 32)), block(32);
+  if (d.precision == TDMA_F64) {
+    if (d.nrhs == 1) thomas_short_kernel<double, 1><<<grid, block, short_smem<double, 1>(d), s>>>(A);
+    else thomas_short_kernel<double, 2><<<grid, block, short_smem<double, 2>(d), s>>>(A);
+  } else {
+    if (d.nrhs == 1) thomas_short_kernel<float, 1><<<grid, block, short_smem<float, 1>(d), s>>>(A);
+    else thomas_short_kernel<float, 2><<<grid, block, short_smem<float, 2>(d), s>>>(A);
+  }
+  return cudaGetLastError();
+}
+
 // Clusters of the merge-tree kernel that fit on the current device at once (0 if unknown).
 int64_t tree_resident_clusters(int M, int C, bool xl, size_t smem) {
   static std::mutex mu;
@@ -571,6 +594,7 @@ cudaError_t launch_forward(const tdma_plan_s* p, const Args& A, cudaStream_t s) 
     }
     case TDMA_VARIANT_THOMAS:
       if (A.lay.es == 1) return launch_thomas_staged(p->desc.precision, p->desc.nrhs, A, s);  // contiguous lines
+      if (thomas_short_ok(p->desc)) return launch_thomas_short(p->desc, A, s);  // short lines, small batch
       return launch_thomas(p->desc.precision, p->desc.nrhs, A, c, s);
     case TDMA_VARIANT_SHARED:
       return launch_shared_any(p->desc.precision, p->desc.nrhs, false, A, s);
@@ -645,6 +669,7 @@ cudaError_t prepare_kernel(const tdma_plan_s* p) {
     }
     case TDMA_VARIANT_THOMAS:
       if (p->desc.elem_stride == 1) return prepare_thomas_staged(p->desc.precision, p->desc.nrhs);
+      if (thomas_short_ok(p->desc)) return prepare_thomas_short(p->desc);
       return prepare_thomas(p->desc.precision, p->desc.nrhs, sm);
     case TDMA_VARIANT_SHARED:
       return prepare_shared(p->desc.precision, p->desc.nrhs);
