@@ -94,6 +94,16 @@ bool choose_block(const tdma_desc_t& d, int P, tdma_config_t& c) {
     c.variant = TDMA_VARIANT_DC_GLOBAL;
     return true;
   }
+  // a batch too small to give every SM four blocks: smaller blocks (whole warps) spread it over
+  // more SMs and more of their FP64 pipes (a warp-wide FP64 instruction holds one SM
+  // sub-partition's pipe for about 64 cycles)
+  int sms = 0, dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    sms = 0;
+  (void)cudaGetLastError();
+  while (sms > 0 && Lb % 2 == 0 && (Lb / 2) * P >= 32 && ((Lb / 2) * P) % 32 == 0 &&
+         (d.n_lines + Lb - 1) / Lb < 4 * (int64_t)sms)
+    Lb /= 2;
   const int T = Lb * P;
   if (T > 512) return false;
   const size_t smem = dc_bytes(d, T, Lb, P, mmax);
