@@ -25,7 +25,13 @@
 // Refinement (the FP32 + refinement path): pass 0 solves with the float part of d; pass 1
 // recomputes the same factors and solves for the extra-precise residual r = d - A x_0 (float
 // pairs); x = x_0 + dx goes to global memory in FP64. The stop rule (per line, on the line's
-// max norms) needs one more exchange; later passes, rare, re-read x from global memory.
+// max norms) compares the line's max |dx| with a bound made of its max |x_0|, which the pass-1
+// exchange already brings to every CTA: so each CTA takes the rule on its own rows, and the line
+// meets it exactly when every CTA's rows do. Out of place, the per-line flags of a group travel
+// with the next group's pass-0 exchange (the cluster's last group has one exchange of its own),
+// and a group that needs further corrections (rare) gets them then, from global memory; in place
+// (x is d) the rule takes one exchange of the line maxima and the corrections follow at once.
+// Later passes re-read x from global memory.
 // Exchanges are point to point (st.async into the other CTAs' shared memory, completing on
 // their mbarriers): a CTA waits only for the data it needs, never for another CTA's threads.
 #pragma once
@@ -80,10 +86,12 @@ __host__ __device__ constexpr size_t refine_tree_smem_bytes() {
 // this CTA's first and last unknowns of the line as the neighbouring CTAs see them (every CTA
 // computes the cluster tree from the same data in the same order, so the values agree bit for
 // bit).
-template <int C>
+// `extra2` (with F2) rides in the slot's last word the same way: its maximum over the cluster comes
+// back in extra2_max.
+template <int C, bool F2 = false>
 TDMA_DEV void tree_stage_b(const Blk& b, unsigned extra, float* slots, uint64_t* bar, uint32_t phase, int rank, int p,
                            int jj, int j, float& u, float& v, float& xs_c, float& xe_c, unsigned& extra_max,
-                           bool& alive, DevStatus* st) {
+                           bool& alive, DevStatus* st, unsigned extra2 = 0u, unsigned* extra2_max = nullptr) {
   constexpr int LC = C == 8 ? 3 : (C == 4 ? 2 : 1);
   Aff kc[3];
   const Blk B = tree_up<3>(b, p, kc);
@@ -91,12 +99,13 @@ TDMA_DEV void tree_stage_b(const Blk& b, unsigned extra, float* slots, uint64_t*
   if (p < C) {
     const uint32_t dst = map_rank(slots + rank * kTreeSlotPitch + j * 8, p), rb = map_rank(bar, p);
     st_async4(dst, B.p1, B.q1, B.r1, B.p2, rb);
-    st_async4(dst + 16, B.q2, B.r2, __uint_as_float(extra), 0.f, rb);
+    st_async4(dst + 16, B.q2, B.r2, __uint_as_float(extra), __uint_as_float(extra2), rb);
   }
   tree_wait(bar, phase, alive, st);
   const float4* s = reinterpret_cast<const float4*>(slots + (p & (C - 1)) * kTreeSlotPitch + j * 8);
   const float4 s0 = s[0], s1 = s[1];
   extra_max = line_max(__float_as_uint(s1.z));
+  if constexpr (F2) *extra2_max = line_max(__float_as_uint(s1.w));
   float uq = 0.f, vq = 0.f, xsq = 0.f, xeq = 0.f;
   {
     Mrg kq[3];
@@ -337,6 +346,141 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
   cluster_arrive();
   bool started = false, alive = true;
   uint32_t tph0 = 0, tph1 = 0, xph0 = 0, xph1 = 0, xph2 = 0, xph3 = 0;  // phases of bar[0..1], xbar[0..3]
+  // Out of place, the stop rule of a group is settled one group later (see below): this thread's
+  // line of the cluster's previous group pg failed the rule on this CTA's rows (pf_line), that
+  // group's certificate and this CTA's max |dx| of the line, and the line's flag over the cluster
+  // once the next pass-0 exchange has brought it (pfl).
+  bool pf_line = false, pcert = false;
+  unsigned pndx = 0u, pfl = 0u;
+  int64_t pg = -1;
+
+  // Further corrections of group gg (rare): a fresh float solve of the residual per pass, operands
+  // from global memory (out of place the tiles hold another group's rows by then); in place, a and
+  // b reloaded into their tiles (which held the outgoing x) and c and the d pairs from the tiles.
+  // Every CTA of the cluster runs the same passes (the decision is the cluster's). prevd is the
+  // line's previous max |dx| (the ratio of the rule). Reports the corrections made and, for a line
+  // still short of the rule after max_iters, TDMA_ERR_NOT_CONVERGED.
+  auto later = [&](int64_t gg, bool cert, unsigned prevd, bool line_done, bool all_done) {
+    const int64_t l0 = gg * kTreeLines;
+    const bool act = l0 + j < A.lay.n_lines;
+    const bool rep = rank == 0 && p == 0 && act;
+    const int64_t eo = A.lay.off(act ? l0 + j : 0) + (int64_t)kg * M * es;
+    double* pxg = (double*)A.x + eo;
+    const int ci = (int)(l0 % ic), co = (int)(l0 / ic), cp = rank * kTreeParts;
+    const float* ga = (const float*)A.a + eo;
+    const float* gb = (const float*)A.b + eo;
+    const float* gc = (const float*)A.c + eo;
+    const double* gd = (const double*)A.d + eo;
+    int it = 1;
+    while (!all_done && it < A.max_iters) {
+      ++it;
+      if (tid == 0 && (XL || inplace)) {
+        bulk_wait_all();  // x of the last pass is in global memory
+        fence_proxy_async_global();
+      }
+      if (inplace) {
+        if (tid == 0) {
+          mbar_arrive_expect_tx(&bar[0], 2u * M * 1024u);  // a and b again (x went through their tiles)
+          if constexpr (XL) {
+#pragma unroll
+            for (int i = 0; i < M / 4; ++i) {
+              tma_load_3d(ta + i * 1024, &maps.a, &bar[0], cp * M + 32 * i, ci, co);
+              tma_load_3d(tb + i * 1024, &maps.b, &bar[0], cp * M + 32 * i, ci, co);
+            }
+          } else {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              tma_load_4d(ta + h * H * 256, &maps.a, &bar[0], ci, co, cp, h * H);
+              tma_load_4d(tb + h * H * 256, &maps.b, &bar[0], ci, co, cp, h * H);
+            }
+          }
+        }
+        if (!mbar_wait_bounded(&bar[0], tph0, kTmaWaitPolls) && alive) {
+          alive = false;
+          report_error(A.st, 6);
+        }
+        tph0 ^= 1u;
+      }
+      cluster_arrive();  // x of the previous pass, written by every CTA, visible to all
+      cluster_wait();
+      Sweep<M> S;
+      ff xm{0.f, 0.f}, xc{0.f, 0.f}, xe{0.f, 0.f};
+      if (act) {
+        if (!first_part) xm = split_f64(pxg[-es]);
+        if (!last_part) xe = split_f64(pxg[M * es]);
+        xc = split_f64(pxg[0]);
+      }
+#pragma unroll
+      for (int t = 0; t < M; ++t) {
+        float a = 0.f, b = 1.f, c = 0.f;
+        ff dd{0.f, 0.f};
+        if (inplace) {
+          a = ta[fidx(t)];
+          b = tb[fidx(t)];
+          c = tc[fidx(t)];
+          const float2 dp = td2[didx(t)];
+          dd = ff{dp.x, dp.y};
+        } else if (act) {
+          a = ga[t * es];
+          b = gb[t * es];
+          c = gc[t * es];
+          dd = split_f64(gd[t * es]);
+        }
+        if (t == 0 && first_part) a = 0.f;
+        if (t == M - 1 && last_part) c = 0.f;
+        const ff xn = t == M - 1 ? xe : (act ? split_f64(pxg[(t + 1) * es]) : ff{0.f, 0.f});
+        S.row(t, a, b, c, residual_ff(a, b, c, dd, xm, xc, xn));
+        xm = xc;
+        xc = xn;
+      }
+      const Blk blk = S.block();
+      float u, v, xs_c, xe_c;
+      unsigned unused;
+      // pass `it` uses the buffers of its parity; the phase counters follow each mbarrier
+      const int q = it & 1;
+      tree_stage_b<C>(blk, 0u, slots + q * C * kTreeSlotPitch, &xbar[q], (q ? xph1 : xph0) & 1u, rank, p, jj, j, u, v,
+                      xs_c, xe_c, unused, alive, A.st);
+      if (q) ++xph1; else ++xph0;
+      float dx[M];
+      S.solve(Sweep<M>::first(blk, u, v), Sweep<M>::last(blk, u, v), dx);
+      unsigned ndx = 0u, nxm = 0u;
+      if (act) {
+#pragma unroll
+        for (int t = 0; t < M; ++t) {
+          const double xn = pxg[t * es] + f2d(dx[t]);
+          pxg[t * es] = xn;
+          ndx = max(ndx, abs_bits(dx[t]));
+          nxm = max(nxm, abs_bits(__double2float_rn(xn)));
+        }
+      }
+      unsigned* nb = norms + q * C * kTreeNormPitch;
+      unsigned gdx, gxm;
+      tree_norms_push<C>(line_max(ndx), line_max(nxm), nb, &xbar[2 + q], rank, p, j);
+      tree_norms_read<C>(gdx, gxm, nb, &xbar[2 + q], (q ? xph3 : xph2) & 1u, p, j, alive, A.st);
+      if (q) ++xph3; else ++xph2;
+      line_done = tree_line_done(gdx, gxm, prevd, act, A.tol, cert, rep, A.st);
+      all_done = __syncthreads_and(line_done) != 0;
+    }
+    if (rep) {
+      report_iters(A.st, it);
+      if (!line_done) report_error(A.st, 7);
+    }
+  };
+  // Out of place: the previous group pg failed the rule on some line (pflag: this thread's line's
+  // flag over the cluster). Every CTA of the cluster comes here at the same point.
+  auto settle = [&](unsigned pflag) {
+    cluster_arrive();  // every CTA is past its reads of the norm slots
+    cluster_wait();
+    if (A.max_iters <= 1) {
+      if (rank == 0 && p == 0 && pflag != 0u) report_error(A.st, 7);
+      return;
+    }
+    unsigned gdx1, unused;  // the line's max |dx| of pass 1 of group pg
+    tree_norms_push<C>(pndx, 0u, norms + C * kTreeNormPitch, &xbar[3], rank, p, j);
+    tree_norms_read<C>(gdx1, unused, norms + C * kTreeNormPitch, &xbar[3], xph3 & 1u, p, j, alive, A.st);
+    ++xph3;
+    later(pg, pcert, gdx1, pflag == 0u, false);
+  };
 
   for (int64_t g = blockIdx.x / C; g < n_groups; g += n_clusters) {
     const int64_t line0 = g * kTreeLines;
@@ -421,7 +565,9 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
       const unsigned unc = line_max(__float_as_uint(fmaxf(dom, 0.f)));
       unsigned unc_line;
       float xs_c, xe_c;
-      tree_stage_b<C>(blk, unc, slots, &xbar[0], xph0 & 1u, rank, p, jj, j, u0, v0, xs_c, xe_c, unc_line, alive, A.st);
+      // the flags of the previous group's lines ride along (out of place)
+      tree_stage_b<C, true>(blk, unc, slots, &xbar[0], xph0 & 1u, rank, p, jj, j, u0, v0, xs_c, xe_c, unc_line, alive,
+                            A.st, pf_line ? 1u : 0u, &pfl);
       ++xph0;
       certified = unc_line == 0u;
       // Boundary unknowns exactly as the neighbours will see them in the residual: at a CTA edge
@@ -438,11 +584,11 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
       for (int t = 0; t < M; ++t) nx = max(nx, abs_bits(x0[t]));
       nx = line_max(nx);  // this CTA's rows of the line
     }
-    // at least one correction always runs (the host passes max_iters >= 1): every tile makes the
-    // same three exchanges, so no CTA can send into a buffer another CTA is still reading
+    // at least one correction always runs (the host passes max_iters >= 1)
     {
       // ---------------- pass 1: correction for r = d - A x_0, x = x_0 + dx
-      unsigned prev, gdx, gxm;
+      unsigned prev, gdx = 0u, gxm = 0u, ndx_l;
+      bool fixup = false;  // out of place: some line of the cluster's previous group failed the rule
       {
         auto row1 = [&](int t, float a, float b, float c, float dh, float dl) {
           if (t == 0 && first_part) a = 0.f;
@@ -480,10 +626,11 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
         // Every thread has finished its pass-1 sweep, the last read of the a, b and c tiles (and,
         // unless x goes through it, of the d tile): the next group's rows may come in. The d pairs
         // written in place by pass 0 are ordered before the copies' writes by each writer's proxy
-        // fence.
+        // fence. The same barrier gathers the previous group's verdict: every CTA of the cluster
+        // holds the same per-line flags (from this group's pass-0 exchange), so all agree.
         if (!inplace) {
           fence_proxy_async_smem();
-          __syncthreads();
+          fixup = __syncthreads_or(pfl != 0u) != 0;
           if (tid == 0 && g + n_clusters < n_groups) {
             const int64_t l1 = (g + n_clusters) * kTreeLines;
             tree_load_tiles<M, XL>(maps, ta, tb, tc, td, bar, (int)(l1 % ic), (int)(l1 / ic), c_p, XL ? 1 : 3, !XL);
@@ -494,7 +641,8 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
         unsigned ndx = 0u;
 #pragma unroll
         for (int t = 0; t < M; ++t) ndx = max(ndx, abs_bits(dx[t]));
-        tree_norms_push<C>(line_max(ndx), nx, norms + C * kTreeNormPitch, &xbar[3], rank, p, j);
+        ndx_l = line_max(ndx);  // this CTA's rows of the line
+        if (inplace) tree_norms_push<C>(ndx_l, nx, norms + C * kTreeNormPitch, &xbar[3], rank, p, j);
         // x = x_0 + dx (exact widenings, one FP64 add): straight to global memory (for a fixed
         // row the four lines of a lane quad are 32 contiguous bytes), or by TMA store through the
         // thread's own d slots (XL) or, in place, through the a and b tiles (every thread's pass-1
@@ -528,118 +676,45 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
             bulk_commit();
           }
         }
-        tree_norms_read<C>(gdx, gxm, norms + C * kTreeNormPitch, &xbar[3], xph3 & 1u, p, j, alive, A.st);
-        ++xph3;
-      }
-      bool line_done = tree_line_done(gdx, gxm, prev, active, A.tol, certified, reporter, A.st);
-      bool all_done = __syncthreads_and(line_done) != 0;
-
-      // ---------------- later corrections (rare): operands from global memory (the tiles hold the
-      // next group's rows); in place, a and b reloaded into their tiles (which held the outgoing x)
-      // and c and the d pairs from the tiles
-      int it = 1;
-      const float* ga = (const float*)A.a + eoff;
-      const float* gb = (const float*)A.b + eoff;
-      const float* gc = (const float*)A.c + eoff;
-      const double* gd = (const double*)A.d + eoff;
-      while (!all_done && it < A.max_iters) {
-        ++it;
-        if (tid == 0 && (XL || inplace)) {
-          bulk_wait_all();  // x of pass 1 is in global memory
-          fence_proxy_async_global();
-        }
         if (inplace) {
-          if (tid == 0) {
-            mbar_arrive_expect_tx(&bar[0], 2u * M * 1024u);  // a and b again (x went through their tiles)
-            if constexpr (XL) {
-#pragma unroll
-              for (int i = 0; i < M / 4; ++i) {
-                tma_load_3d(ta + i * 1024, &maps.a, &bar[0], c_p * M + 32 * i, c_in, c_out);
-                tma_load_3d(tb + i * 1024, &maps.b, &bar[0], c_p * M + 32 * i, c_in, c_out);
-              }
-            } else {
-#pragma unroll
-              for (int h = 0; h < 2; ++h) {
-                tma_load_4d(ta + h * H * 256, &maps.a, &bar[0], c_in, c_out, c_p, h * H);
-                tma_load_4d(tb + h * H * 256, &maps.b, &bar[0], c_in, c_out, c_p, h * H);
-              }
-            }
-          }
-          if (!mbar_wait_bounded(&bar[0], tph0, kTmaWaitPolls) && alive) {
-            alive = false;
-            report_error(A.st, 6);
-          }
-          tph0 ^= 1u;
+          tree_norms_read<C>(gdx, gxm, norms + C * kTreeNormPitch, &xbar[3], xph3 & 1u, p, j, alive, A.st);
+          ++xph3;
         }
-        cluster_arrive();  // x of the previous pass, written by every CTA, visible to all
-        cluster_wait();
-        Sweep<M> S;  // a fresh solve (the first pass's factors are not kept past pass 1)
-        ff xm{0.f, 0.f}, xc{0.f, 0.f}, xe{0.f, 0.f};
-        if (active) {
-          if (!first_part) xm = split_f64(px[-es]);
-          if (!last_part) xe = split_f64(px[M * es]);
-          xc = split_f64(px[0]);
-        }
-#pragma unroll
-        for (int t = 0; t < M; ++t) {
-          float a = 0.f, b = 1.f, c = 0.f;
-          ff dd{0.f, 0.f};
-          if (inplace) {
-            a = ta[fidx(t)];
-            b = tb[fidx(t)];
-            c = tc[fidx(t)];
-            const float2 dp = td2[didx(t)];
-            dd = ff{dp.x, dp.y};
-          } else if (active) {
-            a = ga[t * es];
-            b = gb[t * es];
-            c = gc[t * es];
-            dd = split_f64(gd[t * es]);
-          }
-          if (t == 0 && first_part) a = 0.f;
-          if (t == M - 1 && last_part) c = 0.f;
-          const ff xn = t == M - 1 ? xe : (active ? split_f64(px[(t + 1) * es]) : ff{0.f, 0.f});
-          S.row(t, a, b, c, residual_ff(a, b, c, dd, xm, xc, xn));
-          xm = xc;
-          xc = xn;
-        }
-        const Blk blk = S.block();
-        float u, v, xs_c, xe_c;
-        unsigned unused;
-        // pass `it` uses the buffers of its parity; the phase counters follow each mbarrier
-        const int q = it & 1;
-        tree_stage_b<C>(blk, 0u, slots + q * C * kTreeSlotPitch, &xbar[q], (q ? xph1 : xph0) & 1u, rank, p, jj, j, u,
-                        v, xs_c, xe_c, unused, alive, A.st);
-        if (q) ++xph1; else ++xph0;
-        float dx[M];
-        S.solve(Sweep<M>::first(blk, u, v), Sweep<M>::last(blk, u, v), dx);
-        unsigned ndx = 0u, nxm = 0u;
-        if (active) {
-#pragma unroll
-          for (int t = 0; t < M; ++t) {
-            const double xn = px[t * es] + f2d(dx[t]);
-            px[t * es] = xn;
-            ndx = max(ndx, abs_bits(dx[t]));
-            nxm = max(nxm, abs_bits(__double2float_rn(xn)));
-          }
-        }
-        unsigned* nb = norms + q * C * kTreeNormPitch;
-        tree_norms_push<C>(line_max(ndx), line_max(nxm), nb, &xbar[2 + q], rank, p, j);
-        tree_norms_read<C>(gdx, gxm, nb, &xbar[2 + q], (q ? xph3 : xph2) & 1u, p, j, alive, A.st);
-        if (q) ++xph3; else ++xph2;
-        line_done = tree_line_done(gdx, gxm, prev, active, A.tol, certified, reporter, A.st);
-        all_done = __syncthreads_and(line_done) != 0;
       }
-      if (reporter) {
-        report_iters(A.st, it);
-        if (!line_done) report_error(A.st, 7);
+      if (inplace) {  // the rule on the line maxima now, and this group's further corrections
+        bool line_done = tree_line_done(gdx, gxm, prev, active, A.tol, certified, reporter, A.st);
+        const bool all_done = __syncthreads_and(line_done) != 0;
+        later(g, certified, prev, line_done, all_done);
+      } else {
+        if (fixup) settle(pfl);  // the previous group's further corrections (rare)
+        // This group's rule on this CTA's rows of each line. prev is the line's max |x_0| over the
+        // cluster and the rule is monotone in max |dx|, so the line meets it exactly when every
+        // CTA's rows do: the verdict needs no exchange of |dx| maxima now, only the flags, which
+        // ride on the next group's pass-0 exchange.
+        const bool fin = bits_finite(ndx_l) && bits_finite(prev);
+        if (!fin && active && p == 0) report_error(A.st, 5);
+        pf_line = active && fin &&
+                  !refine_done(__uint_as_float(ndx_l), __uint_as_float(prev), __uint_as_float(prev), A.tol, certified);
+        pndx = ndx_l;
+        pcert = certified;
+        pg = g;
       }
     }
     // Where x went through the tiles by TMA store, the next TMA load into them waits for the store's
     // read (at the top); the generic-proxy writes to them (d split in place, x) were fenced before
-    // the store, and the last __syncthreads_and above ordered every read.
+    // the store, and the last barrier above ordered every read.
   }
   if (!started) cluster_wait();  // a CTA without a group still completes the start-up barrier
+  if (!inplace && pg >= 0) {  // the cluster's last group: one exchange of its per-line flags
+    cluster_arrive();  // every CTA is past its reads of the norm slots
+    cluster_wait();
+    unsigned f, unused;
+    tree_norms_push<C>(pf_line ? 1u : 0u, 0u, norms + C * kTreeNormPitch, &xbar[3], rank, p, j);
+    tree_norms_read<C>(f, unused, norms + C * kTreeNormPitch, &xbar[3], xph3 & 1u, p, j, alive, A.st);
+    ++xph3;
+    if (__syncthreads_or(f != 0u)) settle(f);
+    if (rank == 0 && tid == 0) report_iters(A.st, 1);
+  }
   if (tid == 0) bulk_wait_all();  // the last x store has been written
   // every store into this CTA's shared memory has arrived: each exchange was waited for
 }
