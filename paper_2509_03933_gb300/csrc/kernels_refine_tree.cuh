@@ -346,13 +346,12 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
   cluster_arrive();
   bool started = false, alive = true;
   uint32_t tph0 = 0, tph1 = 0, xph0 = 0, xph1 = 0, xph2 = 0, xph3 = 0;  // phases of bar[0..1], xbar[0..3]
-  // Out of place, the stop rule of a group is settled one group later (see below): this thread's
-  // line of the cluster's previous group pg failed the rule on this CTA's rows (pf_line), that
-  // group's certificate and this CTA's max |dx| of the line, and the line's flag over the cluster
-  // once the next pass-0 exchange has brought it (pfl).
-  bool pf_line = false, pcert = false;
+  // Out of place, the stop rule of a group is settled one group later (see below), from what this
+  // thread keeps of its line in the cluster's previous group: this CTA's max |dx| of the line in
+  // pndx (bits 0..30; bit 31: the line failed the rule on this CTA's rows), the group's certificate,
+  // and the line's flag over the cluster once the next pass-0 exchange has brought it (pfl).
+  bool pcert = false;
   unsigned pndx = 0u, pfl = 0u;
-  int64_t pg = -1;
 
   // Further corrections of group gg (rare): a fresh float solve of the residual per pass, operands
   // from global memory (out of place the tiles hold another group's rows by then); in place, a and
@@ -466,20 +465,20 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
       if (!line_done) report_error(A.st, 7);
     }
   };
-  // Out of place: the previous group pg failed the rule on some line (pflag: this thread's line's
+  // Out of place: the previous group gg failed the rule on some line (pflag: this thread's line's
   // flag over the cluster). Every CTA of the cluster comes here at the same point.
-  auto settle = [&](unsigned pflag) {
+  auto settle = [&](unsigned pflag, int64_t gg) {
     cluster_arrive();  // every CTA is past its reads of the norm slots
     cluster_wait();
     if (A.max_iters <= 1) {
       if (rank == 0 && p == 0 && pflag != 0u) report_error(A.st, 7);
       return;
     }
-    unsigned gdx1, unused;  // the line's max |dx| of pass 1 of group pg
-    tree_norms_push<C>(pndx, 0u, norms + C * kTreeNormPitch, &xbar[3], rank, p, j);
+    unsigned gdx1, unused;  // the line's max |dx| of pass 1 of group gg
+    tree_norms_push<C>(pndx & 0x7FFFFFFFu, 0u, norms + C * kTreeNormPitch, &xbar[3], rank, p, j);
     tree_norms_read<C>(gdx1, unused, norms + C * kTreeNormPitch, &xbar[3], xph3 & 1u, p, j, alive, A.st);
     ++xph3;
-    later(pg, pcert, gdx1, pflag == 0u, false);
+    later(gg, pcert, gdx1, pflag == 0u, false);
   };
 
   for (int64_t g = blockIdx.x / C; g < n_groups; g += n_clusters) {
@@ -567,7 +566,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
       float xs_c, xe_c;
       // the flags of the previous group's lines ride along (out of place)
       tree_stage_b<C, true>(blk, unc, slots, &xbar[0], xph0 & 1u, rank, p, jj, j, u0, v0, xs_c, xe_c, unc_line, alive,
-                            A.st, pf_line ? 1u : 0u, &pfl);
+                            A.st, pndx >> 31, &pfl);
       ++xph0;
       certified = unc_line == 0u;
       // Boundary unknowns exactly as the neighbours will see them in the residual: at a CTA edge
@@ -686,18 +685,18 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
         const bool all_done = __syncthreads_and(line_done) != 0;
         later(g, certified, prev, line_done, all_done);
       } else {
-        if (fixup) settle(pfl);  // the previous group's further corrections (rare)
+        if (fixup) settle(pfl, g - n_clusters);  // the previous group's further corrections (rare)
         // This group's rule on this CTA's rows of each line. prev is the line's max |x_0| over the
         // cluster and the rule is monotone in max |dx|, so the line meets it exactly when every
         // CTA's rows do: the verdict needs no exchange of |dx| maxima now, only the flags, which
         // ride on the next group's pass-0 exchange.
         const bool fin = bits_finite(ndx_l) && bits_finite(prev);
         if (!fin && active && p == 0) report_error(A.st, 5);
-        pf_line = active && fin &&
-                  !refine_done(__uint_as_float(ndx_l), __uint_as_float(prev), __uint_as_float(prev), A.tol, certified);
-        pndx = ndx_l;
+        const bool fail = active && fin &&
+                          !refine_done(__uint_as_float(ndx_l), __uint_as_float(prev), __uint_as_float(prev), A.tol,
+                                       certified);
+        pndx = (ndx_l & 0x7FFFFFFFu) | (fail ? 0x80000000u : 0u);
         pcert = certified;
-        pg = g;
       }
     }
     // Where x went through the tiles by TMA store, the next TMA load into them waits for the store's
@@ -705,14 +704,16 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
     // the store, and the last barrier above ordered every read.
   }
   if (!started) cluster_wait();  // a CTA without a group still completes the start-up barrier
-  if (!inplace && pg >= 0) {  // the cluster's last group: one exchange of its per-line flags
+  const int64_t g_first = blockIdx.x / C;
+  if (!inplace && g_first < n_groups) {  // the cluster's last group: one exchange of its per-line flags
+    const int64_t g_last = g_first + (n_groups - 1 - g_first) / n_clusters * n_clusters;
     cluster_arrive();  // every CTA is past its reads of the norm slots
     cluster_wait();
     unsigned f, unused;
-    tree_norms_push<C>(pf_line ? 1u : 0u, 0u, norms + C * kTreeNormPitch, &xbar[3], rank, p, j);
+    tree_norms_push<C>(pndx >> 31, 0u, norms + C * kTreeNormPitch, &xbar[3], rank, p, j);
     tree_norms_read<C>(f, unused, norms + C * kTreeNormPitch, &xbar[3], xph3 & 1u, p, j, alive, A.st);
     ++xph3;
-    if (__syncthreads_or(f != 0u)) settle(f);
+    if (__syncthreads_or(f != 0u)) settle(f, g_last);
     if (rank == 0 && tid == 0) report_iters(A.st, 1);
   }
   if (tid == 0) bulk_wait_all();  // the last x store has been written
