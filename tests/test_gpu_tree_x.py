@@ -126,3 +126,27 @@ def test_cluster_variants_refuse_arrays_off_16_bytes(axis):
     assert plan.last_error()[0] == 0
     ref = O.thomas(*(_lines(t if axis == 1 else t.T) for t in (a, b, c, d)))
     assert rel_err(_lines(x if axis == 1 else x.T), ref) <= 1e-12
+
+
+@pytest.mark.parametrize("axis", [0, 1])
+def test_single_correction_reports_lines_short_of_the_rule(axis):
+    # With one correction allowed, a line that fails the stop rule is reported (status 7) without
+    # further passes; out of place the rule of a line group is settled with the next group's
+    # exchange, or, for a cluster's last group, by an exchange of its own: 4100 lines give every
+    # cluster several groups. A line group that meets the rule reports status 0 with the same x.
+    n, L = 256, 4100
+    shape = (n, L) if axis == 0 else (L, n)
+    g = synth.grid_general(shape, axis, 73, device="cuda", fp32_coefficients=True)
+    a, b, c, d = g["a32"], g["b32"], g["c32"], g["d"]
+    stiff = tdma.Plan(*tdma.line_layout(d, axis), precision="f32r", max_refine_iters=1, refine_tol=1e-30)
+    assert stiff.config["variant"] == (8 if axis == 0 else TREE_X)
+    x1 = torch.empty_like(d)
+    stiff.solve(a, b, c, d, x1)
+    assert stiff.last_error() == (7, 1)
+    plan = tdma.Plan(*tdma.line_layout(d, axis), precision="f32r", max_refine_iters=1)
+    x2 = torch.empty_like(d)
+    plan.solve(a, b, c, d, x2)
+    assert plan.last_error() == (0, 1)
+    assert torch.equal(x1, x2)  # one correction either way
+    ref = O.thomas(*(_lines(t if axis == 1 else t.T) for t in (a, b, c, d)))
+    assert rel_err(_lines(x2 if axis == 1 else x2.T), ref) <= 1e-12
