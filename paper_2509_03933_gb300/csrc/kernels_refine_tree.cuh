@@ -33,7 +33,9 @@
 // (x is d) the rule takes one exchange of the line maxima and the corrections follow at once.
 // Later passes re-read x from global memory.
 // Exchanges are point to point (st.async into the other CTAs' shared memory, completing on
-// their mbarriers): a CTA waits only for the data it needs, never for another CTA's threads.
+// their mbarriers): a CTA waits only for the data it needs, never for another CTA's threads, and
+// the block exchanges have one mbarrier per warp, so that a warp waits only for its own 4 lines
+// (warp w of every CTA of the cluster holds the same lines), not for the CTA's other warps.
 #pragma once
 #include <cooperative_groups.h>
 #include "layout.cuh"
@@ -80,8 +82,9 @@ __host__ __device__ constexpr size_t refine_tree_smem_bytes() {
 // Stage B for one pass: CTA tree, exchange of the CTA blocks, cluster tree, down-sweeps.
 // The exchange is point to point: lane p sends this CTA's block of line j (and `extra`, a
 // per-line norm of this CTA as abs_bits) into slot [rank][j] of CTA p with st.async, which
-// completes on CTA p's mbarrier `bar` for this buffer; every CTA waits on its own mbarrier for
-// the C x 32 slots (phase `phase`), so no CTA waits for another CTA's threads, only for data.
+// completes on CTA p's mbarrier bar[w] of this buffer (w: the warp, whose 4 lines are the same in
+// every CTA); warp w waits on its own bar[w] for the C x 4 slots of its lines (phase `phase`), so
+// no warp waits for other threads, only for the data of its lines.
 // `extra_max` is the maximum of `extra` over the cluster. Returns this partition's (u, v) and
 // this CTA's first and last unknowns of the line as the neighbouring CTAs see them (every CTA
 // computes the cluster tree from the same data in the same order, so the values agree bit for
@@ -95,7 +98,8 @@ TDMA_DEV void tree_stage_b(const Blk& b, unsigned extra, float* slots, uint64_t*
   constexpr int LC = C == 8 ? 3 : (C == 4 ? 2 : 1);
   Aff kc[3];
   const Blk B = tree_up<3>(b, p, kc);
-  if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, (uint32_t)C * kTreeLines * 32u);
+  bar += threadIdx.x >> 5;  // this warp's barrier: its 4 lines from every CTA
+  if ((threadIdx.x & 31) == 0) mbar_arrive_expect_tx(bar, (uint32_t)C * 4u * 32u);
   if (p < C) {
     const uint32_t dst = map_rank(slots + rank * kTreeSlotPitch + j * 8, p), rb = map_rank(bar, p);
     st_async4(dst, B.p1, B.q1, B.r1, B.p2, rb);
@@ -297,8 +301,10 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
   // tile mbarriers: rows [0, M/2) and [M/2, M) of every array arrive on bar[0] and bar[1] (XL:
   // the whole tile on bar[0])
   __shared__ __align__(8) uint64_t bar[2];
-  // exchange mbarriers: [0], [1] block slots of even / odd passes, [2], [3] norm slots
+  // exchange mbarriers: wbar[q][w] the block slots of warp w's lines in even (q = 0) / odd passes,
+  // xbar[2], xbar[3] the norm slots ([0] and [1] unused)
   __shared__ __align__(8) uint64_t xbar[4];
+  __shared__ __align__(8) uint64_t wbar[2][8];
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, p = lane >> 2, jj = lane & 3;
   const int j = 4 * w + jj;  // line within the cluster's 32
   const int rank = (int)cluster_rank();
@@ -338,6 +344,8 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
     mbar_init(&bar[1], 1);
 #pragma unroll
     for (int i = 0; i < 4; ++i) mbar_init(&xbar[i], 1);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) mbar_init(&wbar[i >> 3][i & 7], 1);
     mbar_fence_init();
   }
   __syncthreads();
@@ -345,7 +353,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
   // store into another CTA's shared memory
   cluster_arrive();
   bool started = false, alive = true;
-  uint32_t tph0 = 0, tph1 = 0, xph0 = 0, xph1 = 0, xph2 = 0, xph3 = 0;  // phases of bar[0..1], xbar[0..3]
+  uint32_t tph0 = 0, tph1 = 0, xph0 = 0, xph1 = 0, xph2 = 0, xph3 = 0;  // phases of bar[0..1], wbar[0..1][w], xbar[2..3]
   // Out of place, the stop rule of a group is settled one group later (see below), from what this
   // thread keeps of its line in the cluster's previous group: this CTA's max |dx| of the line in
   // pndx (bits 0..30; bit 31: the line failed the rule on this CTA's rows), the group's certificate,
@@ -437,7 +445,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
       unsigned unused;
       // pass `it` uses the buffers of its parity; the phase counters follow each mbarrier
       const int q = it & 1;
-      tree_stage_b<C>(blk, 0u, slots + q * C * kTreeSlotPitch, &xbar[q], (q ? xph1 : xph0) & 1u, rank, p, jj, j, u, v,
+      tree_stage_b<C>(blk, 0u, slots + q * C * kTreeSlotPitch, wbar[q], (q ? xph1 : xph0) & 1u, rank, p, jj, j, u, v,
                       xs_c, xe_c, unused, alive, A.st);
       if (q) ++xph1; else ++xph0;
       float dx[M];
@@ -565,7 +573,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
       unsigned unc_line;
       float xs_c, xe_c;
       // the flags of the previous group's lines ride along (out of place)
-      tree_stage_b<C, true>(blk, unc, slots, &xbar[0], xph0 & 1u, rank, p, jj, j, u0, v0, xs_c, xe_c, unc_line, alive,
+      tree_stage_b<C, true>(blk, unc, slots, wbar[0], xph0 & 1u, rank, p, jj, j, u0, v0, xs_c, xe_c, unc_line, alive,
                             A.st, pndx >> 31, &pfl);
       ++xph0;
       certified = unc_line == 0u;
@@ -619,7 +627,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
         }
         const Blk blk = S.block();
         float u, v, xs_c, xe_c;
-        tree_stage_b<C>(blk, nx, slots + C * kTreeSlotPitch, &xbar[1], xph1 & 1u, rank, p, jj, j, u, v, xs_c, xe_c,
+        tree_stage_b<C>(blk, nx, slots + C * kTreeSlotPitch, wbar[1], xph1 & 1u, rank, p, jj, j, u, v, xs_c, xe_c,
                         prev, alive, A.st);  // prev: line max |x_0|
         ++xph1;
         // Every thread has finished its pass-1 sweep, the last read of the a, b and c tiles (and,
