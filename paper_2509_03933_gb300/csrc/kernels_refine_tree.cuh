@@ -232,8 +232,10 @@ TDMA_DEV bool tree_line_done(unsigned gdx, unsigned gxm, unsigned& prev, bool ac
   return refine_done(__uint_as_float(gdx), __uint_as_float(gxm), pv, tol, certified);
 }
 
-// One thread loads a group's tile. Lines along a strided axis: rows [h M/2, (h + 1) M/2) of a, b,
-// c (float) and d (double, two boxes of 16 lines) arrive on bar[h], 5 KB per row. Unit-stride
+// One thread loads a group's tile. Lines along a strided axis: the M rows of a, b, c (float) and d
+// (double, two boxes of 16 lines) arrive on bar[0], 5 KB per row, one box per array (a wait part
+// way through the row loop, for a second half of the rows, kept the compiler from moving shared
+// loads ahead across it and cost more than it overlapped). Unit-stride
 // lines (XL): the CTA's 8 M rows of the 32 lines, a, b and c in boxes of 32 rows and d in boxes of
 // 16 rows (each box 128 bytes of every line, 4 KB), all on bar[0]; `parts` selects a, b and c (1),
 // d (2) or both (3), and `arrive` whether this call also arrives on bar[0] (without it, the copies
@@ -242,16 +244,12 @@ template <int M, bool XL>
 TDMA_DEV void tree_load_tiles(const TmaMaps& maps, float* ta, float* tb, float* tc, double* td, uint64_t* bar, int c_in,
                               int c_out, int c_p, int parts = 3, bool arrive = true) {
   if constexpr (!XL) {
-    constexpr int H = M / 2;
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      mbar_arrive_expect_tx(&bar[h], 5u * H * 1024u);
-      tma_load_4d(ta + h * H * 256, &maps.a, &bar[h], c_in, c_out, c_p, h * H);
-      tma_load_4d(tb + h * H * 256, &maps.b, &bar[h], c_in, c_out, c_p, h * H);
-      tma_load_4d(tc + h * H * 256, &maps.c, &bar[h], c_in, c_out, c_p, h * H);
-      tma_load_4d(td + h * H * 128, &maps.d, &bar[h], c_in, c_out, c_p, h * H);
-      tma_load_4d(td + M * 128 + h * H * 128, &maps.d, &bar[h], c_in + 16, c_out, c_p, h * H);
-    }
+    mbar_arrive_expect_tx(&bar[0], 5u * M * 1024u);
+    tma_load_4d(ta, &maps.a, &bar[0], c_in, c_out, c_p, 0);
+    tma_load_4d(tb, &maps.b, &bar[0], c_in, c_out, c_p, 0);
+    tma_load_4d(tc, &maps.c, &bar[0], c_in, c_out, c_p, 0);
+    tma_load_4d(td, &maps.d, &bar[0], c_in, c_out, c_p, 0);
+    tma_load_4d(td + M * 128, &maps.d, &bar[0], c_in + 16, c_out, c_p, 0);
   } else {
     const int r0 = c_p * M;  // the CTA's first row (c_p = rank x 8 partitions)
     const uint32_t bytes = ((parts & 1) ? 3u * M * 1024u : 0u) + ((parts & 2) ? 2u * M * 1024u : 0u);
@@ -296,11 +294,9 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
   static_assert(C == 2 || C == 4 || C == 8, "cluster size");
   static_assert(M >= 4 && M % 2 == 0, "rows per partition");
   static_assert(!XL || M == 16, "unit-stride tiles: a partition is half of a 32-row box");
-  constexpr int H = M / 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];  // aligned to 1 KB below
-  // tile mbarriers: rows [0, M/2) and [M/2, M) of every array arrive on bar[0] and bar[1] (XL:
-  // the whole tile on bar[0])
-  __shared__ __align__(8) uint64_t bar[2];
+  // tile mbarrier: the whole tile of a group arrives on bar[0]
+  __shared__ __align__(8) uint64_t bar[1];
   // exchange mbarriers: wbar[q][w] the block slots of warp w's lines in even (q = 0) / odd passes,
   // xbar[2], xbar[3] the norm slots ([0] and [1] unused)
   __shared__ __align__(8) uint64_t xbar[4];
@@ -341,7 +337,6 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
 
   if (tid == 0) {
     mbar_init(&bar[0], 1);
-    mbar_init(&bar[1], 1);
 #pragma unroll
     for (int i = 0; i < 4; ++i) mbar_init(&xbar[i], 1);
 #pragma unroll
@@ -353,7 +348,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
   // store into another CTA's shared memory
   cluster_arrive();
   bool started = false, alive = true;
-  uint32_t tph0 = 0, tph1 = 0, xph0 = 0, xph1 = 0, xph2 = 0, xph3 = 0;  // phases of bar[0..1], wbar[0..1][w], xbar[2..3]
+  uint32_t tph0 = 0, xph0 = 0, xph1 = 0, xph2 = 0, xph3 = 0;  // phases of bar[0], wbar[0..1][w], xbar[2..3]
   // Out of place, the stop rule of a group is settled one group later (see below), from what this
   // thread keeps of its line in the cluster's previous group: this CTA's max |dx| of the line in
   // pndx (bits 0..30; bit 31: the line failed the rule on this CTA's rows), the group's certificate,
@@ -395,11 +390,8 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
               tma_load_3d(tb + i * 1024, &maps.b, &bar[0], cp * M + 32 * i, ci, co);
             }
           } else {
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              tma_load_4d(ta + h * H * 256, &maps.a, &bar[0], ci, co, cp, h * H);
-              tma_load_4d(tb + h * H * 256, &maps.b, &bar[0], ci, co, cp, h * H);
-            }
+            tma_load_4d(ta, &maps.a, &bar[0], ci, co, cp, 0);
+            tma_load_4d(tb, &maps.b, &bar[0], ci, co, cp, 0);
           }
         }
         if (!mbar_wait_bounded(&bar[0], tph0, kTmaWaitPolls) && alive) {
@@ -547,13 +539,6 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
       } else {
 #pragma unroll
         for (int t = 0; t < M; ++t) {
-          if (t == H) {  // the second half of the rows (the first half is being swept meanwhile)
-            if (!mbar_wait_bounded(&bar[1], tph1, kTmaWaitPolls) && alive) {
-              alive = false;
-              report_error(A.st, 6);
-            }
-            tph1 ^= 1u;
-          }
           float a = ta[fidx(t)], b = tb[fidx(t)], c = tc[fidx(t)];
           if (t == 0 && first_part) a = 0.f;
           if (t == M - 1 && last_part) c = 0.f;

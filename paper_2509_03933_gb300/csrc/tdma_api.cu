@@ -552,7 +552,7 @@ cudaError_t launch_forward(const tdma_plan_s* p, const Args& A, cudaStream_t s) 
       TmaMaps maps;
       std::memset(&maps, 0, sizeof(maps));
       const int C = c.partitions / kTreeParts;
-      const int H = c.rows_per_thread / 2;  // tiles travel in two halves of rows
+      const int H = c.rows_per_thread;  // one box per array holds all rows of the tile
       const bool ok = encode_map(&maps.a, A.a, false, p->desc, c, kTreeParts, 32, true, H) &&
                       encode_map(&maps.b, A.b, false, p->desc, c, kTreeParts, 32, true, H) &&
                       encode_map(&maps.c, A.c, false, p->desc, c, kTreeParts, 32, true, H) &&
