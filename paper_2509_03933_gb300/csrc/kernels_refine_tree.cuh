@@ -298,9 +298,9 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
   // tile mbarrier: the whole tile of a group arrives on bar[0]
   __shared__ __align__(8) uint64_t bar[1];
   // exchange mbarriers: wbar[q][w] the block slots of warp w's lines in even (q = 0) / odd passes,
-  // xbar[2], xbar[3] the norm slots ([0] and [1] unused)
-  __shared__ __align__(8) uint64_t xbar[4];
+  // nbar[q] the norm slots
   __shared__ __align__(8) uint64_t wbar[2][8];
+  __shared__ __align__(8) uint64_t nbar[2];
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31, p = lane >> 2, jj = lane & 3;
   const int j = 4 * w + jj;  // line within the cluster's 32
   const int rank = (int)cluster_rank();
@@ -338,9 +338,9 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
   if (tid == 0) {
     mbar_init(&bar[0], 1);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) mbar_init(&xbar[i], 1);
-#pragma unroll
     for (int i = 0; i < 16; ++i) mbar_init(&wbar[i >> 3][i & 7], 1);
+    mbar_init(&nbar[0], 1);
+    mbar_init(&nbar[1], 1);
     mbar_fence_init();
   }
   __syncthreads();
@@ -348,7 +348,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
   // store into another CTA's shared memory
   cluster_arrive();
   bool started = false, alive = true;
-  uint32_t tph0 = 0, xph0 = 0, xph1 = 0, xph2 = 0, xph3 = 0;  // phases of bar[0], wbar[0..1][w], xbar[2..3]
+  uint32_t tph0 = 0, xph0 = 0, xph1 = 0, xph2 = 0, xph3 = 0;  // phases of bar[0], wbar[0..1][w], nbar[0..1]
   // Out of place, the stop rule of a group is settled one group later (see below), from what this
   // thread keeps of its line in the cluster's previous group: this CTA's max |dx| of the line in
   // pndx (bits 0..30; bit 31: the line failed the rule on this CTA's rows), the group's certificate,
@@ -454,8 +454,8 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
       }
       unsigned* nb = norms + q * C * kTreeNormPitch;
       unsigned gdx, gxm;
-      tree_norms_push<C>(line_max(ndx), line_max(nxm), nb, &xbar[2 + q], rank, p, j);
-      tree_norms_read<C>(gdx, gxm, nb, &xbar[2 + q], (q ? xph3 : xph2) & 1u, p, j, alive, A.st);
+      tree_norms_push<C>(line_max(ndx), line_max(nxm), nb, &nbar[q], rank, p, j);
+      tree_norms_read<C>(gdx, gxm, nb, &nbar[q], (q ? xph3 : xph2) & 1u, p, j, alive, A.st);
       if (q) ++xph3; else ++xph2;
       line_done = tree_line_done(gdx, gxm, prevd, act, A.tol, cert, rep, A.st);
       all_done = __syncthreads_and(line_done) != 0;
@@ -475,8 +475,8 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
       return;
     }
     unsigned gdx1, unused;  // the line's max |dx| of pass 1 of group gg
-    tree_norms_push<C>(pndx & 0x7FFFFFFFu, 0u, norms + C * kTreeNormPitch, &xbar[3], rank, p, j);
-    tree_norms_read<C>(gdx1, unused, norms + C * kTreeNormPitch, &xbar[3], xph3 & 1u, p, j, alive, A.st);
+    tree_norms_push<C>(pndx & 0x7FFFFFFFu, 0u, norms + C * kTreeNormPitch, &nbar[1], rank, p, j);
+    tree_norms_read<C>(gdx1, unused, norms + C * kTreeNormPitch, &nbar[1], xph3 & 1u, p, j, alive, A.st);
     ++xph3;
     later(gg, pcert, gdx1, pflag == 0u, false);
   };
@@ -634,7 +634,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
 #pragma unroll
         for (int t = 0; t < M; ++t) ndx = max(ndx, abs_bits(dx[t]));
         ndx_l = line_max(ndx);  // this CTA's rows of the line
-        if (inplace) tree_norms_push<C>(ndx_l, nx, norms + C * kTreeNormPitch, &xbar[3], rank, p, j);
+        if (inplace) tree_norms_push<C>(ndx_l, nx, norms + C * kTreeNormPitch, &nbar[1], rank, p, j);
         // x = x_0 + dx (exact widenings, one FP64 add): straight to global memory (for a fixed
         // row the four lines of a lane quad are 32 contiguous bytes), or by TMA store through the
         // thread's own d slots (XL) or, in place, through the a and b tiles (every thread's pass-1
@@ -669,7 +669,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
           }
         }
         if (inplace) {
-          tree_norms_read<C>(gdx, gxm, norms + C * kTreeNormPitch, &xbar[3], xph3 & 1u, p, j, alive, A.st);
+          tree_norms_read<C>(gdx, gxm, norms + C * kTreeNormPitch, &nbar[1], xph3 & 1u, p, j, alive, A.st);
           ++xph3;
         }
       }
@@ -703,8 +703,8 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
     cluster_arrive();  // every CTA is past its reads of the norm slots
     cluster_wait();
     unsigned f, unused;
-    tree_norms_push<C>(pndx >> 31, 0u, norms + C * kTreeNormPitch, &xbar[3], rank, p, j);
-    tree_norms_read<C>(f, unused, norms + C * kTreeNormPitch, &xbar[3], xph3 & 1u, p, j, alive, A.st);
+    tree_norms_push<C>(pndx >> 31, 0u, norms + C * kTreeNormPitch, &nbar[1], rank, p, j);
+    tree_norms_read<C>(f, unused, norms + C * kTreeNormPitch, &nbar[1], xph3 & 1u, p, j, alive, A.st);
     ++xph3;
     if (__syncthreads_or(f != 0u)) settle(f, g_last);
     if (rank == 0 && tid == 0) report_iters(A.st, 1);
