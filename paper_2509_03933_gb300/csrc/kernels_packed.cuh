@@ -70,6 +70,7 @@ struct PackedTables {
   const PackedChunk* chunks;
   const uint2* meta;      // kPackC * kPackT pairs per distinct chunk structure
   uint32_t* norms;        // kPackNormWords per line in memory order (see packed_first_verdict)
+  uint32_t* fix;          // [0]: chunks listed for further corrections, [1..]: their indices (out of place)
   int32_t n_chunks;
 };
 
@@ -600,24 +601,105 @@ TDMA_DEV void packed_prefetch(const PackedTables& PT, const Args& A, int g, int 
   prefetch_l2_range((const double*)A.d + b1, 8ll * n1);
 }
 
+// Shared memory of the Stage B hand-offs and of the per-chunk verdict (both kernels below).
+template <int C>
+struct PackedXchg {
+  uint64_t xbar[2];      // exchange mbarriers, by pass parity
+  float wsl[2][8 * 8];   // warp blocks (slot 7 unused), by pass parity
+  float4 dsl[2][8];      // per warp: u, v, first and last unknowns
+  float csl[2][C * 8];   // CTA blocks of the cluster, by pass parity
+  uint32_t s_more;       // epoch stamp: some line of the chunk needs more
+};
+// One thread: the barriers and the empty warp slot 7 (before the CTA's first barrier).
+template <int C>
+TDMA_DEV void packed_xchg_init(PackedXchg<C>& X) {
+  mbar_init(&X.xbar[0], 1);
+  mbar_init(&X.xbar[1], 1);
+  X.s_more = 0u;
+  for (int i = 0; i < 8; ++i) X.wsl[i / 4][7 * 8 + (i & 3)] = 0.f;
+  mbar_fence_init();
+}
+
+// Where this thread stands in chunk g: its rows (m of M, from segment row tid M), the line starts
+// among them (mask), the line ends (endmask, c = 0 there) and the line of its first row.
+struct PackedPart {
+  PackedChunk ch;
+  PackedSeg q;
+  int m;
+  uint32_t mask, endmask;
+  int line;
+};
+template <int C>
+TDMA_DEV PackedPart packed_part(const PackedTables& PT, int g, int rank, int tid, int kp, bool coord) {
+  PackedPart r;
+  r.ch = PT.chunks[g];
+  r.q = packed_seg(PT, g, rank);
+  const int M = r.q.M;
+  r.m = coord ? 0 : max(0, min(M, r.q.segn - tid * M));
+  const uint2 meta = coord ? make_uint2(0u, 0u) : PT.meta[(int64_t)r.ch.meta * (C * kPackT) + kp];
+  r.mask = meta.x & ((1u << kPackRowBits) - 1u);
+  r.line = r.ch.line0 + (int)meta.y;
+  // c = 0 on rows that end a line: row t ends one when row t + 1 starts one
+  r.endmask = r.m > 0 ? ((r.mask >> 1) | (((meta.x >> kPackRowBits) & 1u) << (r.m - 1))) : 0u;
+  return r;
+}
+
+// Further corrections of a chunk some of whose lines failed the stop rule after the first one
+// (rare): passes that read the coefficients and x from global memory (d too, unless sd holds the
+// chunk's d pairs), every CTA of the cluster the same number of times (the cluster's verdict),
+// until every line meets the rule or max_iters corrections. Returns the corrections made.
+template <int C, bool TR>
+TDMA_DEV int packed_more_passes(const Args& A, const PackedTables& PT, const PackedPart& P, const float2* sd,
+                                PackedXchg<C>& X, uint32_t (&xph)[2], uint32_t& epoch, bool& alive, int tid, int w,
+                                int lane, int rank, int kp, bool coord) {
+  const int M = P.q.M;
+  int it = 1;
+  bool again = true;
+  cluster_arrive();  // x of every CTA went out before this arrival
+  cluster_wait();
+  while (again && it < A.max_iters) {
+    ++it;
+    const int qp = it & 1;
+    if (coord) {
+      packed_coord_b<C>(X.wsl[qp], X.dsl[qp], X.csl[qp], &X.xbar[qp], xph[qp] & 1u, rank, lane, alive, A.st);
+      ++xph[qp];
+    } else {
+      packed_later_pass<TR>(PT, (const float*)A.a, (const float*)A.b, (const float*)A.c, (const double*)A.d, sd,
+                            X.wsl[qp], X.dsl[qp], (double*)A.x, P.q.gbase + (int64_t)tid * M, w, lane, kp, P.m, P.mask,
+                            P.endmask, P.line, P.q.seg0 + tid * M, P.ch.rows);
+    }
+    __syncthreads();
+    ++epoch;
+    cluster_arrive();
+    cluster_wait();
+    bool more = !coord && packed_later_verdict(P.mask, P.m, P.line, PT.norms, it == 2, A.tol, it >= A.max_iters, A.st);
+    more = __syncthreads_or(more) != 0;
+    if (more && tid < C) st_cluster_u32(map_rank(&X.s_more, tid), epoch);
+    cluster_arrive();
+    cluster_wait();
+    again = X.s_more == epoch;
+  }
+  return it;
+}
+
 // Persistent: the grid holds the clusters that fit on the GPU at once; cluster q takes chunks
 // q, q + Q, q + 2Q, ... (Q clusters, chunks sorted longest first at plan time). Warps 0..6 of a
-// CTA compute (one partition per thread), warp 7 coordinates Stage B. Unless x is written over d,
-// the next chunk's a, b and c copies go out (from the coordinator) as soon as pass 1's Stage B has
+// CTA compute (one partition per thread), warp 7 coordinates Stage B. Out of place (IP false), the
+// next chunk's a, b and c copies go out (from the coordinator) as soon as pass 1's Stage B has
 // passed the compute warps' last read of them, and its d copies once every warp's x has left the
-// d tile, so that they overlap Stage C, the x copy-out and the per-line stop rule; the rare further
-// corrections then read the coefficients and d from global memory. With x over d, d stays in
-// shared memory until its chunk is done, and every copy of the next chunk goes out after it.
-template <int C, bool TR>
+// d tile, so that they overlap Stage C, the x copy-out and the per-line stop rule; a chunk with a
+// line that needs further corrections (rare) is listed for packed_fixup_kernel, launched after
+// this kernel, which reads the coefficients, d and x from global memory. (Kept out of this kernel,
+// whose call into the further passes cost spills on the main path: 0.75 -> 0.69 ms on the
+// 20000-line batch without it.) In place (IP true, x is d), d stays in shared memory until its
+// chunk is done, every copy of the next chunk goes out after it, and the further corrections run
+// here, with d from the shared-memory float pairs.
+template <int C, bool TR, bool IP>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
     packed_refine_kernel(const Args A, const PackedTables PT) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ __align__(8) uint64_t xbar[2];      // exchange mbarriers, by pass parity
-  __shared__ __align__(8) uint64_t tbar;         // tile copies of a chunk
-  __shared__ __align__(16) float wsl[2][8 * 8];  // warp blocks (slot 7 unused), by pass parity
-  __shared__ __align__(16) float4 dsl[2][8];     // per warp: u, v, first and last unknowns
-  __shared__ __align__(16) float csl[2][C * 8];  // CTA blocks of the cluster, by pass parity
-  __shared__ uint32_t s_more;                    // epoch stamp: some line of the chunk needs more
+  __shared__ __align__(16) PackedXchg<C> X;
+  __shared__ __align__(8) uint64_t tbar;  // tile copies of a chunk
   const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
   const float keep = certify_keep(A.tol);
   const bool coord = w == kPackW;
@@ -629,19 +711,12 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
   double* td = reinterpret_cast<double*>(tc + kPackTile);
   float2* td2 = reinterpret_cast<float2*>(td);
   double* tx_ab = reinterpret_cast<double*>(ta);  // with x over d, x leaves through the a and b space
-  const float* fa = (const float*)A.a;
-  const float* fb = (const float*)A.b;
-  const float* fc = (const float*)A.c;
-  const double* gd = (const double*)A.d;
   double* gx = (double*)A.x;
-  const bool overlap = A.x != A.d;  // with x over d, d must stay in shared memory until done
+  constexpr bool overlap = !IP;  // with x over d, d must stay in shared memory until done
 
   if (tid == 0) {
-    mbar_init(&xbar[0], 1);
-    mbar_init(&xbar[1], 1);
+    packed_xchg_init<C>(X);
     mbar_init(&tbar, 1);
-    s_more = 0u;
-    for (int i = 0; i < 8; ++i) wsl[i / 4][7 * 8 + (i & 3)] = 0.f;  // the empty slot 7
     mbar_fence_init();
   }
   __syncthreads();
@@ -657,15 +732,9 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
   }
 
   for (int g = g0; g < PT.n_chunks; g += n_clusters) {
-    const PackedChunk ch = PT.chunks[g];
-    const PackedSeg q = packed_seg(PT, g, rank);
+    const PackedPart P = packed_part<C>(PT, g, rank, tid, kp, coord);
+    const PackedSeg& q = P.q;
     const int M = q.M;
-    const int m = coord ? 0 : max(0, min(M, q.segn - tid * M));
-    const uint2 meta = coord ? make_uint2(0u, 0u) : PT.meta[(int64_t)ch.meta * (C * kPackT) + kp];
-    const uint32_t mask = meta.x & ((1u << kPackRowBits) - 1u);
-    const int line = ch.line0 + (int)meta.y;
-    // c = 0 on rows that end a line: row t ends one when row t + 1 starts one
-    const uint32_t endmask = m > 0 ? ((mask >> 1) | (((meta.x >> kPackRowBits) & 1u) << (m - 1))) : 0u;
     const bool has_next = g + n_clusters < PT.n_chunks;
     PackedArr r[4];
     packed_arrs<TR>(A, q, ta, tb, tc, td, r);
@@ -684,15 +753,15 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
       started = true;
     }
     // a = 0 where a line starts, c = 0 where one ends (each thread its own rows)
-    for (uint32_t bm = mask; bm; bm &= bm - 1u) ta[r[0].sh + tid * M + (__ffs(bm) - 1)] = 0.f;
-    for (uint32_t bm = endmask; bm; bm &= bm - 1u) tc[r[2].sh + tid * M + (__ffs(bm) - 1)] = 0.f;
+    for (uint32_t bm = P.mask; bm; bm &= bm - 1u) ta[r[0].sh + tid * M + (__ffs(bm) - 1)] = 0.f;
+    for (uint32_t bm = P.endmask; bm; bm &= bm - 1u) tc[r[2].sh + tid * M + (__ffs(bm) - 1)] = 0.f;
     // this chunk's generic-proxy writes to the tiles come before the next chunk's copies into them
     fence_proxy_async_smem();
     const bool edge_s = lane == 0 && kp > 0, edge_e = lane == 31 && kp + 1 < C * kPackT;
 
     if (coord) {
-      packed_coord_b<C>(wsl[0], dsl[0], csl[0], &xbar[0], xph[0] & 1u, rank, lane, alive, A.st);
-      packed_coord_b<C>(wsl[1], dsl[1], csl[1], &xbar[1], xph[1] & 1u, rank, lane, alive, A.st);
+      packed_coord_b<C>(X.wsl[0], X.dsl[0], X.csl[0], &X.xbar[0], xph[0] & 1u, rank, lane, alive, A.st);
+      packed_coord_b<C>(X.wsl[1], X.dsl[1], X.csl[1], &X.xbar[1], xph[1] & 1u, rank, lane, alive, A.st);
       ++xph[0];
       ++xph[1];
       // pass 1's barrier 1 is behind: every compute warp has made its last read of a, b and c
@@ -707,15 +776,16 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
 #define TDMA_PASSES(MM)                                                                                      \
   case MM:                                                                                                    \
     packed_passes<MM>(ta + r[0].sh + o, tb + r[1].sh + o, tc + r[2].sh + o, td + r[3].sh + o, td2 + r[3].sh + o, \
-                      rx, wsl[0], dsl[0], wsl[1], dsl[1], w, lane, edge_s, edge_e, mask, line, PT.norms, keep);  \
+                      rx, X.wsl[0], X.dsl[0], X.wsl[1], X.dsl[1], w, lane, edge_s, edge_e, P.mask, P.line,      \
+                      PT.norms, keep);                                                                        \
     break;
         TDMA_PACKED_M(TDMA_PASSES)
 #undef TDMA_PASSES
         default: {  // not a compiled M (the plan never makes one): report; the barriers still run
           if (tid == 0) report_error(A.st, 2);
           float du, dv;
-          packed_compute_b(Blk{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, wsl[0], dsl[0], w, lane, du, dv);
-          packed_compute_b(Blk{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, wsl[1], dsl[1], w, lane, du, dv);
+          packed_compute_b(Blk{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, X.wsl[0], X.dsl[0], w, lane, du, dv);
+          packed_compute_b(Blk{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, X.wsl[1], X.dsl[1], w, lane, du, dv);
         }
       }
       fence_proxy_async_smem();  // the d pairs and x come before the next chunk's copies
@@ -733,40 +803,47 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
       packed_bulk<TR>(A, packed_seg(PT, g + n_clusters, rank), ta, tb, tc, td, &tbar, 8, true);
     cluster_wait();  // the atomics of every CTA are complete and visible
     // ---------------- stop rule per line: every CTA evaluates all lines of the chunk
-    bool again = __syncthreads_or(packed_first_verdict(ch, PT.norms, A.tol, A.max_iters <= 1, rank == 0, A.st)) != 0;
+    const bool again =
+        __syncthreads_or(packed_first_verdict(P.ch, PT.norms, A.tol, A.max_iters <= 1, rank == 0, A.st)) != 0;
     int it = 1;
-
-    // ---------------- further corrections (rare): coefficients and x from global memory
-    if (again && it < A.max_iters) {  // x of every CTA went out before its first arrival: wait for it
-      cluster_arrive();
-      cluster_wait();
-    }
-    while (again && it < A.max_iters) {
-      ++it;
-      const int qp = it & 1;
-      if (coord) {
-        packed_coord_b<C>(wsl[qp], dsl[qp], csl[qp], &xbar[qp], xph[qp] & 1u, rank, lane, alive, A.st);
-        ++xph[qp];
-        __syncthreads();
-      } else {
-        packed_later_pass<TR>(PT, fa, fb, fc, gd, overlap ? nullptr : td2 + r[3].sh + tid * M, wsl[qp], dsl[qp],
-                              gx, q.gbase + (int64_t)tid * M, w, lane, kp, m, mask, endmask, line, q.seg0 + tid * M,
-                              ch.rows);
-        __syncthreads();
+    if (again && A.max_iters > 1) {
+      if constexpr (IP) {  // further corrections here, d from the shared-memory pairs
+        it = packed_more_passes<C, TR>(A, PT, P, coord ? nullptr : td2 + r[3].sh + tid * M, X, xph, epoch, alive,
+                                       tid, w, lane, rank, kp, coord);
+      } else if (rank == 0 && tid == 0) {  // listed for packed_fixup_kernel (every CTA reached the same verdict)
+        PT.fix[1 + atomicAdd(PT.fix, 1u)] = (uint32_t)g;
       }
-      ++epoch;
-      cluster_arrive();
-      cluster_wait();
-      bool more = !coord && packed_later_verdict(mask, m, line, PT.norms, it == 2, A.tol, it >= A.max_iters, A.st);
-      more = __syncthreads_or(more) != 0;
-      if (more && tid < C) st_cluster_u32(map_rank(&s_more, tid), epoch);
-      cluster_arrive();
-      cluster_wait();
-      again = s_more == epoch;
     }
     if (rank == 0 && tid == 0) report_iters(A.st, it);
   }
   if (!started) cluster_wait();  // a cluster without a chunk still completes the start-up barrier
+}
+
+// Further corrections of the chunks that packed_refine_kernel (out of place) listed, launched
+// after it on the same stream: cluster k takes listed chunks k, k + K, ... with the same thread
+// geometry (the partitions of a chunk, warp 7 coordinating Stage B). x, the coefficients and d
+// come from global memory; the per-line table holds the first correction's maxima.
+template <int C, bool TR>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kPackThreads, 2)
+    packed_fixup_kernel(const Args A, const PackedTables PT) {
+  __shared__ __align__(16) PackedXchg<C> X;
+  const int n_fix = (int)ld_relaxed_u32(PT.fix);  // written by the previous launch
+  if ((int)(blockIdx.x / C) >= n_fix) return;       // the whole cluster leaves together
+  const int tid = threadIdx.x, w = tid >> 5, lane = tid & 31;
+  const bool coord = w == kPackW;
+  const int rank = (int)cluster_rank();
+  const int kp = rank * kPackT + tid;
+  if (tid == 0) packed_xchg_init<C>(X);
+  __syncthreads();
+  cluster_arrive();  // every CTA's barriers are initialised before the first remote store
+  cluster_wait();
+  bool alive = true;
+  uint32_t xph[2] = {0u, 0u}, epoch = 0u;
+  for (int k = (int)(blockIdx.x / C); k < n_fix; k += (int)(gridDim.x / C)) {
+    const PackedPart P = packed_part<C>(PT, (int)PT.fix[1 + k], rank, tid, kp, coord);
+    const int it = packed_more_passes<C, TR>(A, PT, P, nullptr, X, xph, epoch, alive, tid, w, lane, rank, kp, coord);
+    if (rank == 0 && tid == 0) report_iters(A.st, it);
+  }
 }
 
 }  // namespace tdma

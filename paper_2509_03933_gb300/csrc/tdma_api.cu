@@ -21,7 +21,7 @@
 #include "kernels_thomas.cuh"
 #include "kernels_thomas_short.cuh"
 #include "kernels_ragged.cuh"
-#include "kernels_packed.cuh"
+#include "packed_launch.h"
 #include "kernels_shared.cuh"
 #include "kernels_thomas_staged.cuh"
 #include "kernels_backward.cuh"
@@ -608,13 +608,8 @@ cudaError_t launch_forward(const tdma_plan_s* p, const Args& A, cudaStream_t s) 
       return launch_thomas(p->desc.precision, p->desc.nrhs, A, c, s);
     case TDMA_VARIANT_SHARED:
       return launch_shared_any(p->desc.precision, p->desc.nrhs, false, A, s);
-    case TDMA_VARIANT_PACKED: {
-      // the per-line maxima start from zero (the kernel also leaves them zero)
-      cudaError_t e = cudaMemsetAsync(p->pk.norms, 0, sizeof(uint32_t) * kPackNormWords * (size_t)p->desc.n_lines, s);
-      if (e != cudaSuccess) return e;
-      packed_refine_kernel<kPackC, false><<<grid, block, sm, s>>>(A, p->pk);
-      break;
-    }
+    case TDMA_VARIANT_PACKED:
+      return packed_launch(false, p->pk, c, p->desc.n_lines, A, s);
     case TDMA_VARIANT_RAGGED: {
       cudaError_t e = cudaMemsetAsync(p->rt.queue, 0, sizeof(int32_t), s);
       if (e != cudaSuccess) return e;
@@ -686,7 +681,7 @@ cudaError_t prepare_kernel(const tdma_plan_s* p) {
     case TDMA_VARIANT_RAGGED:
       return cudaSuccess;
     case TDMA_VARIANT_PACKED:
-      return set_smem(packed_refine_kernel<kPackC, false>, sm);
+      return packed_prepare(sm);
   }
   return cudaSuccess;
 }
@@ -729,10 +724,8 @@ cudaError_t backward_impl(const tdma_plan_s* p, const void* a, const void* b, co
     if (d.precision == TDMA_F64) ragged_dc_kernel<double, true><<<rc.blocks, rc.threads_per_block, sm, s>>>(A, p->rt);
     else if (d.precision == TDMA_F32) ragged_dc_kernel<float, true><<<rc.blocks, rc.threads_per_block, sm, s>>>(A, p->rt);
     else if (p->pk_mem) {  // the chunk kernel on the transposed rows
-      e = cudaMemsetAsync(p->pk.norms, 0, sizeof(uint32_t) * kPackNormWords * (size_t)d.n_lines, s);
+      e = packed_launch(true, p->pk, p->cfg, d.n_lines, A, s);
       if (e != cudaSuccess) return e;
-      const tdma_config_t& pc = p->cfg;
-      packed_refine_kernel<kPackC, true><<<pc.blocks, pc.threads_per_block, (size_t)pc.smem_bytes, s>>>(A, p->pk);
     } else ragged_refine_kernel<true><<<rc.blocks, rc.threads_per_block, sm, s>>>(A, p->rt);
     e = cudaGetLastError();
     if (e != cudaSuccess || (!ga && !gb && !gc)) return e;
@@ -970,33 +963,29 @@ bool build_packed_tables(tdma_plan_s* p, const std::vector<int64_t>& off, const 
   const size_t b_chunks = sizeof(PackedChunk) * chunks.size();
   const size_t off_meta = (b_chunks + 255) / 256 * 256;
   const size_t off_norms = off_meta + (sizeof(uint2) * meta.size() + 255) / 256 * 256;
-  const size_t total = off_norms + sizeof(uint32_t) * kPackNormWords * (size_t)L;
+  // the per-line table, then the list of chunks for further corrections (count, indices)
+  const size_t b_norms = sizeof(uint32_t) * kPackNormWords * (size_t)L;
+  const size_t total = off_norms + b_norms + sizeof(uint32_t) * (1 + chunks.size());
   void* mem = nullptr;
   if (cudaMalloc(&mem, total) != cudaSuccess) { (void)cudaGetLastError(); return false; }
   unsigned char* m = (unsigned char*)mem;
   if (cudaMemcpy(m, chunks.data(), b_chunks, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(m + off_meta, meta.data(), sizeof(uint2) * meta.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
-      cudaMemset(m + off_norms, 0, sizeof(uint32_t) * kPackNormWords * (size_t)L) != cudaSuccess) {
+      cudaMemset(m + off_norms, 0, b_norms + sizeof(uint32_t)) != cudaSuccess) {
     cudaFree(mem);
     return false;
   }
   const size_t sm = (size_t)kPackTile * (3 * sizeof(float) + sizeof(double));
-  if (set_smem(packed_refine_kernel<kPackC, false>, sm) != cudaSuccess ||
-      set_smem(packed_refine_kernel<kPackC, true>, sm) != cudaSuccess) {
+  if (packed_prepare(sm) != cudaSuccess) {
     cudaFree(mem);
     return false;
   }
-  cudaLaunchConfig_t lc{};
-  lc.gridDim = dim3(kPackC);
-  lc.blockDim = dim3(kPackThreads);
-  lc.dynamicSmemBytes = sm;
-  int resident = 0;
-  if (cudaOccupancyMaxActiveClusters(&resident, packed_refine_kernel<kPackC, false>, &lc) != cudaSuccess) resident = 0;
-  (void)cudaGetLastError();
+  const int resident = packed_resident_clusters(sm);
   p->pk_mem = mem;
   p->pk.chunks = (const PackedChunk*)m;
   p->pk.meta = (const uint2*)(m + off_meta);
   p->pk.norms = (uint32_t*)(m + off_norms);
+  p->pk.fix = (uint32_t*)(m + off_norms + b_norms);
   p->pk.n_chunks = (int32_t)chunks.size();
   tdma_config_t c{};
   c.variant = TDMA_VARIANT_PACKED;

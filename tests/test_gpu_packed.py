@@ -152,6 +152,55 @@ def test_packed_second_correction_for_weakly_dominant_lines():
     assert _err(x, _oracle(a, b, c, dn, o, n, dtype=np.longdouble), o, n) <= 1e-12
 
 
+def _weak(lengths, seed):
+    """tridiag(-1, 2.01, -1) lines (condition number about 400: the stop rule asks for a second
+    correction) with the right-hand side of a known smooth solution."""
+    a, b, c, d, offs, lens = _problem(lengths, seed)
+    o, n = offs.cpu().numpy(), lens.cpu().numpy()
+    a.fill_(-1.0)
+    c.fill_(-1.0)
+    b.fill_(2.01)
+    xt = torch.sin(torch.arange(a.numel(), device="cuda", dtype=torch.float64) * 0.37)
+    dn = 2.01 * xt
+    for l in range(len(o)):
+        s, e = o[l], o[l] + n[l]
+        dn[s + 1:e] -= xt[s:e - 1]
+        dn[s:e - 1] -= xt[s + 1:e]
+    return a, b, c, dn, offs, lens, o, n
+
+
+def test_packed_second_correction_in_place():
+    # x over d: the chunk kernel keeps d's float pairs and makes the further corrections itself
+    a, b, c, dn, offs, lens, o, n = _weak(np.array([3000, 50, 17000, 700], np.int32), 15)
+    ref = _oracle(a, b, c, dn, o, n, dtype=np.longdouble)
+    xd = dn.clone()
+    _, plan = _solve(a, b, c, xd, offs, lens, out=xd, check=False)
+    assert plan.config["variant"] == PACKED
+    st, iters = plan.last_error()
+    assert st == 0 and iters >= 2
+    assert _err(xd, ref, o, n) <= 1e-12
+
+
+def test_packed_every_chunk_corrected_again():
+    # Out of place every chunk is listed for the further-correction launch, more chunks than
+    # clusters, so each cluster of that launch takes several; in place the same in the chunk kernel
+    lengths = synth.ragged_lengths(3000, 16, 16384, seed=12)
+    a, b, c, dn, offs, lens, o, n = _weak(lengths, 16)
+    x, plan = _solve(a, b, c, dn, offs, lens, check=False)
+    assert plan.config["variant"] == PACKED
+    assert int(n.sum()) > CHUNK_ROWS * (plan.config["blocks"] // 4)  # more chunks than clusters
+    st, iters = plan.last_error()
+    assert st == 0 and iters >= 2
+    lines = sorted(set(np.random.default_rng(3).choice(len(o), 40, replace=False).tolist()) | {int(np.argmax(n))})
+    ref = _oracle(a, b, c, dn, o, n, lines=lines, dtype=np.longdouble)
+    assert _err(x, ref, o, n) <= 1e-12
+    xd = dn.clone()
+    _solve(a, b, c, xd, offs, lens, out=xd, check=False, plan=plan)
+    st2, iters2 = plan.last_error()
+    assert st2 == 0 and iters2 >= 2
+    assert torch.equal(xd, x)  # the same passes in either kernel
+
+
 def test_packed_stop_rule_run_out_and_nonfinite_values():
     # Chunks whose lines fail the local stop test go to the rule on the line maxima after the last
     # chunk: an unreachable tolerance runs max_refine_iters corrections and reports
