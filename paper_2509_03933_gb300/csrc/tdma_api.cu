@@ -723,8 +723,9 @@ cudaError_t backward_impl(const tdma_plan_s* p, const void* a, const void* b, co
     const size_t sm = (size_t)rc.smem_bytes;
     if (d.precision == TDMA_F64) ragged_dc_kernel<double, true><<<rc.blocks, rc.threads_per_block, sm, s>>>(A, p->rt);
     else if (d.precision == TDMA_F32) ragged_dc_kernel<float, true><<<rc.blocks, rc.threads_per_block, sm, s>>>(A, p->rt);
-    else if (p->pk_mem) {  // the chunk kernel on the transposed rows
-      e = packed_launch(true, p->pk, p->cfg, d.n_lines, A, s);
+    else if (p->pk_mem) {  // the chunk kernel on the transposed rows, with its own configuration (the
+      // forward pass may run the group kernel: a tuned or cached choice)
+      e = packed_launch(true, p->pk, p->pkcfg, d.n_lines, A, s);
       if (e != cudaSuccess) return e;
     } else ragged_refine_kernel<true><<<rc.blocks, rc.threads_per_block, sm, s>>>(A, p->rt);
     e = cudaGetLastError();

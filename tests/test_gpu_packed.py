@@ -322,3 +322,43 @@ def test_uniform_unit_stride_lines_use_the_chunk_kernel(n, L, gap):
     if n <= 5000:  # explicit partitions keep the partition kernels
         fixed = tdma.Plan(*tdma.line_layout(d, 1), precision="f32r", partitions=1 if n < 4 else 2)
         assert fixed.config["variant"] != PACKED
+
+
+def test_backward_with_group_kernel_forward_and_chunk_tables(tmp_path):
+    # A ragged FP32 + refinement plan whose forward pass runs the group kernel (a cached choice, as
+    # after an autotune that picked it) while the chunk kernel's tables exist: the adjoint solve
+    # runs the chunk kernel with the chunk kernel's own configuration. The choice is seeded through
+    # the tuning cache file, read once per process, so the check runs in a child process.
+    import subprocess
+    import sys
+    lengths = synth.ragged_lengths(300, 16, 16384, seed=21)
+    lb = lambda v: int(max(1, int(v))).bit_length() - 1
+    key = f"ragged p2 l{lb(len(lengths))} m{lb(lengths.max())} t{lb(lengths.sum())}"
+    path = tmp_path / "tune.txt"
+    path.write_text(f"{key}|{RAGGED}|16\n")
+    code = (
+        "import sys, os, numpy as np, torch; sys.path.insert(0, os.getcwd())\n"
+        "import oracle as O, synth, paper_2509_03933_gb300 as tdma\n"
+        "lengths = synth.ragged_lengths(300, 16, 16384, seed=21)\n"
+        "r = synth.ragged_general(lengths, 21, device='cuda', fp32_coefficients=True)\n"
+        "a, b, c, d = r['a32'], r['b32'], r['c32'], r['d']\n"
+        "x, plan = tdma.solve_ragged(a, b, c, d, r['offsets'], r['lengths'], precision='f32r')\n"
+        f"assert plan.config['variant'] == {RAGGED}, plan.config\n"
+        "assert plan.last_error()[0] == 0\n"
+        "w = synth.normal(21, synth.AID['w'], torch.arange(r['total'], device='cuda'))\n"
+        "ga, gb, gc, gd = (torch.empty_like(a), torch.empty_like(b), torch.empty_like(c), torch.empty_like(x))\n"
+        "plan.backward(a, b, c, x, w, ga, gb, gc, gd)\n"
+        "assert plan.last_error()[0] == 0\n"
+        "offs, lens = r['offsets'].cpu().numpy(), r['lengths'].cpu().numpy()\n"
+        "ha, hb, hc = (r[k].cpu().numpy() for k in ('a', 'b', 'c'))\n"
+        "xs, hw, hg = x.cpu().numpy(), w.cpu().numpy(), gd.cpu().numpy()\n"
+        "worst = 0.0\n"
+        "for l in list(np.argsort(-lengths)[:3]) + list(range(0, 300, 29)):\n"
+        "    s = slice(offs[l], offs[l] + lens[l])\n"
+        "    worst = max(worst, O.rel_l2(hg[s], O.adjoint_grads(ha[s], hb[s], hc[s], xs[s], hw[s])[3]))\n"
+        "print('worst', worst)\n"
+        "assert worst <= 1e-12, worst\n")
+    env = dict(os.environ, TDMA_AUTOTUNE_CACHE=str(path))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    run = subprocess.run([sys.executable, "-c", code], env=env, cwd=root, capture_output=True, text=True, timeout=600)
+    assert run.returncode == 0, run.stdout + run.stderr
