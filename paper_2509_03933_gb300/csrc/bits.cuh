@@ -99,6 +99,28 @@ TDMA_HD bool widen_normal(float f, double& d) {
   return true;
 }
 
+// Double -> float rounded to nearest, ties to even, for the doubles whose float lies in the
+// normal range: biased exponent e in [897, 1150] (2^-126 <= |v| < 2^128). The float keeps the
+// sign, the exponent rebased by 896 and the top 23 of the 52 fraction bits; the other 29 bits
+// decide the rounding (up above half, or at half when the kept bits are odd); a carry out of the
+// fraction moves to the exponent, up to infinity for the largest values, as the rounding rule
+// gives. Returns false outside the range (then nothing is written).
+TDMA_HD bool narrow_normal(double v, float& f) {
+  const uint64_t u = dbits(v);
+  const uint32_t hi = (uint32_t)(u >> 32), lo = (uint32_t)u;
+  const uint32_t e = (hi >> 20) & 0x7FFu;
+  if (e - 897u >= 254u) return false;
+#ifdef __CUDA_ARCH__
+  const uint32_t keep = __funnelshift_l(lo, hi, 3) & 0x7FFFFFu;
+#else
+  const uint32_t keep = ((hi << 3) | (lo >> 29)) & 0x7FFFFFu;
+#endif
+  const uint32_t rest = lo & 0x1FFFFFFFu, half = 1u << 28;
+  const uint32_t up = (rest > half || (rest == half && (keep & 1u))) ? 1u : 0u;
+  f = bitsf((((e - 896u) << 23) | keep) + up | (hi & 0x80000000u));
+  return true;
+}
+
 #ifdef __CUDACC__
 // Device entry points with the general routines as the (rare) fallback.
 TDMA_DEV ff split_f64_fast(double v) {
@@ -110,6 +132,11 @@ TDMA_DEV double f2d_fast(float f) {
   double d;
   if (widen_normal(f, d)) return d;
   return f2d(f);
+}
+TDMA_DEV float d2f_fast(double v) {
+  float f;
+  if (narrow_normal(v, f)) return f;
+  return __double2float_rn(v);
 }
 #endif
 

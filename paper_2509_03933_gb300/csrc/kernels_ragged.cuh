@@ -18,6 +18,7 @@
 #include "layout.cuh"
 #include "kernels_dc.cuh"
 #include "kernels_refine.cuh"
+#include "bits.cuh"
 
 namespace tdma {
 
@@ -311,23 +312,43 @@ __global__ void __launch_bounds__(kRaggedThreads) ragged_refine_kernel(const Arg
   }
 }
 
-// Gradient epilogue for ragged batches: one warp per line, lanes striding over its rows.
+// -l x in the gradient type: in the precision of x (for float x exact before its one rounding: the
+// product of two floats fits in a double), narrowed to float on the integer pipe for double x and
+// float gradients (the FP64 pipe converts at its own low rate).
+template <class GT, class XT> TDMA_DEV GT neg_prod(XT l, XT x) { return (GT)(-(l * x)); }
+template <> TDMA_DEV float neg_prod<float, double>(double l, double x) { return d2f_fast(-(l * x)); }
+
+// Gradient epilogue for ragged batches (kRaggedEpiThreads per block): grad_a_i = -lambda_i x_{i-1},
+// grad_b_i = -lambda_i x_i, grad_c_i = -lambda_i x_{i+1}, with grad_a = 0 on a line's first row and
+// grad_c = 0 on its last. The blocks take lines in turn, a block's warps consecutive windows of 32
+// rows of its line: x_{i-1} and x_{i+1} come from the neighbouring lanes, across a window's edges
+// by one load each, so that a long line keeps many warps busy.
+constexpr int kRaggedEpiThreads = 128;
 template <class GT, class XT>
-__global__ void __launch_bounds__(256) ragged_epilogue(const int64_t n_lines, const int64_t* __restrict__ roff,
-                                                       const int32_t* __restrict__ rlen, const XT* __restrict__ x,
-                                                       const XT* __restrict__ lam, GT* __restrict__ ga,
-                                                       GT* __restrict__ gb, GT* __restrict__ gc) {
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t l = warp; l < n_lines; l += nwarps) {
-    const int64_t base = roff[l], n = rlen[l];
-    for (int64_t i = lane; i < n; i += 32) {
-      const int64_t e = base + i;
-      const double lv = (double)lam[e];
-      if (gb) gb[e] = (GT)(-lv * (double)x[e]);
-      if (ga) ga[e] = (GT)(i > 0 ? -lv * (double)x[e - 1] : 0.0);
-      if (gc) gc[e] = (GT)(i < n - 1 ? -lv * (double)x[e + 1] : 0.0);
+__global__ void __launch_bounds__(kRaggedEpiThreads) ragged_epilogue(const int64_t n_lines,
+                                                                     const int64_t* __restrict__ roff,
+                                                                     const int32_t* __restrict__ rlen,
+                                                                     const XT* __restrict__ x,
+                                                                     const XT* __restrict__ lam, GT* __restrict__ ga,
+                                                                     GT* __restrict__ gb, GT* __restrict__ gc) {
+  const int lane = threadIdx.x & 31, wb = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int64_t l = blockIdx.x; l < n_lines; l += gridDim.x) {
+    const int64_t base = roff[l];
+    const int n = rlen[l];
+    for (int i0 = wb * 32; i0 < n; i0 += nw * 32) {  // the same for the 32 lanes
+      const int i = i0 + lane;
+      const bool in = i < n;
+      const XT xc = in ? x[base + i] : XT(0);
+      const XT lv = in ? lam[base + i] : XT(0);
+      XT xp = __shfl_up_sync(~0u, xc, 1), xn = __shfl_down_sync(~0u, xc, 1);
+      if (lane == 0) xp = i > 0 ? x[base + i - 1] : XT(0);
+      if (lane == 31) xn = i + 1 < n ? x[base + i + 1] : XT(0);
+      if (in) {
+        const int64_t e = base + i;
+        if (gb) gb[e] = neg_prod<GT>(lv, xc);
+        if (ga) ga[e] = i > 0 ? neg_prod<GT>(lv, xp) : GT(0);
+        if (gc) gc[e] = i + 1 < n ? neg_prod<GT>(lv, xn) : GT(0);
+      }
     }
   }
 }

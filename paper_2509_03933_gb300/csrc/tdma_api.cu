@@ -730,19 +730,18 @@ cudaError_t backward_impl(const tdma_plan_s* p, const void* a, const void* b, co
     } else ragged_refine_kernel<true><<<rc.blocks, rc.threads_per_block, sm, s>>>(A, p->rt);
     e = cudaGetLastError();
     if (e != cudaSuccess || (!ga && !gb && !gc)) return e;
-    const int64_t blocks = std::min<int64_t>((d.n_lines + 7) / 8, 65535);
+    const unsigned blocks = (unsigned)std::min<int64_t>(d.n_lines, 65535), th = kRaggedEpiThreads;
+    const int64_t* ro = d.ragged_offsets;
+    const int32_t* rl = d.ragged_lengths;
     if (d.precision == TDMA_F64)
-      ragged_epilogue<double, double><<<(unsigned)blocks, 256, 0, s>>>(d.n_lines, d.ragged_offsets, d.ragged_lengths,
-                                                                     (const double*)x, (const double*)gd, (double*)ga,
-                                                                     (double*)gb, (double*)gc);
+      ragged_epilogue<double, double><<<blocks, th, 0, s>>>(d.n_lines, ro, rl, (const double*)x, (const double*)gd,
+                                                            (double*)ga, (double*)gb, (double*)gc);
     else if (d.precision == TDMA_F32)
-      ragged_epilogue<float, float><<<(unsigned)blocks, 256, 0, s>>>(d.n_lines, d.ragged_offsets, d.ragged_lengths,
-                                                                   (const float*)x, (const float*)gd, (float*)ga,
-                                                                   (float*)gb, (float*)gc);
+      ragged_epilogue<float, float><<<blocks, th, 0, s>>>(d.n_lines, ro, rl, (const float*)x, (const float*)gd,
+                                                          (float*)ga, (float*)gb, (float*)gc);
     else
-      ragged_epilogue<float, double><<<(unsigned)blocks, 256, 0, s>>>(d.n_lines, d.ragged_offsets, d.ragged_lengths,
-                                                                    (const double*)x, (const double*)gd, (float*)ga,
-                                                                    (float*)gb, (float*)gc);
+      ragged_epilogue<float, double><<<blocks, th, 0, s>>>(d.n_lines, ro, rl, (const double*)x, (const double*)gd,
+                                                           (float*)ga, (float*)gb, (float*)gc);
     return cudaGetLastError();
   }
   if (d.precision == TDMA_F32_REFINE) {
