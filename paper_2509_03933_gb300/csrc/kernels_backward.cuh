@@ -11,8 +11,17 @@
 #pragma once
 #include "tdma.h"
 #include "layout.cuh"
+#include "bits.cuh"
 
 namespace tdma {
+
+// 0 - l x in the gradient type (+0 for a zero product): in the precision of x (for float x exact
+// before its one rounding: the product of two floats fits in a double, so its float rounding is
+// the float product), narrowed to float on the integer pipe for double x and float gradients (the
+// FP64 pipe converts at its own low rate). The results equal those of 0 - l x formed in double and
+// rounded once to the gradient type.
+template <class GT, class XT> TDMA_DEV GT neg_prod(XT l, XT x) { return (GT)(XT(0) - l * x); }
+template <> TDMA_DEV float neg_prod<float, double>(double l, double x) { return d2f_fast(0.0 - l * x); }
 
 template <class GT, class XT, int NR>
 __global__ void __launch_bounds__(256) adjoint_epilogue(const Layout lay, const int bcast, const int line_fastest,
@@ -27,6 +36,17 @@ __global__ void __launch_bounds__(256) adjoint_epilogue(const Layout lay, const 
   else { line = idx / lay.n; i = idx % lay.n; }
   if (!live) { line = 0; i = 0; }
   const int64_t e = lay.off(line) + i * lay.es;
+  if constexpr (NR == 1) {  // one product per gradient: no sum to carry in double
+    if (!bcast) {
+      if (live) {
+        const XT l = lam[e];
+        if (ga) ga[e] = i > 0 ? neg_prod<GT>(l, x[e - lay.es]) : GT(0);
+        if (gb) gb[e] = neg_prod<GT>(l, x[e]);
+        if (gc) gc[e] = i < lay.n - 1 ? neg_prod<GT>(l, x[e + lay.es]) : GT(0);
+      }
+      return;
+    }
+  }
   double sa = 0.0, sb = 0.0, sc = 0.0;
   if (live) {
 #pragma unroll

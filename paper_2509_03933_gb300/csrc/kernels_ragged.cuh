@@ -18,7 +18,7 @@
 #include "layout.cuh"
 #include "kernels_dc.cuh"
 #include "kernels_refine.cuh"
-#include "bits.cuh"
+#include "kernels_backward.cuh"
 
 namespace tdma {
 
@@ -311,12 +311,6 @@ __global__ void __launch_bounds__(kRaggedThreads) ragged_refine_kernel(const Arg
     __syncthreads();
   }
 }
-
-// -l x in the gradient type: in the precision of x (for float x exact before its one rounding: the
-// product of two floats fits in a double), narrowed to float on the integer pipe for double x and
-// float gradients (the FP64 pipe converts at its own low rate).
-template <class GT, class XT> TDMA_DEV GT neg_prod(XT l, XT x) { return (GT)(-(l * x)); }
-template <> TDMA_DEV float neg_prod<float, double>(double l, double x) { return d2f_fast(-(l * x)); }
 
 // Gradient epilogue for ragged batches (kRaggedEpiThreads per block): grad_a_i = -lambda_i x_{i-1},
 // grad_b_i = -lambda_i x_i, grad_c_i = -lambda_i x_{i+1}, with grad_a = 0 on a line's first row and
