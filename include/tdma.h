@@ -42,8 +42,9 @@
  *                    until the estimated error is below refine_tol (relative, per line).
  *   TDMA_F64_REFINE  as TDMA_F64, followed by max_refine_iters (default 1) corrections, for
  *                    badly conditioned lines where plain FP64 elimination stops a few 1e-12
- *                    short: the residual r = d - A x is formed exactly (integer arithmetic on
- *                    the 53-bit significands) and the correction A dx = r is solved in FP32.
+ *                    short: the residual r = d - A x is formed in fixed point to within
+ *                    2^-104 of its largest term (integer arithmetic on the 53-bit significands)
+ *                    and the correction A dx = r is solved in FP32.
  *                    With coef_broadcast, only the lines that need it are corrected: a line whose
  *                    condition-number bound ||A||_inf / delta is below refine_kappa keeps the plain
  *                    FP64 result (delta: the smallest diagonal-dominance margin of a row,
