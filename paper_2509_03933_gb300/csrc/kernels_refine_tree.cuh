@@ -287,7 +287,7 @@ TDMA_DEV void tree_load_tiles(const TmaMaps& maps, float* ta, float* tb, float* 
 // of box p: the 8 lanes of each quarter-warp access of a, b and c then cover the 32 banks, and d
 // costs two wavefronts per quarter. A thread's x rows are contiguous in memory but 8 KB apart from
 // its lane neighbours', so x goes out through the d tile (the thread's own d slots) by TMA store;
-// the next group's a, b and c tiles load early, its d tile at the top once the store has read it.
+// the next group's a, b and c tiles load early, its d tile as soon as the store has read it.
 template <int M, int C, bool XL>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
     refine_tree_kernel(const Args A, const __grid_constant__ TmaMaps maps) {
@@ -491,7 +491,7 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
     // every group after the cluster's first came in during the previous group (XL: its a, b and
     // c), unless in place
     const bool first_group = g == (int64_t)(blockIdx.x / C);
-    if (tid == 0 && (XL || inplace || first_group)) {
+    if (tid == 0 && (inplace || first_group)) {
       bulk_wait_read_all();  // the previous group's x store has read the tile it went through
       tree_load_tiles<M, XL>(maps, ta, tb, tc, td, bar, c_in, c_out, c_p, (inplace || first_group) ? 3 : 2);
     }
@@ -666,6 +666,11 @@ __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(256, 2)
               tma_store_4d(&maps.x, tx + M * 128, c_in + 16, c_out, c_p, 0);
             }
             bulk_commit();
+            if (XL && !inplace && g + n_clusters < n_groups) {  // the next group's d tile, once the store has read it
+              bulk_wait_read_all();
+              const int64_t l1 = (g + n_clusters) * kTreeLines;
+              tree_load_tiles<M, XL>(maps, ta, tb, tc, td, bar, (int)(l1 % ic), (int)(l1 / ic), c_p, 2, true);
+            }
           }
         }
         if (inplace) {
